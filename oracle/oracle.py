@@ -1,0 +1,181 @@
+"""ctypes wrapper of the C oracle (smcx_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Argument marshalling between numpy arrays and the
+C functions; every computation happens in the C file, whose header cites the
+paper's passages each function follows.
+"""
+import ctypes as C
+import numpy as np
+
+from . import build as _build
+
+BCC, FCC = 0, 1
+KMAX = 8
+NA_MAX = 4096
+NB = 1024
+KB_MEV = 8.617333262e-2
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        i32, i64, u64, dbl, vp = C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
+        L.orc_sites_per_cell.argtypes = [i32]
+        L.orc_shells.argtypes = [i32, i32, vp, vp, i32]
+        L.orc_neighbour.argtypes = [i32, i32, i32, i32, i64, vp]
+        L.orc_neighbour.restype = i64
+        L.orc_check_geometry.argtypes = [i32] * 5
+        L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        L.orc_philox4x32_10.restype = None
+        L.orc_attempt_words.argtypes = [u64, u64, i32, i64, vp, vp]
+        L.orc_attempt_words.restype = None
+        L.orc_species_counts.argtypes = [i32, vp, i64, vp]
+        L.orc_init_config.argtypes = [i32, i32, i32, i32, i32, vp, u64, vp]
+        L.orc_pair_counts.argtypes = [i32] * 6 + [vp, vp]
+        L.orc_energy.argtypes = [i32] * 6 + [vp, vp]
+        L.orc_energy.restype = i64
+        L.orc_delta_e.argtypes = [i32] * 6 + [vp, vp, i64, i32]
+        L.orc_delta_e.restype = i64
+        L.orc_sro.argtypes = [i32] * 6 + [vp, vp]
+        L.orc_threshold_tables.argtypes = [dbl, vp, vp, vp]
+        L.orc_threshold.argtypes = [vp, i32, vp, i64]
+        L.orc_threshold.restype = C.c_uint32
+        L.orc_schedule_check.argtypes = [i32] * 9
+        L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
+        L.orc_phase_of.argtypes = [i32] * 8 + [i64, vp]
+        L.orc_phase_of.restype = i64
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def sites_per_cell(kind):
+    return lib().orc_sites_per_cell(kind)
+
+
+def n_sites(kind, dims):
+    nx, ny, nz = dims
+    return nx * ny * nz * sites_per_cell(kind)
+
+
+def shells(kind, K):
+    """Shell sizes z[K] and vectors [sum z, 3] in half-lattice units."""
+    z = np.zeros(KMAX, np.int32)
+    v = np.zeros((512, 3), np.int32)
+    n = lib().orc_shells(kind, K, _p(z), _p(v), 512)
+    if n < 0:
+        raise ValueError("bad shell request")
+    return z[:K].copy(), v[:n].copy()
+
+
+def neighbour(kind, dims, s, vec):
+    v = np.ascontiguousarray(vec, np.int32)
+    return lib().orc_neighbour(kind, *dims, int(s), _p(v))
+
+
+def check_geometry(kind, dims, K):
+    return lib().orc_check_geometry(kind, *dims, K)
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(o))
+    return o
+
+
+def attempt_words(seed, sweep, replica, site):
+    rd = np.zeros(1, np.uint32)
+    ru = np.zeros(1, np.uint32)
+    lib().orc_attempt_words(seed, sweep, replica, site, _p(rd), _p(ru))
+    return int(rd[0]), int(ru[0])
+
+
+def species_counts(M, comp, N):
+    c = np.ascontiguousarray(comp, np.float64)
+    out = np.zeros(M, np.int64)
+    if lib().orc_species_counts(M, _p(c), N, _p(out)):
+        raise ValueError("bad composition")
+    return out
+
+
+def init_config(kind, dims, M, comp, seed):
+    sig = np.zeros(n_sites(kind, dims), np.int8)
+    c = np.ascontiguousarray(comp, np.float64)
+    if lib().orc_init_config(kind, *dims, M, _p(c), seed, _p(sig)):
+        raise ValueError("init failed")
+    return sig
+
+
+def pair_counts(kind, dims, M, K, sigma):
+    Cc = np.zeros((K, M, M), np.int64)
+    sig = np.ascontiguousarray(sigma, np.int8)
+    if lib().orc_pair_counts(kind, *dims, M, K, _p(sig), _p(Cc)):
+        raise ValueError("pair counts failed")
+    return Cc
+
+
+def energy(kind, dims, M, K, V, sigma):
+    Vv = np.ascontiguousarray(V, np.int32)
+    sig = np.ascontiguousarray(sigma, np.int8)
+    return int(lib().orc_energy(kind, *dims, M, K, _p(Vv), _p(sig)))
+
+
+def delta_e(kind, dims, M, K, V, sigma, s, d):
+    Vv = np.ascontiguousarray(V, np.int32)
+    sig = np.ascontiguousarray(sigma, np.int8)
+    return int(lib().orc_delta_e(kind, *dims, M, K, _p(Vv), _p(sig), int(s), int(d)))
+
+
+def sro(kind, dims, M, K, sigma):
+    a = np.zeros((K, M, M), np.float64)
+    sig = np.ascontiguousarray(sigma, np.int8)
+    if lib().orc_sro(kind, *dims, M, K, _p(sig), _p(a)):
+        raise ValueError("sro failed")
+    return a
+
+
+def threshold_tables(T):
+    A = np.zeros(NA_MAX, np.uint32)
+    B = np.zeros(NB, np.uint32)
+    nA = np.zeros(1, np.int32)
+    if lib().orc_threshold_tables(float(T), _p(A), _p(nA), _p(B)):
+        raise ValueError("bad temperature")
+    return A, int(nA[0]), B
+
+
+def threshold(A, nA, B, dE):
+    return int(lib().orc_threshold(_p(A), nA, _p(B), int(dE)))
+
+
+def schedule_check(kind, dims, K, L, nt):
+    return lib().orc_schedule_check(kind, *dims, K, L, *nt)
+
+
+def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
+          L=0, nt=(1, 1, 1)):
+    """Run n_sweeps in place on sigma (int8, contiguous); returns stats
+    (attempts, accepts, same-species proposals)."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    Vv = np.ascontiguousarray(V, np.int32)
+    st = np.zeros(3, np.int64)
+    rc = lib().orc_sweep(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
+                         int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
+                         _p(st))
+    if rc:
+        raise ValueError(f"oracle sweep rejected the request ({rc})")
+    return st
+
+
+def phase_of(kind, dims, L, nt, s):
+    t = np.zeros(3, np.int32)
+    ph = lib().orc_phase_of(kind, *dims, L, *nt, int(s), _p(t))
+    return int(ph), tuple(int(x) for x in t)

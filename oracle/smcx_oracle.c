@@ -1,0 +1,623 @@
+/*
+ * smcx_oracle.c -- plain serial CPU reference of the swap-sweep method.
+ *
+ * TEST INFRASTRUCTURE ONLY (see smcx_oracle.h).  Written for a reader who
+ * checks it against the paper by eye: no blocking, no tables beyond what the
+ * definitions name, neighbours recomputed from coordinates on every use.
+ */
+#include "smcx_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Geometry                                                            */
+/* ------------------------------------------------------------------ */
+
+static const int BASIS_BCC[2][3] = {{0, 0, 0}, {1, 1, 1}};
+static const int BASIS_FCC[4][3] = {{0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+
+int orc_sites_per_cell(int kind) {
+  if (kind == ORC_BCC) return 2;
+  if (kind == ORC_FCC) return 4;
+  return 0;
+}
+
+static const int* basis_vec(int kind, int b) {
+  return kind == ORC_BCC ? BASIS_BCC[b] : BASIS_FCC[b];
+}
+
+/* basis index of a parity residual (rx,ry,rz) in {0,1}^3, or -1 */
+static int basis_index(int kind, int rx, int ry, int rz) {
+  int m = orc_sites_per_cell(kind);
+  for (int b = 0; b < m; b++) {
+    const int* B = basis_vec(kind, b);
+    if (B[0] == rx && B[1] == ry && B[2] == rz) return b;
+  }
+  return -1;
+}
+
+typedef struct {
+  int v[3];
+  int d2;
+} hvec;
+
+static int cmp_hvec(const void* pa, const void* pb) {
+  const hvec* a = (const hvec*)pa;
+  const hvec* b = (const hvec*)pb;
+  if (a->d2 != b->d2) return a->d2 < b->d2 ? -1 : 1;
+  for (int i = 0; i < 3; i++)
+    if (a->v[i] != b->v[i]) return a->v[i] < b->v[i] ? -1 : 1;
+  return 0;
+}
+
+/* All lattice vectors 2c + basis_b with |c_i| <= 4, sorted by length then
+ * lexicographically; the first K distinct lengths are the K shells. */
+int orc_shells(int kind, int K, int* z, int* vecs, int max_vecs) {
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || K < 1 || K > ORC_KMAX) return -1;
+  const int R = 4;
+  int cap = (2 * R + 1) * (2 * R + 1) * (2 * R + 1) * m;
+  hvec* all = (hvec*)malloc(sizeof(hvec) * (size_t)cap);
+  int n = 0;
+  for (int cx = -R; cx <= R; cx++)
+    for (int cy = -R; cy <= R; cy++)
+      for (int cz = -R; cz <= R; cz++)
+        for (int b = 0; b < m; b++) {
+          const int* B = basis_vec(kind, b);
+          hvec h;
+          h.v[0] = 2 * cx + B[0];
+          h.v[1] = 2 * cy + B[1];
+          h.v[2] = 2 * cz + B[2];
+          h.d2 = h.v[0] * h.v[0] + h.v[1] * h.v[1] + h.v[2] * h.v[2];
+          if (h.d2 == 0) continue;
+          all[n++] = h;
+        }
+  qsort(all, (size_t)n, sizeof(hvec), cmp_hvec);
+  int shell = 0, total = 0, prev = -1;
+  for (int i = 0; i < n; i++) {
+    if (all[i].d2 != prev) {
+      if (prev != -1) shell++;
+      prev = all[i].d2;
+      if (shell >= K) break;
+      z[shell] = 0;
+    }
+    if (total >= max_vecs) {
+      free(all);
+      return -1;
+    }
+    vecs[3 * total + 0] = all[i].v[0];
+    vecs[3 * total + 1] = all[i].v[1];
+    vecs[3 * total + 2] = all[i].v[2];
+    z[shell]++;
+    total++;
+  }
+  free(all);
+  return total;
+}
+
+static int wrapi(int p, int n) {
+  int r = p % n;
+  return r < 0 ? r + n : r;
+}
+
+int64_t orc_neighbour(int kind, int nx, int ny, int nz, int64_t s, const int v[3]) {
+  int m = orc_sites_per_cell(kind);
+  int b = (int)(s % m);
+  int64_t c = s / m;
+  int x = (int)(c % nx);
+  c /= nx;
+  int y = (int)(c % ny);
+  int zz = (int)(c / ny);
+  const int* B = basis_vec(kind, b);
+  int px = wrapi(2 * x + B[0] + v[0], 2 * nx);
+  int py = wrapi(2 * y + B[1] + v[1], 2 * ny);
+  int pz = wrapi(2 * zz + B[2] + v[2], 2 * nz);
+  int bb = basis_index(kind, px & 1, py & 1, pz & 1);
+  if (bb < 0) return -1; /* not a lattice vector */
+  return (((int64_t)(pz >> 1) * ny + (py >> 1)) * nx + (px >> 1)) * m + bb;
+}
+
+/* Shell table of one (kind, K), built on demand. */
+typedef struct {
+  int K;
+  int z[ORC_KMAX];
+  int start[ORC_KMAX + 1];
+  int v[512][3];
+} shells_t;
+
+static int load_shells(int kind, int K, shells_t* S) {
+  int tot = orc_shells(kind, K, S->z, &S->v[0][0], 512);
+  if (tot < 0) return -1;
+  S->K = K;
+  S->start[0] = 0;
+  for (int k = 0; k < K; k++) S->start[k + 1] = S->start[k] + S->z[k];
+  return 0;
+}
+
+int orc_check_geometry(int kind, int nx, int ny, int nz, int K) {
+  shells_t S;
+  if (orc_sites_per_cell(kind) == 0 || nx < 1 || ny < 1 || nz < 1) return -1;
+  if (load_shells(kind, K, &S)) return -1;
+  for (int i = 0; i < S.start[K]; i++) {
+    if (wrapi(S.v[i][0], 2 * nx) == 0 && wrapi(S.v[i][1], 2 * ny) == 0 &&
+        wrapi(S.v[i][2], 2 * nz) == 0)
+      return -2; /* a shell vector maps every site onto itself */
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random  */
+/* numbers: as easy as 1, 2, 3"), written from the published round:   */
+/* two 32x32->64 multiplies by M0, M1, a word permutation with key     */
+/* xor, and a Weyl key schedule between rounds.                        */
+/* ------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Counter of one attempt: pair index j = site >> 1 (words 0..1, replica in
+ * the top half of word 1), cumulative sweep index (words 2..3); key = seed.
+ * The even site of the pair uses outputs (0,1), the odd site (2,3). */
+void orc_attempt_words(uint64_t seed, uint64_t sweep, int replica, int64_t site,
+                       uint32_t* rd, uint32_t* ru) {
+  uint64_t j = (uint64_t)site >> 1;
+  uint32_t ctr[4], key[2], out[4];
+  ctr[0] = (uint32_t)j;
+  ctr[1] = (uint32_t)(j >> 32) | ((uint32_t)replica << 16);
+  ctr[2] = (uint32_t)sweep;
+  ctr[3] = (uint32_t)(sweep >> 32);
+  key[0] = (uint32_t)seed;
+  key[1] = (uint32_t)(seed >> 32);
+  orc_philox4x32_10(ctr, key, out);
+  if (site & 1) {
+    *rd = out[2];
+    *ru = out[3];
+  } else {
+    *rd = out[0];
+    *ru = out[1];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial configuration: exact composition (largest remainder), then  */
+/* species by rank of a 64-bit Philox key per site (ties by site id).  */
+/* ------------------------------------------------------------------ */
+
+int orc_species_counts(int M, const double* comp, int64_t N, int64_t* counts) {
+  if (M < 1 || M > ORC_MMAX || N < 0) return -1;
+  double sum = 0.0;
+  for (int p = 0; p < M; p++) {
+    if (!(comp[p] >= 0.0)) return -1;
+    sum += comp[p];
+  }
+  if (fabs(sum - 1.0) > 1e-9) return -1;
+  double frac[ORC_MMAX];
+  int64_t assigned = 0;
+  for (int p = 0; p < M; p++) {
+    double r = comp[p] * (double)N;
+    double f = floor(r);
+    counts[p] = (int64_t)f;
+    frac[p] = r - f;
+    assigned += counts[p];
+  }
+  int64_t left = N - assigned;
+  while (left > 0) {
+    int best = -1;
+    for (int p = 0; p < M; p++)
+      if (best < 0 || frac[p] > frac[best]) best = p; /* ties: lower index */
+    counts[best]++;
+    frac[best] = -1.0;
+    left--;
+  }
+  while (left < 0) { /* only reachable through rounding of sum != 1 */
+    int best = -1;
+    for (int p = 0; p < M; p++)
+      if (counts[p] > 0 && (best < 0 || frac[p] < frac[best])) best = p;
+    counts[best]--;
+    frac[best] = 2.0;
+    left++;
+  }
+  return 0;
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t id;
+} keyed_t;
+
+static int cmp_keyed(const void* pa, const void* pb) {
+  const keyed_t* a = (const keyed_t*)pa;
+  const keyed_t* b = (const keyed_t*)pb;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  if (a->id != b->id) return a->id < b->id ? -1 : 1;
+  return 0;
+}
+
+int orc_init_config(int kind, int nx, int ny, int nz, int M, const double* comp,
+                    uint64_t seed, int8_t* sigma) {
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || nx < 1 || ny < 1 || nz < 1) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t counts[ORC_MMAX];
+  if (orc_species_counts(M, comp, N, counts)) return -1;
+  keyed_t* a = (keyed_t*)malloc(sizeof(keyed_t) * (size_t)N);
+  if (!a) return -1;
+  for (int64_t i = 0; i < N; i++) {
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0x80000000u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    a[i].key = ((uint64_t)out[0] << 32) | out[1];
+    a[i].id = i;
+  }
+  qsort(a, (size_t)N, sizeof(keyed_t), cmp_keyed);
+  int64_t r = 0;
+  for (int p = 0; p < M; p++)
+    for (int64_t c = 0; c < counts[p]; c++) sigma[a[r++].id] = (int8_t)p;
+  free(a);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Energy model (EPI, pair form)                                        */
+/* ------------------------------------------------------------------ */
+
+int orc_pair_counts(int kind, int nx, int ny, int nz, int M, int K,
+                    const int8_t* sigma, int64_t* C) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  memset(C, 0, sizeof(int64_t) * (size_t)K * M * M);
+  for (int64_t s = 0; s < N; s++) {
+    int p = sigma[s];
+    for (int k = 0; k < K; k++)
+      for (int i = S.start[k]; i < S.start[k + 1]; i++) {
+        int64_t t = orc_neighbour(kind, nx, ny, nz, s, S.v[i]);
+        C[((int64_t)k * M + p) * M + sigma[t]]++;
+      }
+  }
+  return 0;
+}
+
+/* E = 1/2 sum over sites i, shells k and vectors v of V_k[s_i][s_{i+v}]:
+ * every unordered pair of the pair model counted once (Eq. Total_EPI with
+ * the single-site and bias terms dropped at fixed composition). */
+int64_t orc_energy(int kind, int nx, int ny, int nz, int M, int K,
+                   const int32_t* V, const int8_t* sigma) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return INT64_MIN;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t twice = 0;
+  for (int64_t s = 0; s < N; s++)
+    for (int k = 0; k < K; k++)
+      for (int i = S.start[k]; i < S.start[k + 1]; i++) {
+        int64_t t = orc_neighbour(kind, nx, ny, nz, s, S.v[i]);
+        twice += V[((int64_t)k * M + sigma[s]) * M + sigma[t]];
+      }
+  return twice / 2;
+}
+
+/* Energy change of swapping site s (species a) with its shell-1 neighbour
+ * along direction dir (species b), from the environments of the two sites
+ * only: for every pair model the other sites' local energies change by the
+ * same bond terms, so the change is the bond sum around s and s'. */
+static int64_t delta_e_local(int kind, int nx, int ny, int nz, int M, const shells_t* S,
+                             const int32_t* V, const int8_t* sigma, int64_t s, int64_t sp) {
+  int a = sigma[s], b = sigma[sp];
+  int64_t d = 0;
+  for (int k = 0; k < S->K; k++)
+    for (int i = S->start[k]; i < S->start[k + 1]; i++) {
+      int64_t t = orc_neighbour(kind, nx, ny, nz, s, S->v[i]);
+      if (t == s || t == sp) continue;
+      int c = sigma[t];
+      d += (int64_t)V[((int64_t)k * M + b) * M + c] - V[((int64_t)k * M + a) * M + c];
+    }
+  for (int k = 0; k < S->K; k++)
+    for (int i = S->start[k]; i < S->start[k + 1]; i++) {
+      int64_t t = orc_neighbour(kind, nx, ny, nz, sp, S->v[i]);
+      if (t == s || t == sp) continue;
+      int c = sigma[t];
+      d += (int64_t)V[((int64_t)k * M + a) * M + c] - V[((int64_t)k * M + b) * M + c];
+    }
+  return d;
+}
+
+int64_t orc_delta_e(int kind, int nx, int ny, int nz, int M, int K,
+                    const int32_t* V, const int8_t* sigma, int64_t s, int dir) {
+  shells_t S;
+  if (load_shells(kind, K, &S)) return INT64_MIN;
+  if (dir < 0 || dir >= S.z[0]) return INT64_MIN;
+  int64_t sp = orc_neighbour(kind, nx, ny, nz, s, S.v[dir]);
+  return delta_e_local(kind, nx, ny, nz, M, &S, V, sigma, s, sp);
+}
+
+/* Warren-Cowley SRO over ordered pairs: alpha = 1 - C_k[p][q]/(z_k N_p c_q),
+ * c_q = N_q/N; 0 where a species is absent. */
+int orc_sro(int kind, int nx, int ny, int nz, int M, int K, const int8_t* sigma,
+            double* alpha) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t* C = (int64_t*)malloc(sizeof(int64_t) * (size_t)K * M * M);
+  int64_t Np[ORC_MMAX] = {0};
+  for (int64_t s = 0; s < N; s++) Np[sigma[s]]++;
+  orc_pair_counts(kind, nx, ny, nz, M, K, sigma, C);
+  for (int k = 0; k < K; k++)
+    for (int p = 0; p < M; p++)
+      for (int q = 0; q < M; q++) {
+        double denom = (double)S.z[k] * (double)Np[p] * ((double)Np[q] / (double)N);
+        double v = 0.0;
+        if (denom > 0.0) v = 1.0 - (double)C[((int64_t)k * M + p) * M + q] / denom;
+        alpha[((int64_t)k * M + p) * M + q] = v;
+      }
+  free(C);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Metropolis acceptance: P = 1 for dE <= 0, exp(-beta dE) otherwise,   */
+/* realised as u < thr(dE) with a 32-bit uniform u and                 */
+/*   F(d)    = min(2^32-1, floor(2^32 exp(-d * 0.01 meV / (kB T))))    */
+/*   thr(dE) = (A[dE >> 10] * B[dE & 1023]) >> 32,                     */
+/*   A[h] = F(1024 h), B[l] = F(l); thr = 0 once A reaches 0.          */
+/* ------------------------------------------------------------------ */
+
+static uint32_t fixed_boltzmann(int64_t d, double beta_q) {
+  double e = exp(-((double)d * beta_q));
+  double v = e * 4294967296.0;
+  if (v >= 4294967295.0) return 4294967295u;
+  return (uint32_t)v;
+}
+
+int orc_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B) {
+  if (!(T > 0.0)) return -1;
+  double beta_q = 0.01 / (ORC_KB_MEV * T);
+  int n = 0;
+  for (int h = 0; h < ORC_NA_MAX; h++) {
+    uint32_t a = fixed_boltzmann((int64_t)h * ORC_NB, beta_q);
+    A[h] = a;
+    if (a == 0) break;
+    n = h + 1;
+  }
+  for (int h = n; h < ORC_NA_MAX; h++) A[h] = 0;
+  for (int l = 0; l < ORC_NB; l++) B[l] = fixed_boltzmann(l, beta_q);
+  *nA = n;
+  return 0;
+}
+
+uint32_t orc_threshold(const uint32_t* A, int nA, const uint32_t* B, int64_t dE) {
+  if (dE < 0) return 0xFFFFFFFFu;
+  int64_t h = dE >> 10;
+  if (h >= nA) return 0;
+  return (uint32_t)(((uint64_t)A[h] * (uint64_t)B[dE & (ORC_NB - 1)]) >> 32);
+}
+
+/* ------------------------------------------------------------------ */
+/* Schedule: generalized checkerboard.                                  */
+/*   Each axis is cut into nt tiles (sizes differ by at most one, the   */
+/*   first n % nt tiles one larger).  Tile colour = parity of the tile  */
+/*   index on each axis (8 colours).  Inside a tile, the intra colour   */
+/*   of a site is ((z-z0) mod L, (y-y0) mod L, (x-x0) mod L, b), i.e.   */
+/*   its place in an L^3 link cell measured from the tile origin.  A    */
+/*   sweep visits tile colours 0..7, and inside each the n_A = L^3 m    */
+/*   intra colours in the order ic = ((cz L + cy) L + cx) m + b.  With  */
+/*   one tile on every axis this is the paper's link-cell schedule.     */
+/* ------------------------------------------------------------------ */
+
+/* Largest |component| over shell-1 vectors (R1) and over shells 1..K (RK). */
+static void reaches(const shells_t* S, int* R1, int* RK) {
+  *R1 = 0;
+  *RK = 0;
+  for (int i = 0; i < S->start[S->K]; i++)
+    for (int c = 0; c < 3; c++) {
+      int a = abs(S->v[i][c]);
+      if (a > *RK) *RK = a;
+      if (i < S->z[0] && a > *R1) *R1 = a;
+    }
+}
+
+int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
+                       int ntx, int nty, int ntz) {
+  shells_t S;
+  if (orc_sites_per_cell(kind) == 0 || load_shells(kind, K, &S)) return -1;
+  if (orc_check_geometry(kind, nx, ny, nz, K)) return -1;
+  if (L == 0) return 0; /* serial */
+  int R1, RK;
+  reaches(&S, &R1, &RK);
+  /* same intra colour: half-unit separation >= 2L on some axis; partners
+   * move each end by <= R1, the read reach is RK. */
+  int Lmin = (2 * R1 + RK) / 2 + 1;
+  /* same tile colour, different tiles: a whole tile of g cells between
+   * them, half-unit separation >= 2g + 1. */
+  int gmin = (2 * R1 + RK - 1) / 2 + 1;
+  if (L < Lmin) return -2;
+  int n[3] = {nx, ny, nz}, nt[3] = {ntx, nty, ntz};
+  for (int a = 0; a < 3; a++) {
+    if (nt[a] < 1) return -2;
+    if (nt[a] == 1) {
+      if (n[a] % L) return -2;
+    } else {
+      if (nt[a] % 2) return -2;
+      if (n[a] / nt[a] < gmin) return -2;
+    }
+  }
+  return 0;
+}
+
+static void tile_bounds(int n, int nt, int i, int* start, int* size) {
+  int base = n / nt, rem = n % nt;
+  *size = base + (i < rem ? 1 : 0);
+  *start = i * base + (i < rem ? i : rem);
+}
+
+static int tile_of(int n, int nt, int x) {
+  for (int i = 0; i < nt; i++) {
+    int st, sz;
+    tile_bounds(n, nt, i, &st, &sz);
+    if (x >= st && x < st + sz) return i;
+  }
+  return -1;
+}
+
+int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,
+                     int ntz, int64_t s, int* tile) {
+  int m = orc_sites_per_cell(kind);
+  if (L == 0) return -1;
+  int b = (int)(s % m);
+  int64_t c = s / m;
+  int x = (int)(c % nx);
+  c /= nx;
+  int y = (int)(c % ny);
+  int z = (int)(c / ny);
+  int ix = tile_of(nx, ntx, x), iy = tile_of(ny, nty, y), iz = tile_of(nz, ntz, z);
+  int x0, y0, z0, sz;
+  tile_bounds(nx, ntx, ix, &x0, &sz);
+  tile_bounds(ny, nty, iy, &y0, &sz);
+  tile_bounds(nz, ntz, iz, &z0, &sz);
+  int tc = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
+  int64_t nA = (int64_t)L * L * L * m;
+  int64_t ic = ((((int64_t)((z - z0) % L) * L + (y - y0) % L) * L + (x - x0) % L) * m) + b;
+  if (tile) {
+    tile[0] = ix;
+    tile[1] = iy;
+    tile[2] = iz;
+  }
+  return tc * nA + ic;
+}
+
+typedef struct {
+  int kind, nx, ny, nz, m, M;
+  const shells_t* S;
+  const int32_t* V;
+  int8_t* sigma;
+  const uint32_t *A, *B;
+  int nA;
+  uint64_t seed, sweep;
+  int replica;
+  int64_t* stats;
+} attempt_ctx;
+
+/* One canonical swap trial at site s (Supplementary "Monte Carlo
+ * Simulation Algorithms"): partner = a uniformly chosen shell-1 neighbour,
+ * energy change from the two sites' environments, Metropolis acceptance. */
+static void attempt(attempt_ctx* c, int64_t s) {
+  uint32_t rd, ru;
+  orc_attempt_words(c->seed, c->sweep, c->replica, s, &rd, &ru);
+  int z1 = c->S->z[0];
+  int dir = (int)(((uint64_t)rd * (uint64_t)z1) >> 32);
+  int64_t sp = orc_neighbour(c->kind, c->nx, c->ny, c->nz, s, c->S->v[dir]);
+  c->stats[0]++;
+  int a = c->sigma[s], b = c->sigma[sp];
+  if (a == b) {
+    c->stats[2]++;
+    return;
+  }
+  int64_t dE = delta_e_local(c->kind, c->nx, c->ny, c->nz, c->M, c->S, c->V, c->sigma, s, sp);
+  int accept = 0;
+  if (dE <= 0)
+    accept = 1;
+  else if (ru < orc_threshold(c->A, c->nA, c->B, dE))
+    accept = 1;
+  if (accept) {
+    c->sigma[s] = (int8_t)b;
+    c->sigma[sp] = (int8_t)a;
+    c->stats[1]++;
+  }
+}
+
+int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+              int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+              uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+              int64_t* stats) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  if (orc_schedule_check(kind, nx, ny, nz, K, L, ntx, nty, ntz)) return -2;
+  uint32_t* A = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NA_MAX);
+  uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NB);
+  int nA;
+  if (!A || !B || orc_threshold_tables(T, A, &nA, B)) {
+    free(A);
+    free(B);
+    return -1;
+  }
+  attempt_ctx c;
+  c.kind = kind;
+  c.nx = nx;
+  c.ny = ny;
+  c.nz = nz;
+  c.m = m;
+  c.M = M;
+  c.S = &S;
+  c.V = V;
+  c.sigma = sigma;
+  c.A = A;
+  c.B = B;
+  c.nA = nA;
+  c.seed = seed;
+  c.replica = replica;
+  c.stats = stats;
+  stats[0] = stats[1] = stats[2] = 0;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  for (int64_t n = 0; n < n_sweeps; n++) {
+    c.sweep = sweep0 + (uint64_t)n;
+    if (L == 0) {
+      for (int64_t s = 0; s < N; s++) attempt(&c, s);
+      continue;
+    }
+    int nA_ic = L * L * L * m;
+    for (int tc = 0; tc < 8; tc++)
+      for (int ic = 0; ic < nA_ic; ic++) {
+        int b = ic % m;
+        int cx = (ic / m) % L, cy = (ic / m / L) % L, cz = ic / m / L / L;
+        for (int iz = 0; iz < ntz; iz++)
+          for (int iy = 0; iy < nty; iy++)
+            for (int ix = 0; ix < ntx; ix++) {
+              if (((ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2)) != tc) continue;
+              int x0, sx, y0, sy, z0, sz;
+              tile_bounds(nx, ntx, ix, &x0, &sx);
+              tile_bounds(ny, nty, iy, &y0, &sy);
+              tile_bounds(nz, ntz, iz, &z0, &sz);
+              for (int z = z0 + cz; z < z0 + sz; z += L)
+                for (int y = y0 + cy; y < y0 + sy; y += L)
+                  for (int x = x0 + cx; x < x0 + sx; x += L)
+                    attempt(&c, (((int64_t)z * ny + y) * nx + x) * m + b);
+            }
+      }
+  }
+  free(A);
+  free(B);
+  return 0;
+}

@@ -1,0 +1,108 @@
+/*
+ * smcx_oracle.h -- plain serial CPU reference of the swap-sweep method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists so that the CUDA path can be
+ * checked against an independent, obviously-correct implementation.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header, table or constant generator with the CUDA
+ * library: the geometry, the Philox generator, the Metropolis threshold table,
+ * the schedule and the energy arithmetic are all written out again here.
+ *
+ * Paper: Liu et al., "Revealing Nanostructures in High-Entropy Alloys via
+ * Machine-Learning Accelerated Scalable Monte Carlo Simulation" (SMC-X).
+ *   - EPI energy model: Method "The EPI and qSRO model", Eqs. Linear_EPI and
+ *     Total_EPI.
+ *   - Pairwise energy change of a swap from the two swapped sites only:
+ *     same section, the paragraph after Eq. Total_EPI.
+ *   - Metropolis acceptance and canonical swap trial: Supplementary
+ *     "Monte Carlo Simulation Algorithms" (acceptance equation).
+ *   - Sweep = one trial per lattice site: same section; also Method
+ *     "Theoretical speedup".
+ *   - Link-cell generalized checkerboard: Results "Performance of the SMC-X
+ *     algorithm" and Method "Implementation of SMC-GPU" (link-cell size item).
+ *
+ * Parity status of every function is stated beside it.  Every function is
+ * pinned by a test under tests/ against something other than itself.
+ *
+ * Conventions (readings of the paper, all listed in the design notes):
+ *   - positions in half-lattice-constant integer units; BCC basis (0,0,0),
+ *     (1,1,1); FCC basis (0,0,0),(1,1,0),(1,0,1),(0,1,1);
+ *   - canonical site id = ((z*ny + y)*nx + x)*m + b;
+ *   - shells: lattice vectors grouped by length, ascending; within a shell
+ *     in ascending lexicographic (vx, vy, vz) order;
+ *   - V is int32 in units of 0.01 meV, [K][M][M], symmetric;
+ *   - E = 1/2 sum_i sum_k sum_{v in shell k} V_k[s_i][s_{i+v}]  (exact int64).
+ */
+#ifndef SMCX_ORACLE_H
+#define SMCX_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_BCC 0
+#define ORC_FCC 1
+#define ORC_KMAX 8
+#define ORC_MMAX 15
+#define ORC_NA_MAX 4096      /* high-part entries of the acceptance table */
+#define ORC_NB 1024          /* low-part entries (10 bits) */
+
+/* Boltzmann constant in meV/K (exact SI value 1.380649e-23 J/K). */
+#define ORC_KB_MEV 8.617333262e-2
+
+/* ---- geometry (pinned: textbook coordination numbers, closed-form energies) */
+int orc_sites_per_cell(int kind);
+/* Enumerate the first K shells; z[k] = size of shell k, vecs = concatenated
+ * (vx,vy,vz) triples (half units).  Returns total vector count, or -1. */
+int orc_shells(int kind, int K, int* z, int* vecs, int max_vecs);
+/* Neighbour of site s along half-unit vector v with periodic wrap. */
+int64_t orc_neighbour(int kind, int nx, int ny, int nz, int64_t s, const int v[3]);
+/* 0 if no shell vector of the first K shells maps a site onto itself. */
+int orc_check_geometry(int kind, int nx, int ny, int nz, int K);
+
+/* ---- Philox4x32-10 (pinned: ATen's philox_engine run on the same inputs) */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Random words of one attempt at `site` (direction word rd, uniform word ru). */
+void orc_attempt_words(uint64_t seed, uint64_t sweep, int replica, int64_t site,
+                       uint32_t* rd, uint32_t* ru);
+
+/* ---- initial configuration (pinned: numpy lexsort of the same keys) */
+int orc_species_counts(int M, const double* comp, int64_t N, int64_t* counts);
+int orc_init_config(int kind, int nx, int ny, int nz, int M, const double* comp,
+                    uint64_t seed, int8_t* sigma);
+
+/* ---- energy model (pinned: B2 / L1_2 / pure-element closed forms,
+ *      row-sum identity, brute-force E(after)-E(before)) */
+int orc_pair_counts(int kind, int nx, int ny, int nz, int M, int K,
+                    const int8_t* sigma, int64_t* C /*[K][M][M]*/);
+int64_t orc_energy(int kind, int nx, int ny, int nz, int M, int K,
+                   const int32_t* V, const int8_t* sigma);
+int64_t orc_delta_e(int kind, int nx, int ny, int nz, int M, int K,
+                    const int32_t* V, const int8_t* sigma, int64_t s, int dir);
+int orc_sro(int kind, int nx, int ny, int nz, int M, int K, const int8_t* sigma,
+            double* alpha /*[K][M][M]*/);
+
+/* ---- acceptance table (pinned: closed-form exp and its limits) */
+int orc_threshold_tables(double T, uint32_t* A /*[ORC_NA_MAX]*/, int* nA,
+                         uint32_t* B /*[ORC_NB]*/);
+uint32_t orc_threshold(const uint32_t* A, int nA, const uint32_t* B, int64_t dE);
+
+/* ---- schedule and sweep (pinned: exact enumeration of the canonical
+ *      distribution, split-sweep identity, brute-force phase independence) */
+/* L == 0 selects the serial schedule (canonical site order). */
+int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
+                       int ntx, int nty, int ntz);
+int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+              int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+              uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+              int64_t* stats /*[3]: attempts, accepts, same-species*/);
+/* Phase id of a site under schedule (L, nt*): tile colour * nA + intra colour,
+ * or -1 for the serial schedule.  Used by the independence test. */
+int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,
+                     int ntz, int64_t s, int* tile /*[3] out, may be NULL*/);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
