@@ -1,0 +1,212 @@
+/*
+ * smcx.h -- C ABI of the GB300 (sm_103a) swap-sweep library for SMC-X.
+ *
+ * Method: Liu et al., "Revealing Nanostructures in High-Entropy Alloys via
+ * Machine-Learning Accelerated Scalable Monte Carlo Simulation" (SMC-X,
+ * SMC-GPU).  The library runs the canonical-ensemble (fixed composition)
+ * Metropolis swap sweep of an effective-pair-interaction (EPI) lattice model
+ * on one GPU:
+ *   - energy model: EPI over K neighbour shells (Method "The EPI and qSRO
+ *     model", Eq. Linear_EPI, Eq. Total_EPI), pair form
+ *       E = 1/2 sum_i sum_k sum_{v in shell k} V_k[s_i][s_{i+v}],
+ *     V in int32 units of 0.01 meV, so every energy is an exact integer;
+ *   - trial: swap a site with a uniformly chosen nearest neighbour (Results
+ *     "Performance of the SMC-X algorithm"; Supplementary "Monte Carlo
+ *     Simulation Algorithms", canonical swap);
+ *   - energy change from the two swapped sites' environments only (Method
+ *     "The EPI and qSRO model", paragraph after Eq. Total_EPI);
+ *   - Metropolis acceptance P = min(1, exp(-beta dE)) (Supplementary, the
+ *     acceptance equation), realised as u < thr(dE) with a 32-bit uniform u
+ *     and an integer table thr computed on the host in double precision:
+ *       F(d) = min(2^32-1, floor(2^32 exp(-d 0.01 meV / (k_B T)))),
+ *       thr(d) = (A[d >> 10] * B[d & 1023]) >> 32, A[h] = F(1024 h), B[l] = F(l);
+ *   - sweep = one trial per site (Supplementary, sweep definition), ordered by
+ *     the generalized checkerboard (Results "Performance of the SMC-X
+ *     algorithm"; Method "Implementation of SMC-GPU", link-cell item) in its
+ *     tiled form described at smcx_sched;
+ *   - trial random numbers: Philox4x32-10 (the paper uses cuRAND, Method
+ *     "Implementation of SMC-GPU", random-number item) with counter
+ *     (pair index j = site >> 1, replica << 16 | j >> 32, sweep lo, sweep hi)
+ *     and key = seed; the even site of a pair uses outputs (0,1), the odd
+ *     site (2,3); direction = floor(word0 * z1 / 2^32), u = word1.
+ *
+ * Conventions
+ *   - Lattices: SMCX_BCC (2 sites per cubic cell, basis (0,0,0),(1/2,1/2,1/2))
+ *     and SMCX_FCC (4 sites, basis (0,0,0),(1/2,1/2,0),(1/2,0,1/2),(0,1/2,1/2));
+ *     dimensions "nx x ny x nz x m" as in Tab. models_summary; periodic.
+ *   - Canonical site id = ((z*ny + y)*nx + x)*m + b.
+ *   - Shells: lattice vectors grouped by length; inside a shell in ascending
+ *     lexicographic order of the half-lattice-unit components.
+ *   - Every call returns an int status: SMCX_OK (0) or a negative SMCX_E_*
+ *     code; smcx_last_error() gives a message for the calling thread.  No
+ *     C++ exception crosses the ABI.
+ *   - Ownership: a lattice handle owns all device memory it allocates; host
+ *     arrays passed in are owned by the caller and read or written only
+ *     during the call.  Work is ordered on the handle's CUDA stream; calls
+ *     that return host data synchronise that stream before returning;
+ *     smcx_sweep only enqueues.  A handle must not be used by two threads at
+ *     once.
+ *   - No CPU fallback: every compute call runs CUDA kernels and fails with
+ *     SMCX_E_CUDA when no device is usable.
+ */
+#ifndef SMCX_H
+#define SMCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SMCX_OK 0
+#define SMCX_E_INVALID_ARG (-1) /* a bad argument value or a NULL pointer      */
+#define SMCX_E_NO_EPI (-2)      /* sweep/energy before smcx_set_epi            */
+#define SMCX_E_SCHEDULE (-3)    /* no valid checkerboard for this lattice      */
+#define SMCX_E_CUDA (-4)        /* a CUDA runtime error (message has details)  */
+#define SMCX_E_OOM (-5)         /* device allocation failed                    */
+#define SMCX_E_TIMEOUT (-6)     /* a bounded device wait gave up               */
+#define SMCX_E_RANGE (-7)       /* |dE| of this EPI table may overflow int32   */
+#define SMCX_E_UNSUPPORTED (-8) /* valid request this build does not run       */
+
+/* ---- enumerations ---------------------------------------------------- */
+#define SMCX_BCC 0
+#define SMCX_FCC 1
+#define SMCX_INT8 0    /* one int8 species id per site                        */
+#define SMCX_PACKED4 1 /* two 4-bit ids per byte, byte = site pair (id >> 1)  */
+#define SMCX_NA_MAX 4096 /* entries of the high-part acceptance table A       */
+#define SMCX_NB 1024     /* entries of the low-part acceptance table B        */
+
+/*
+ * Checkerboard schedule (Results "Performance of the SMC-X algorithm":
+ * link cells of n_A sites; trials at the same i_A in different link cells are
+ * independent when the link cell is larger than the interaction reach).
+ *
+ * Each axis is cut into nt[a] tiles whose sizes differ by at most one (the
+ * first n % nt tiles are one cell larger).  Tile colour = parity of the tile
+ * index on each axis.  Inside a tile, a site's intra colour is its place in
+ * an L^3 link cell counted from the tile origin, ic = ((cz L + cy) L + cx) m + b.
+ * A sweep runs tile colours 0..7 in order and, inside each, the L^3 m intra
+ * colours in order; all trials of one (tile colour, intra colour) phase are
+ * independent, and trials in different tiles of one tile colour are
+ * independent whatever their intra colour, so tiles of one colour may run
+ * concurrently at different intra colours.
+ *   - nt = {1,1,1}: the paper's link-cell schedule (n_A sequential steps of
+ *     n_C parallel trials); every n must be a multiple of L.
+ *   - otherwise every nt must be even (>= 2) and every tile at least as thick
+ *     as the interaction reach requires (3 cells for BCC <= 4 shells).
+ * L must exceed the reach: L >= 3 for BCC with 2..4 shells and FCC with 2..3.
+ * Passing NULL (or L == 0) asks the library to choose; its choice is L == 0
+ * ("none") for lattices too small for any valid schedule, in which case the
+ * handle works for configuration I/O and observables but smcx_sweep returns
+ * SMCX_E_SCHEDULE.
+ */
+typedef struct smcx_sched {
+  int32_t L;
+  int32_t nt[3];
+} smcx_sched;
+
+typedef struct smcx_lattice smcx_lattice;
+
+/* Message of the last failed call on this thread ("" if none).  The string is
+ * owned by the library and valid until the next call on this thread. */
+const char* smcx_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int smcx_version(void);
+
+/*
+ * Create a lattice with an exact-composition initial configuration.
+ *   kind      SMCX_BCC or SMCX_FCC;  nx, ny, nz >= 1 cubic cells.
+ *   M         species count, 1 <= M <= 15 (PACKED4) or 127 (INT8); the sweep
+ *             kernels of this build run M <= 8.
+ *   comp      [M] fractions summing to 1; counts are floor(c_p N) plus one for
+ *             the largest remainders (ties to the lower index).
+ *   init_seed species are placed by the rank of a 64-bit Philox key per site
+ *             (counter (id lo, id hi, 0, 2^31), key init_seed; ties by id): the
+ *             paper's random initial configuration (Results, FeCoNiAlTi
+ *             section), made exactly reproducible.
+ *   storage   SMCX_INT8 or SMCX_PACKED4.
+ *   sched     schedule (see smcx_sched) or NULL for the library's choice.
+ *   stream    a cudaStream_t (NULL = legacy default stream) that orders all
+ *             work of the handle.
+ * Returns SMCX_E_SCHEDULE if no valid schedule exists for these dimensions,
+ * SMCX_E_OOM if the device buffers cannot be allocated.
+ */
+int smcx_lattice_create(smcx_lattice** out, int kind, int nx, int ny, int nz, int M,
+                        const double* comp, uint64_t init_seed, int storage,
+                        const smcx_sched* sched, void* stream);
+
+/* Release the handle and its device memory (synchronises its stream). */
+int smcx_lattice_destroy(smcx_lattice* h);
+
+/*
+ * Set the EPI table V[K][M][M] (int32, 0.01 meV units), copied by the call.
+ * V must be symmetric in its species indices (Eq. Total_EPI sums unordered
+ * pairs).  K ranges over 1..4 (BCC) or 1..3 (FCC).  Returns SMCX_E_RANGE when
+ * the largest possible |dE| would not fit int32, SMCX_E_SCHEDULE when the
+ * handle's schedule is too small for the new interaction reach.
+ */
+int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V);
+
+/* Replace the schedule (NULL = library's choice).  The trajectory depends on
+ * it: equal schedules give bit-identical results. */
+int smcx_set_schedule(smcx_lattice* h, const smcx_sched* sched);
+int smcx_get_schedule(const smcx_lattice* h, smcx_sched* out);
+
+/*
+ * Enqueue n_sweeps >= 0 sweeps at temperature T (kelvin, > 0) with Philox
+ * seed `seed`.  The Philox counter uses the handle's cumulative sweep index,
+ * so sweep(T, a, s); sweep(T, b, s) equals sweep(T, a + b, s).  Asynchronous.
+ */
+int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed);
+
+/* Exact total energy (0.01 meV units) of the current configuration. */
+int smcx_energy(smcx_lattice* h, int64_t* E);
+
+/* Ordered pair counts C[k][p][q] = #{(i, v in shell k): s_i = p, s_{i+v} = q}
+ * (int64, K*M*M entries, symmetric); E = 1/2 sum V*C. */
+int smcx_pair_counts(smcx_lattice* h, int64_t* C);
+
+/* Warren-Cowley SRO over ordered pairs, alpha_k[p][q] = 1 - C_k[p][q] /
+ * (z_k N_p c_q), c_q = N_q / N (0 where a species is absent); the local
+ * fraction of Method Eq. quadratic_local_SRO summed over the lattice. */
+int smcx_sro(smcx_lattice* h, double* alpha);
+
+/* Copy the configuration out / in as int8 species ids in canonical site
+ * order (N = nx*ny*nz*m entries).  set_config checks ids < M and keeps the
+ * sweep counter; it does not require the old composition. */
+int smcx_get_config(smcx_lattice* h, int8_t* host);
+int smcx_set_config(smcx_lattice* h, const int8_t* host);
+
+/* Cumulative sweep index and trial statistics since creation (int64[4]):
+ * stats[0] = trials, stats[1] = accepted swaps, stats[2] = proposals whose
+ * two sites held the same species (no-ops; counted as trials), stats[3] =
+ * sum of the energy changes of accepted swaps (0.01 meV), so that
+ * E(now) = E(creation or last set_config) + stats[3] - (stats[3] then). */
+int smcx_get_state(smcx_lattice* h, uint64_t* sweep_cum, int64_t* stats);
+int smcx_set_sweep_counter(smcx_lattice* h, uint64_t sweep_cum);
+
+/* Device pointer and size in bytes of the species buffer (INT8: N bytes;
+ * PACKED4: ceil(N/2) bytes).  Owned by the handle. */
+int smcx_device_buffer(const smcx_lattice* h, void** ptr, size_t* bytes);
+
+/* Block until all work enqueued on the handle's stream is done. */
+int smcx_synchronize(smcx_lattice* h);
+
+/* Total sites N and the handle's geometry. */
+int smcx_lattice_info(const smcx_lattice* h, int* kind, int* dims /*[3]*/, int* M,
+                      int* K, int* storage, int64_t* n_sites);
+
+/*
+ * Host-only helper: the acceptance tables this library uses at temperature T
+ * (A[SMCX_NA_MAX], B[SMCX_NB], nA = entries of A before the first zero).
+ * Needs no GPU.
+ */
+int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMCX_H */

@@ -163,10 +163,10 @@ def schedule_check(kind, dims, K, L, nt):
 def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
           L=0, nt=(1, 1, 1)):
     """Run n_sweeps in place on sigma (int8, contiguous); returns stats
-    (attempts, accepts, same-species proposals)."""
+    (attempts, accepts, same-species proposals, sum of accepted dE)."""
     assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
     Vv = np.ascontiguousarray(V, np.int32)
-    st = np.zeros(3, np.int64)
+    st = np.zeros(4, np.int64)
     rc = lib().orc_sweep(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
                          int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
                          _p(st))

@@ -554,6 +554,7 @@ static void attempt(attempt_ctx* c, int64_t s) {
     c->sigma[s] = (int8_t)b;
     c->sigma[sp] = (int8_t)a;
     c->stats[1]++;
+    c->stats[3] += dE;
   }
 }
 
@@ -589,7 +590,7 @@ int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
   c.seed = seed;
   c.replica = replica;
   c.stats = stats;
-  stats[0] = stats[1] = stats[2] = 0;
+  stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int64_t N = (int64_t)nx * ny * nz * m;
   for (int64_t n = 0; n < n_sweeps; n++) {
     c.sweep = sweep0 + (uint64_t)n;

@@ -96,7 +96,8 @@ int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
 int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
-              int64_t* stats /*[3]: attempts, accepts, same-species*/);
+              int64_t* stats /*[4]: attempts, accepts, same-species,
+                                 sum of accepted dE*/);
 /* Phase id of a site under schedule (L, nt*): tile colour * nA + intra colour,
  * or -1 for the serial schedule.  Used by the independence test. */
 int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,

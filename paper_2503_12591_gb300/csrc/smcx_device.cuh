@@ -1,0 +1,95 @@
+// Device-side building blocks shared by the kernel translation units.
+#pragma once
+
+#include <stdint.h>
+
+#include "smcx_internal.h"
+
+namespace smcx {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies with a word permutation and key xor; the key is
+// bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Random words of the pair (site id >> 1) in sweep `sweep` of replica `rep`.
+__device__ __forceinline__ uint4 attempt_block(unsigned long long gid, unsigned long long sweep,
+                                               int rep, uint32_t seed_lo, uint32_t seed_hi) {
+  const unsigned long long j = gid >> 1;
+  return philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32) | ((uint32_t)rep << 16),
+                                  (uint32_t)sweep, (uint32_t)(sweep >> 32)),
+                       make_uint2(seed_lo, seed_hi));
+}
+
+// Shell sizes of the cubic lattices (BCC 8, 6, 12, 24; FCC 12, 6, 24).
+__host__ __device__ constexpr int shell_size(int kind, int k) {
+  return kind == kBCC ? (k == 0 ? 8 : k == 1 ? 6 : k == 2 ? 12 : 24)
+                      : (k == 0 ? 12 : k == 1 ? 6 : 24);
+}
+__host__ __device__ constexpr int vec_count(int kind, int K) {
+  return K <= 0 ? 0 : vec_count(kind, K - 1) + shell_size(kind, K - 1);
+}
+__host__ __device__ constexpr int cell_sites(int kind) { return kind == kBCC ? 2 : 4; }
+
+// Metropolis decision with the two-level integer table (see smcx.h).
+__device__ __forceinline__ bool metropolis_accept(int dE, uint32_t u, const uint32_t* A, int nA,
+                                                  const uint32_t* B) {
+  if (dE <= 0) return true;
+  const int hi = dE >> 10;
+  if (hi >= nA) return false;
+  const uint32_t thr =
+      (uint32_t)(((unsigned long long)A[hi] * (unsigned long long)B[dE & (kNB - 1)]) >> 32);
+  return u < thr;
+}
+
+__device__ __forceinline__ int wrap_add(int x, int d, int n) {
+  int t = x + d;
+  t += (t < 0) ? n : 0;
+  t -= (t >= n) ? n : 0;
+  return t;
+}
+
+// One species id of site `gid` from the lattice store.
+__device__ __forceinline__ int load_site(const uint8_t* sites, long long gid, int storage) {
+  if (storage == SMCX_INT8) return sites[gid];
+  const uint8_t byte = sites[gid >> 1];
+  return (gid & 1) ? (byte >> 4) : (byte & 15);
+}
+
+// Launch parameters of the sweep kernels (passed by value: they live in the
+// kernel parameter bank, so concurrent launches never share them).
+struct SweepParams {
+  uint8_t* sites;
+  const uint32_t* thr;         // A[kNA] then B[kNB]
+  const int32_t* wtab;         // W[a][b][k][c] then X[a][b]
+  unsigned long long* stats;   // trials, accepts, same-species, sum of accepted dE
+  int n[3];
+  int nt[3];
+  int ntc[3];                  // tiles of this launch's colour on each axis
+  int tc;                      // tile colour (bit a = parity on axis a)
+  int L, h, ring;
+  int BX, BY, BZ;              // shared-memory box extents (cells)
+  int M, nA, storage, replica;
+  uint32_t seed_lo, seed_hi;
+  unsigned long long sweep;
+  int ic;                      // link-cell kernel: intra colour of the launch
+  int off[4][kMaxVec];         // box offsets of neighbours, per centre sublattice
+  int poff[4][kMaxZ1];         // box offset of the partner, per sublattice/direction
+  int psub[4][kMaxZ1];         // partner sublattice
+  signed char gd[4][kMaxVec][4];  // global (dx, dy, dz, b') of neighbours
+  signed char gp[4][kMaxZ1][4];   // global (dx, dy, dz, b') of partners
+};
+
+}  // namespace smcx

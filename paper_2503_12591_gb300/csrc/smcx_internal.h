@@ -1,0 +1,116 @@
+// Internal declarations of the smcx library (CUDA sm_103a).
+//
+// Geometry, schedule, acceptance tables and the Philox generator are written
+// here for the GPU path; the CPU oracle under oracle/ carries its own
+// independent copies, so that a mistake in one is caught by the other.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/smcx.h"
+
+namespace smcx {
+
+constexpr int kBCC = SMCX_BCC;
+constexpr int kFCC = SMCX_FCC;
+constexpr int kMaxShells = 4;     // BCC 1..4, FCC 1..3
+constexpr int kMaxVec = 64;       // neighbour vectors of all shells in use
+constexpr int kMaxZ1 = 12;        // shell-1 size (BCC 8, FCC 12)
+constexpr int kMaxSweepM = 8;     // species supported by the sweep kernels
+constexpr double kBoltzmannMeV = 8.617333262e-2;  // k_B in meV/K (exact SI)
+
+// ---------------------------------------------------------------------------
+// Status plumbing: every C entry point catches and converts to an SMCX_E_*.
+// ---------------------------------------------------------------------------
+struct SmcxException {
+  int code;
+  std::string msg;
+};
+void set_error(const std::string& msg);
+const std::string& last_error();
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+
+// ---------------------------------------------------------------------------
+// Host geometry.
+// ---------------------------------------------------------------------------
+struct Shells {
+  int kind = 0;
+  int m = 0;          // sites per cubic cell
+  int K = 0;          // shells in use
+  int z[kMaxShells] = {0};
+  int nv = 0;         // total neighbour vectors
+  int v[kMaxVec][3];  // half-lattice-unit vectors, shell-major, lexicographic
+  int shell_of[kMaxVec];
+  int R1 = 0, RK = 0; // max |component| of shell-1 vectors and of shells 1..K
+};
+
+int sites_per_cell(int kind);
+void basis_of(int kind, int b, int out[3]);
+int basis_index(int kind, int rx, int ry, int rz);
+Shells make_shells(int kind, int K);
+// smallest link-cell edge and tile thickness for which the checkerboard
+// phases are independent (see smcx_sched)
+int min_link_cell(const Shells& s);
+int min_tile(const Shells& s);
+int halo_cells(const Shells& s);   // staging halo around a tile (cells)
+int ring_cells(const Shells& s);   // cells outside a tile a partner can reach
+
+// Validates a schedule; returns "" if valid, else a reason.
+std::string schedule_problem(const Shells& s, const int n[3], const smcx_sched& sc);
+smcx_sched choose_schedule(const Shells& s, const int n[3]);
+
+// Acceptance tables: A[kNA], B[kNB], nA.
+constexpr int kNA = SMCX_NA_MAX;
+constexpr int kNB = SMCX_NB;
+int threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
+
+// ---------------------------------------------------------------------------
+// Lattice handle.
+// ---------------------------------------------------------------------------
+}  // namespace smcx
+
+struct smcx_lattice {
+  int kind = 0, m = 0, M = 0, storage = 0;
+  int n[3] = {0, 0, 0};
+  int64_t N = 0;
+  smcx::Shells shells;  // shells of the EPI in use (K = 0 before set_epi)
+  bool have_epi = false;
+  std::vector<int32_t> V;
+  smcx_sched sched{0, {0, 0, 0}};
+  bool sched_auto = true;
+  cudaStream_t stream = nullptr;
+
+  uint8_t* d_sites = nullptr;
+  size_t site_bytes = 0;
+  unsigned long long* d_stats = nullptr;  // [4] trials, accepts, same, sum dE
+  unsigned long long* d_counts = nullptr; // [K*M*M] reduction output
+  long long* d_energy = nullptr;          // [1]
+  uint32_t* d_thr = nullptr;              // A[kNA] then B[kNB]
+  int32_t* d_wtab = nullptr;              // W[a][b][k][c], then X[a][b]
+  int* d_flag = nullptr;                  // device error flag
+  uint8_t* d_stage = nullptr;             // host<->device staging (int8 ids)
+  size_t stage_bytes = 0;
+
+  double thr_T = -1.0;
+  int thr_nA = 0;
+  uint64_t sweep_cum = 0;
+};
+
+namespace smcx {
+
+// Kernels' host launchers (implemented in the .cu files).
+void init_config_device(smcx_lattice* h, const double* comp, uint64_t seed);
+void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // sets d_flag
+void pack_from_int8(smcx_lattice* h, const int8_t* d_ids, int64_t first, int64_t count);
+void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count);
+void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
+void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
+void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
+void species_counts(int M, const double* comp, int64_t N, int64_t* counts);
+
+}  // namespace smcx

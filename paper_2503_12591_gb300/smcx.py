@@ -1,0 +1,217 @@
+"""Thin Python binding of the smcx C ABI (include/smcx.h).
+
+Argument marshalling only: every computation runs in the CUDA library
+``_build/libsmcx.so``.  There is no CPU fallback; if the library has not been
+built, loading fails with an error that says so.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsmcx.so")
+
+BCC, FCC = 0, 1
+INT8, PACKED4 = 0, 1
+NA_MAX, NB = 4096, 1024
+
+OK = 0
+E_INVALID_ARG, E_NO_EPI, E_SCHEDULE, E_CUDA, E_OOM, E_TIMEOUT, E_RANGE, E_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+
+
+class SmcxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"smcx error {code}: {msg}")
+        self.code = code
+
+
+class Sched(C.Structure):
+    _fields_ = [("L", C.c_int32), ("nt", C.c_int32 * 3)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every entry point returns an int status
+_SIGS = {
+    "smcx_last_error": (C.c_char_p, []),
+    "smcx_version": (C.c_int, []),
+    "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
+    "smcx_set_epi": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "smcx_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64]),
+    "smcx_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_pair_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_sro": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_set_config": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smcx_set_sweep_counter": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "smcx_device_buffer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smcx_synchronize": (C.c_int, [C.c_void_p]),
+    "smcx_lattice_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "smcx_threshold_tables": (C.c_int, [C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def lib():
+    """Load libsmcx.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != OK:
+        raise SmcxError(rc, lib().smcx_last_error().decode())
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def threshold_tables(T):
+    A = np.zeros(NA_MAX, np.uint32)
+    B = np.zeros(NB, np.uint32)
+    nA = np.zeros(1, np.int32)
+    _check(lib().smcx_threshold_tables(float(T), _p(A), _p(nA), _p(B)))
+    return A, int(nA[0]), B
+
+
+class Lattice:
+    """A lattice handle (smcx_lattice)."""
+
+    def __init__(self, kind, dims, M, comp, init_seed=1, storage=INT8, sched=None, stream=None):
+        self.kind, self.dims, self.M, self.storage = kind, tuple(int(d) for d in dims), int(M), storage
+        self.m = 2 if kind == BCC else 4
+        self.N = self.dims[0] * self.dims[1] * self.dims[2] * self.m
+        self.K = 0
+        h = C.c_void_p()
+        c = np.ascontiguousarray(comp, np.float64)
+        sp = None
+        if sched is not None:
+            s = Sched(int(sched[0]), (C.c_int32 * 3)(*[int(t) for t in sched[1]]))
+            sp = C.byref(s)
+        _check(lib().smcx_lattice_create(C.byref(h), kind, *self.dims, self.M, _p(c), int(init_seed), storage,
+                                         sp, _stream_ptr(stream)))
+        self._h = h
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().smcx_lattice_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- model and schedule ---------------------------------------------
+    def set_epi(self, V):
+        V = np.ascontiguousarray(V, np.int32)
+        K = V.shape[0]
+        assert V.shape == (K, self.M, self.M)
+        _check(lib().smcx_set_epi(self._h, K, _p(V)))
+        self.K = K
+
+    def set_schedule(self, sched):
+        if sched is None:
+            _check(lib().smcx_set_schedule(self._h, None))
+        else:
+            s = Sched(int(sched[0]), (C.c_int32 * 3)(*[int(t) for t in sched[1]]))
+            _check(lib().smcx_set_schedule(self._h, C.byref(s)))
+
+    def schedule(self):
+        s = Sched()
+        _check(lib().smcx_get_schedule(self._h, C.byref(s)))
+        return int(s.L), tuple(int(t) for t in s.nt)
+
+    # -- compute ----------------------------------------------------------
+    def sweep(self, T, n_sweeps, seed):
+        _check(lib().smcx_sweep(self._h, float(T), int(n_sweeps), int(seed)))
+
+    def energy(self):
+        e = np.zeros(1, np.int64)
+        _check(lib().smcx_energy(self._h, _p(e)))
+        return int(e[0])
+
+    def pair_counts(self):
+        out = np.zeros((self.K, self.M, self.M), np.int64)
+        _check(lib().smcx_pair_counts(self._h, _p(out)))
+        return out
+
+    def sro(self):
+        out = np.zeros((self.K, self.M, self.M), np.float64)
+        _check(lib().smcx_sro(self._h, _p(out)))
+        return out
+
+    # -- configuration and state -----------------------------------------
+    def get_config(self, out=None):
+        if out is None:
+            out = np.empty(self.N, np.int8)
+        assert out.dtype == np.int8 and out.size == self.N and out.flags.c_contiguous
+        _check(lib().smcx_get_config(self._h, _p(out)))
+        return out
+
+    def set_config(self, cfg):
+        cfg = np.ascontiguousarray(cfg, np.int8)
+        assert cfg.size == self.N
+        _check(lib().smcx_set_config(self._h, _p(cfg)))
+
+    def get_config_ptr(self, host_ptr):
+        _check(lib().smcx_get_config(self._h, C.c_void_p(host_ptr)))
+
+    def set_config_ptr(self, host_ptr):
+        _check(lib().smcx_set_config(self._h, C.c_void_p(host_ptr)))
+
+    def state(self):
+        sw = np.zeros(1, np.uint64)
+        st = np.zeros(4, np.int64)
+        _check(lib().smcx_get_state(self._h, _p(sw), _p(st)))
+        return int(sw[0]), st
+
+    def set_sweep_counter(self, n):
+        _check(lib().smcx_set_sweep_counter(self._h, int(n)))
+
+    def device_buffer(self):
+        p = C.c_void_p()
+        n = C.c_size_t()
+        _check(lib().smcx_device_buffer(self._h, C.byref(p), C.byref(n)))
+        return int(p.value or 0), int(n.value)
+
+    def synchronize(self):
+        _check(lib().smcx_synchronize(self._h))

@@ -1,0 +1,169 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Integer results (configurations, trial statistics, energies, pair counts) must
+match bit for bit; the Warren-Cowley SRO (FP64 from integer counts) within
+1e-12 relative.  Cases span several tiles, uneven tile sizes (ragged tails),
+both storages, both lattices, the paper's link-cell schedule and the tiled
+schedule.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_12591_gb300 import smcx
+from paper_2503_12591_gb300.inputs import epi_gaussian, ORACLE_BCC16
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def stream():
+    assert torch.cuda.is_available()
+    return torch.cuda.current_stream()
+
+
+def _oracle_run(kind, dims, M, K, V, comp, init_seed, T, n, seed, sched):
+    ref = O.init_config(kind, dims, M, comp, init_seed)
+    st = O.sweep(kind, dims, M, K, V, ref, T, n, seed, L=sched[0], nt=sched[1])
+    return ref, st
+
+
+@pytest.mark.parametrize("kind,dims,M,comp,storage", [
+    (smcx.BCC, (6, 7, 5), 4, [0.25] * 4, smcx.INT8),
+    (smcx.BCC, (9, 4, 6), 4, [0.25] * 4, smcx.PACKED4),
+    (smcx.FCC, (5, 6, 7), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4),
+    (smcx.FCC, (4, 4, 4), 3, [0.5, 0.3, 0.2], smcx.INT8),
+])
+def test_initial_configuration(stream, kind, dims, M, comp, storage):
+    lat = smcx.Lattice(kind, dims, M, comp, init_seed=77, storage=storage, stream=stream)
+    got = lat.get_config()
+    ref = O.init_config(kind, dims, M, comp, 77)
+    assert (got == ref).all()
+
+
+@pytest.mark.parametrize("kind,K,dims,M,storage", [
+    (smcx.BCC, 4, (8, 6, 10), 4, smcx.INT8),
+    (smcx.BCC, 2, (6, 6, 6), 3, smcx.PACKED4),
+    (smcx.FCC, 3, (6, 8, 6), 5, smcx.PACKED4),
+])
+def test_energy_pair_counts_sro(stream, kind, K, dims, M, storage):
+    N = O.n_sites(kind, dims)
+    cfg = np.random.default_rng(5).integers(0, M, N).astype(np.int8)
+    V = epi_gaussian(K, M, 20.0, 3)
+    lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, storage=storage, stream=stream)
+    lat.set_epi(V)
+    lat.set_config(cfg)
+    assert (lat.get_config() == cfg).all()
+    C = lat.pair_counts()
+    assert (C == O.pair_counts(kind, dims, M, K, cfg)).all()
+    assert lat.energy() == O.energy(kind, dims, M, K, V, cfg)
+    np.testing.assert_allclose(lat.sro(), O.sro(kind, dims, M, K, cfg), rtol=1e-12, atol=1e-15)
+
+
+SWEEP_CASES = [
+    # kind, K, dims, M, comp, storage, schedule (L, nt), T, sweeps
+    (smcx.BCC, 4, (16, 16, 16), 4, [0.25] * 4, smcx.INT8, (3, (4, 4, 4)), 1000.0, 10),
+    (smcx.BCC, 4, (16, 16, 16), 4, [0.25] * 4, smcx.PACKED4, (4, (2, 2, 2)), 1000.0, 10),
+    (smcx.BCC, 4, (13, 14, 15), 4, [0.25] * 4, smcx.PACKED4, (3, (4, 2, 4)), 1500.0, 6),   # ragged tiles
+    (smcx.BCC, 4, (12, 12, 12), 4, [0.25] * 4, smcx.INT8, (3, (1, 1, 1)), 800.0, 6),       # link-cell
+    (smcx.BCC, 4, (12, 12, 16), 4, [0.25] * 4, smcx.PACKED4, (4, (1, 1, 1)), 2500.0, 4),   # link-cell
+    (smcx.BCC, 2, (12, 10, 8), 3, [0.5, 0.3, 0.2], smcx.INT8, (3, (2, 2, 2)), 1200.0, 5),
+    (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 5),
+    (smcx.FCC, 3, (9, 10, 11), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.INT8, (3, (2, 4, 2)), 1200.0, 4),
+    (smcx.FCC, 3, (9, 9, 9), 4, [0.25] * 4, smcx.PACKED4, (3, (1, 1, 1)), 1000.0, 4),      # link-cell
+]
+
+
+@pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: f"{'bcc' if c[0]==0 else 'fcc'}{c[2]}K{c[1]}L{c[6][0]}nt{c[6][1]}s{c[5]}")
+def test_sweep_bit_exact(stream, case):
+    kind, K, dims, M, comp, storage, sched, T, n = case
+    V = epi_gaussian(K, M, 20.0, 11)
+    lat = smcx.Lattice(kind, dims, M, comp, init_seed=3, storage=storage, sched=sched, stream=stream)
+    lat.set_epi(V)
+    assert lat.schedule() == (sched[0], tuple(sched[1]))
+    lat.sweep(T, n, 9)
+    got = lat.get_config()
+    sw, st = lat.state()
+    ref, rst = _oracle_run(kind, dims, M, K, V, comp, 3, T, n, 9, sched)
+    assert sw == n
+    assert (got == ref).all(), f"{(got != ref).sum()} sites differ"
+    assert st.tolist() == rst.tolist()
+    assert lat.energy() == O.energy(kind, dims, M, K, V, ref)
+
+
+def test_oracle_sized_workload(stream):
+    """BCC 16^3 quaternary, 4 shells, 1000 K, 100 sweeps, seed 1 (the
+    oracle-sized workload), library-chosen schedule."""
+    w = ORACLE_BCC16
+    V = w.epi()
+    lat = smcx.Lattice(w.kind, w.dims, w.M, w.comp, init_seed=w.init_seed, storage=w.storage, stream=stream)
+    lat.set_epi(V)
+    L, nt = lat.schedule()
+    lat.sweep(w.temperatures[0], w.sweeps, w.seed)
+    got = lat.get_config()
+    ref, rst = _oracle_run(w.kind, w.dims, w.M, w.K, V, w.comp, w.init_seed, w.temperatures[0], w.sweeps,
+                           w.seed, (L, nt))
+    assert (got == ref).all()
+    assert lat.state()[1].tolist() == rst.tolist()
+    assert lat.energy() == O.energy(w.kind, w.dims, w.M, w.K, V, ref)
+
+
+def test_split_sweeps_and_resume(stream):
+    dims, M, K = (12, 12, 12), 4, 4
+    V = epi_gaussian(K, M, 20.0, 2)
+    a = smcx.Lattice(smcx.BCC, dims, M, [0.25] * 4, storage=smcx.PACKED4, sched=(3, (2, 2, 2)), stream=stream)
+    a.set_epi(V)
+    a.sweep(1200.0, 3, 5)
+    mid = a.get_config()
+    a.sweep(1200.0, 4, 5)
+    b = smcx.Lattice(smcx.BCC, dims, M, [0.25] * 4, storage=smcx.PACKED4, sched=(3, (2, 2, 2)), stream=stream)
+    b.set_epi(V)
+    b.sweep(1200.0, 7, 5)
+    assert (a.get_config() == b.get_config()).all()
+    # checkpoint / resume: configuration + cumulative sweep counter
+    c = smcx.Lattice(smcx.BCC, dims, M, [0.25] * 4, storage=smcx.INT8, sched=(3, (2, 2, 2)), stream=stream)
+    c.set_epi(V)
+    c.set_config(mid)
+    c.set_sweep_counter(3)
+    c.sweep(1200.0, 4, 5)
+    assert (c.get_config() == b.get_config()).all()
+
+
+def test_error_codes(stream):
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice(smcx.BCC, (12, 12, 12), 4, [0.25] * 4, sched=(2, (1, 1, 1)), stream=stream)
+    assert e.value.code == smcx.E_SCHEDULE
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice(smcx.BCC, (12, 12, 12), 4, [0.25] * 4, sched=(3, (3, 2, 2)), stream=stream)
+    assert e.value.code == smcx.E_SCHEDULE
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice(smcx.BCC, (12, 12, 12), 4, [0.5, 0.6, 0.0, 0.0], stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice(smcx.BCC, (12, 12, 12), 16, [1 / 16] * 16, storage=smcx.PACKED4, stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG
+    lat = smcx.Lattice(smcx.BCC, (12, 12, 12), 4, [0.25] * 4, stream=stream)
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.sweep(1000.0, 1, 1)
+    assert e.value.code == smcx.E_NO_EPI
+    V = epi_gaussian(4, 4, 20.0, 1)
+    bad = V.copy()
+    bad[0, 0, 1] += 1
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_epi(bad)
+    assert e.value.code == smcx.E_INVALID_ARG
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_epi(V * 100000)
+    assert e.value.code == smcx.E_RANGE
+    lat.set_epi(V)
+    for T in (0.0, -5.0, float("nan")):
+        with pytest.raises(smcx.SmcxError) as e:
+            lat.sweep(T, 1, 1)
+        assert e.value.code == smcx.E_INVALID_ARG
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_config(np.full(lat.N, 7, np.int8))
+    assert e.value.code == smcx.E_INVALID_ARG
+    lat.sweep(1000.0, 0, 1)  # zero sweeps is a no-op
+    assert lat.state()[0] == 0
