@@ -1,0 +1,327 @@
+"""Benchmark: swap attempts per second of the checkerboard Metropolis sweep.
+
+Workload (N=1): BCC 800^3 cubic cells = 1,024,000,000 sites, 4 species at
+equiatomic composition, packed 4-bit storage, 4-shell EPI drawn from
+N(0, 20 meV), 1200 K.  A step is one sweep (one swap trial per site).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is device-timed throughput with the lattice
+resident in HBM; `e2e` repeats the measurement through the C ABI with the
+configuration uploaded from pinned host memory every step and the energy read
+back; `roofline` covers the sweep kernel; `cpu_baseline` times the serial CPU
+oracle on a bounded sample of the same workload.  Under torchrun each rank
+sweeps its own independent replica (weak scaling, no collective on the data
+path).  `--impl reference` times the oracle alone (the reference arm).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_12591_gb300.inputs import SCALE_BCC800, epi_gaussian, equiatomic  # noqa: E402
+
+METRIC = "swap attempts/s at 1.02B-site BCC (HBM roofline %); batched & gradient vs plain"
+UNIT = "attempts/s"
+WORK = SCALE_BCC800
+T_KELVIN = WORK.temperatures[0]
+SEED = 1
+# Bytes of the lattice store a sweep must read and write per site (packed
+# 4-bit: half a byte in, half a byte out).
+ALG_BYTES_PER_ATTEMPT = 1.0
+# Shared-memory lane loads per trial the method cannot avoid: the species of
+# s and s' plus the 68 distinct sites of their 4-shell BCC environments.
+ALG_GATHERS_PER_ATTEMPT = 70
+SM_COUNT_NOMINAL = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+# CPU sample: same lattice kind, species, shells, temperature and schedule
+# shape on a smaller box.
+CPU_SAMPLE_DIMS = (64, 64, 64)
+CPU_SAMPLE_SCHED = (3, (4, 4, 4))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="smcx", choices=["smcx", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--dims", type=int, default=0,
+                    help="profiling only: cubic BCC edge other than the 800 of the workload")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n_sweeps=12):
+    """The oracle as it stands, single-threaded, on a BCC 64^3 sample."""
+    import oracle as O
+
+    V = epi_gaussian(WORK.K, WORK.M, WORK.sigma_mev, WORK.epi_seed)
+    sig = O.init_config(O.BCC, CPU_SAMPLE_DIMS, WORK.M, equiatomic(WORK.M), WORK.init_seed)
+    t0 = time.perf_counter()
+    O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_sweeps, SEED,
+            L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+    dt = time.perf_counter() - t0
+    n = sig.size * n_sweeps
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"serial C oracle, BCC {CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites), 4 species, "
+                      f"4 shells, {T_KELVIN:.0f} K, schedule L={CPU_SAMPLE_SCHED[0]} "
+                      f"tiles {CPU_SAMPLE_SCHED[1]}, {n_sweeps} sweeps = {n} trials in {dt:.1f} s"}
+
+
+def config_block(extra=None):
+    c = {"workload": f"BCC {WORK.dims[0]}^3 cells x 2 = {WORK.sites:,} sites, 4 species equiatomic, "
+                     f"packed 4-bit, 4-shell int32 EPI N(0,{WORK.sigma_mev:.0f} meV), {T_KELVIN:.0f} K",
+         "sites": WORK.sites, "lattice": "bcc", "dims": list(WORK.dims), "species": WORK.M, "shells": WORK.K,
+         "storage": "packed4", "temperature_K": T_KELVIN, "step": "one sweep (one swap trial per site)",
+         "l2": "inputs larger than L2 (512 MB lattice store vs 129 MB L2)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the serial CPU oracle, each step one sweep of a BCC
+    64^3 sample of the workload."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    V = epi_gaussian(WORK.K, WORK.M, WORK.sigma_mev, WORK.epi_seed)
+    sig = O.init_config(O.BCC, CPU_SAMPLE_DIMS, WORK.M, equiatomic(WORK.M), WORK.init_seed)
+    sw = 0
+    for _ in range(args.warmup):
+        O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
+                L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+        sw += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
+                L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+        sw += 1
+    dt = time.perf_counter() - t0
+    val = sig.size * args.steps / dt
+    sample = (f"serial C oracle, one sweep of BCC {CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites) per step, "
+              f"same species/shells/temperature/schedule shape")
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": config_block({"sample": sample}), "impl": "reference",
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_smcx(args, rank, world, local_rank):
+    import torch
+
+    from paper_2503_12591_gb300 import smcx
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    V = WORK.epi()
+    with torch.cuda.stream(stream):
+        lat = smcx.Lattice(smcx.BCC, WORK.dims, WORK.M, WORK.comp, init_seed=WORK.init_seed + rank,
+                           storage=smcx.PACKED4, stream=stream)
+        lat.set_epi(V)
+    sched = lat.schedule()
+    # replicas on different ranks differ by their initial configuration
+    for _ in range(args.warmup):
+        lat.sweep(T_KELVIN, 1, SEED)
+    lat.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lat.sweep(T_KELVIN, 1, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    launches_per_sweep = 8 if sched[1] != (1, 1, 1) else sched[0] ** 3 * 2
+    n_launch = launches_per_sweep * args.steps
+    value = WORK.sites * args.steps * world / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(WORK.sites, dtype=torch.int8, pin_memory=True)
+        lat.get_config_ptr(host.data_ptr())
+        for _ in range(2):
+            lat.set_config_ptr(host.data_ptr())
+            lat.sweep(T_KELVIN, 1, SEED)
+            lat.energy()
+        barrier()
+        ne = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            lat.set_config_ptr(host.data_ptr())   # H2D of the step's input configuration
+            lat.sweep(T_KELVIN, 1, SEED)
+            lat.energy()                          # D2H of the step's result
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": WORK.sites,
+               "d2h_bytes_per_step": 8, "steps": ne,
+               "step": "smcx_set_config (int8 ids, pinned host) + smcx_sweep (1 sweep) + smcx_energy"}
+        del host
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    hbm_peak, peak_kind = peaks()
+    per_launch_ms = ms_max / n_launch
+    bytes_per_launch = ALG_BYTES_PER_ATTEMPT * WORK.sites / launches_per_sweep
+    achieved_gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    gathers_per_launch = ALG_GATHERS_PER_ATTEMPT * WORK.sites / launches_per_sweep
+    lds_peak = SM_COUNT_NOMINAL * 32 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e9  # G lane-loads/s
+    achieved_g = gathers_per_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": config_block({"schedule": {"L": sched[0], "tiles": list(sched[1])},
+                                "parallelism": f"replicas x{world}" if world > 1 else "single lattice"}),
+        "roofline": {"bound": "alu", "achieved": achieved_g, "peak": lds_peak, "unit": "Gload/s",
+                     "frac": achieved_g / lds_peak, "traffic": traffic,
+                     "kernel": "k_tile_sweep",
+                     "note": "shared-memory gather roof: 70 lane-loads per trial (s, s' and 68 distinct "
+                             "neighbours) against 152 SMs x 32 lanes x 2070 MHz"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
+                         "note": "1 B per trial (packed 4-bit read + write) per launch / launch time"},
+        "gpu_launches": n_launch,
+        "clocks": clk,
+    }
+    if e2e is not None:
+        out["e2e"] = e2e
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    global WORK
+    args = parse()
+    if args.dims:
+        import dataclasses
+        WORK = dataclasses.replace(WORK, name=f"bcc{args.dims}_q4_k4_packed4", dims=(args.dims,) * 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.impl == "reference" else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if "WORLD_SIZE" not in os.environ:
+        world = 1
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_smcx(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,15 @@ int smcx_lattice_destroy(smcx_lattice* h);
  */
 int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V);
 
+/* Kernel family used by smcx_sweep.  SMCX_KERNEL_AUTO (default) picks the
+ * fastest kernel that supports the lattice (the shared-memory BCC kernel for
+ * BCC with M <= 8 and tiles <= 20 cells); SMCX_KERNEL_GENERIC forces the
+ * generic tiled kernel (or the link-cell kernel for the paper's schedule).
+ * Both give bit-identical trajectories. */
+#define SMCX_KERNEL_AUTO 0
+#define SMCX_KERNEL_GENERIC 1
+int smcx_set_kernel(smcx_lattice* h, int which);
+
 /* Replace the schedule (NULL = library's choice).  The trajectory depends on
  * it: equal schedules give bit-identical results. */
 int smcx_set_schedule(smcx_lattice* h, const smcx_sched* sched);

@@ -218,6 +218,14 @@ int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V) {
   });
 }
 
+int smcx_set_kernel(smcx_lattice* h, int which) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(which == SMCX_KERNEL_AUTO || which == SMCX_KERNEL_GENERIC, SMCX_E_INVALID_ARG, "unknown kernel family");
+    h->kernel_choice = which;
+  });
+}
+
 int smcx_set_schedule(smcx_lattice* h, const smcx_sched* sched) {
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");

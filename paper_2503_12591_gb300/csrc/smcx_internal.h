@@ -96,6 +96,7 @@ struct smcx_lattice {
   uint8_t* d_stage = nullptr;             // host<->device staging (int8 ids)
   size_t stage_bytes = 0;
 
+  int kernel_choice = 0;  // 0 = fastest usable, 1 = generic tile/link-cell kernels
   double thr_T = -1.0;
   int thr_nA = 0;
   uint64_t sweep_cum = 0;
@@ -111,6 +112,8 @@ void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count
 void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
 void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
 void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
+bool bcc_fast_usable(const smcx_lattice* h);
+void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
 void species_counts(int M, const double* comp, int64_t N, int64_t* counts);
 
 }  // namespace smcx

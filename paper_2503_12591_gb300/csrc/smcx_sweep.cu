@@ -345,6 +345,10 @@ static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps) {
 }
 
 void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
+  if (hd->kernel_choice != 1 && bcc_fast_usable(hd)) {
+    sweep_bcc_fast(hd, nA, seed, n_sweeps);
+    return;
+  }
   SweepParams P;
   memset(&P, 0, sizeof(P));
   const smcx_sched& sc = hd->sched;

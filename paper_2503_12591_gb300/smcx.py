@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsmcx.so")
 
 BCC, FCC = 0, 1
 INT8, PACKED4 = 0, 1
+KERNEL_AUTO, KERNEL_GENERIC = 0, 1
 NA_MAX, NB = 4096, 1024
 
 OK = 0
@@ -41,6 +42,7 @@ _SIGS = {
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
     "smcx_set_epi": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "smcx_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
     "smcx_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64]),
@@ -147,6 +149,9 @@ class Lattice:
         assert V.shape == (K, self.M, self.M)
         _check(lib().smcx_set_epi(self._h, K, _p(V)))
         self.K = K
+
+    def set_kernel(self, which):
+        _check(lib().smcx_set_kernel(self._h, int(which)))
 
     def set_schedule(self, sched):
         if sched is None:

@@ -70,17 +70,23 @@ SWEEP_CASES = [
     (smcx.BCC, 4, (12, 12, 12), 4, [0.25] * 4, smcx.INT8, (3, (1, 1, 1)), 800.0, 6),       # link-cell
     (smcx.BCC, 4, (12, 12, 16), 4, [0.25] * 4, smcx.PACKED4, (4, (1, 1, 1)), 2500.0, 4),   # link-cell
     (smcx.BCC, 2, (12, 10, 8), 3, [0.5, 0.3, 0.2], smcx.INT8, (3, (2, 2, 2)), 1200.0, 5),
+    (smcx.BCC, 1, (10, 12, 8), 2, [0.5, 0.5], smcx.PACKED4, (3, (2, 2, 2)), 600.0, 5),
+    (smcx.BCC, 3, (24, 20, 22), 6, [1 / 6] * 6, smcx.PACKED4, (4, (2, 2, 2)), 1500.0, 3),
+    (smcx.BCC, 4, (40, 24, 26), 8, [0.125] * 8, smcx.INT8, (3, (2, 2, 2)), 2000.0, 2),
+    (smcx.BCC, 4, (42, 40, 38), 4, [0.25] * 4, smcx.PACKED4, (4, (4, 2, 2)), 1000.0, 2),
     (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 5),
     (smcx.FCC, 3, (9, 10, 11), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.INT8, (3, (2, 4, 2)), 1200.0, 4),
     (smcx.FCC, 3, (9, 9, 9), 4, [0.25] * 4, smcx.PACKED4, (3, (1, 1, 1)), 1000.0, 4),      # link-cell
 ]
 
 
+@pytest.mark.parametrize("kernel", [smcx.KERNEL_AUTO, smcx.KERNEL_GENERIC], ids=["auto", "generic"])
 @pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: f"{'bcc' if c[0]==0 else 'fcc'}{c[2]}K{c[1]}L{c[6][0]}nt{c[6][1]}s{c[5]}")
-def test_sweep_bit_exact(stream, case):
+def test_sweep_bit_exact(stream, case, kernel):
     kind, K, dims, M, comp, storage, sched, T, n = case
     V = epi_gaussian(K, M, 20.0, 11)
     lat = smcx.Lattice(kind, dims, M, comp, init_seed=3, storage=storage, sched=sched, stream=stream)
+    lat.set_kernel(kernel)
     lat.set_epi(V)
     assert lat.schedule() == (sched[0], tuple(sched[1]))
     lat.sweep(T, n, 9)
@@ -167,3 +173,19 @@ def test_error_codes(stream):
     assert e.value.code == smcx.E_INVALID_ARG
     lat.sweep(1000.0, 0, 1)  # zero sweeps is a no-op
     assert lat.state()[0] == 0
+
+
+@pytest.mark.parametrize("sigma_mev", [0.4, 20.0, 500.0], ids=["1plane", "2planes", "3planes"])
+def test_epi_scale_byte_planes(stream, sigma_mev):
+    """The shared-memory BCC kernel splits V into 1, 2 or 3 byte planes by its
+    largest entry; every split must give the oracle's trajectory."""
+    dims, M, K, sched = (20, 18, 16), 4, 4, (3, (2, 2, 2))
+    V = epi_gaussian(K, M, sigma_mev, 21)
+    T = 3000.0 if sigma_mev > 100 else 900.0
+    lat = smcx.Lattice(smcx.BCC, dims, M, [0.25] * 4, init_seed=4, storage=smcx.PACKED4, sched=sched,
+                       stream=stream)
+    lat.set_epi(V)
+    lat.sweep(T, 3, 2)
+    ref, rst = _oracle_run(smcx.BCC, dims, M, K, V, [0.25] * 4, 4, T, 3, 2, sched)
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[1].tolist() == rst.tolist()
