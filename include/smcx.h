@@ -215,6 +215,31 @@ int smcx_lattice_info(const smcx_lattice* h, int* kind, int* dims /*[3]*/, int* 
  */
 int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
 
+/*
+ * Energy of a device-resident configuration without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc -- code that runs inside another framework's memory
+ * arena, latency-critical loops that must not wait on the allocator, or
+ * callers holding only a device pointer to a configuration (for instance from
+ * smcx_device_buffer) and no handle.
+ *   kind, nx, ny, nz, M, storage  describe d_sites exactly as for
+ *                                 smcx_lattice_create (canonical site order);
+ *   K, V                          EPI table V[K][M][M] on the host (symmetric);
+ *   d_sites                       device pointer to the species ids, read only;
+ *   E                             host output, exact energy in 0.01 meV;
+ *   stream                        cudaStream_t ordering the work (NULL = default).
+ * The histogram, the EPI table and the result live in one fixed device array
+ * of 16 KiB inside the library (held by every GPU that loads it until the
+ * process exits): K*M*M must not exceed 1300, otherwise SMCX_E_INVALID_ARG.
+ * The first call on a device looks up that array's address with the device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: it is cleared at the start of each call, and calls whose GPU work
+ * overlaps (several streams or host threads) race and return wrong energies.
+ * Synchronises `stream` before returning.
+ */
+int smcx_energy_noalloc(int kind, int nx, int ny, int nz, int M, int storage, int K, const int32_t* V,
+                        const void* d_sites, int64_t* E, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

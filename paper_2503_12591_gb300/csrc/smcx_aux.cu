@@ -116,6 +116,36 @@ void energy_device(smcx_lattice* hd) {
   check_cuda(cudaGetLastError(), "energy launch");
 }
 
+// Launchers on caller-provided buffers (used by the non-allocating entry point).
+void pair_counts_raw(int kind, int K, const SweepParams& P, long long ncell, int KMM, unsigned long long* counts,
+                     cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  const int grid = (int)std::min<long long>((ncell + 255) / 256, (long long)nsm * 8);
+  const size_t sm = (size_t)KMM * sizeof(unsigned int);
+  if (kind == kBCC) {
+    switch (K) {
+      case 1: k_pair_counts<kBCC, 1><<<grid, 256, sm, st>>>(P, counts); break;
+      case 2: k_pair_counts<kBCC, 2><<<grid, 256, sm, st>>>(P, counts); break;
+      case 3: k_pair_counts<kBCC, 3><<<grid, 256, sm, st>>>(P, counts); break;
+      default: k_pair_counts<kBCC, 4><<<grid, 256, sm, st>>>(P, counts); break;
+    }
+  } else {
+    switch (K) {
+      case 1: k_pair_counts<kFCC, 1><<<grid, 256, sm, st>>>(P, counts); break;
+      case 2: k_pair_counts<kFCC, 2><<<grid, 256, sm, st>>>(P, counts); break;
+      default: k_pair_counts<kFCC, 3><<<grid, 256, sm, st>>>(P, counts); break;
+    }
+  }
+  check_cuda(cudaGetLastError(), "pair-count launch");
+}
+
+void energy_raw(const unsigned long long* C, const int32_t* V, int KMM, long long* E, cudaStream_t st) {
+  k_energy<<<1, 256, 0, st>>>(C, V, KMM, E);
+  check_cuda(cudaGetLastError(), "energy launch");
+}
+
 // ---------------------------------------------------------------------------
 // Initial configuration.
 // ---------------------------------------------------------------------------

@@ -116,4 +116,9 @@ bool bcc_fast_usable(const smcx_lattice* h);
 void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
 void species_counts(int M, const double* comp, int64_t N, int64_t* counts);
 
+struct SweepParams;
+void pair_counts_raw(int kind, int K, const SweepParams& P, long long ncell, int KMM, unsigned long long* counts,
+                     cudaStream_t st);
+void energy_raw(const unsigned long long* C, const int32_t* V, int KMM, long long* E, cudaStream_t st);
+
 }  // namespace smcx

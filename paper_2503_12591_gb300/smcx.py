@@ -58,6 +58,8 @@ _SIGS = {
     "smcx_lattice_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "smcx_threshold_tables": (C.c_int, [C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smcx_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -104,6 +106,16 @@ def threshold_tables(T):
     nA = np.zeros(1, np.int32)
     _check(lib().smcx_threshold_tables(float(T), _p(A), _p(nA), _p(B)))
     return A, int(nA[0]), B
+
+
+def energy_noalloc(kind, dims, M, storage, V, d_sites, stream=None):
+    """Energy of the configuration at device pointer d_sites (see
+    smcx_energy_noalloc: no device allocation, one shared fixed scratch)."""
+    V = np.ascontiguousarray(V, np.int32)
+    e = np.zeros(1, np.int64)
+    _check(lib().smcx_energy_noalloc(int(kind), *[int(d) for d in dims], int(M), int(storage), int(V.shape[0]),
+                                     _p(V), C.c_void_p(int(d_sites)), _p(e), _stream_ptr(stream)))
+    return int(e[0])
 
 
 class Lattice:
