@@ -28,7 +28,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2503_12591_gb300.inputs import SCALE_BCC800, epi_gaussian, equiatomic  # noqa: E402
+from paper_2503_12591_gb300.inputs import (SCALE_BCC800, batched_edges, epi_gaussian, equiatomic,  # noqa: E402
+                                           log_temperatures)
 
 METRIC = "swap attempts/s at 1.02B-site BCC (HBM roofline %); batched & gradient vs plain"
 UNIT = "attempts/s"
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--impl", default="smcx", choices=["smcx", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -186,6 +188,71 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+BATCH_R, BATCH_SWEEPS = 64, 500
+
+
+def run_batched(stream):
+    """64 BCC replicas with cubic edges drawn from 24..96, temperatures
+    log-spaced 300-3000 K, shared 4-shell EPI: 500 sweeps in one persistent
+    launch (graph-replayed, autotuned schedules) against the same replicas
+    swept one per smcx_sweep call; both from the same start, compared bit for
+    bit at the end."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+
+    edges = batched_edges(BATCH_R, 24, 96, 1)
+    T = log_temperatures(BATCH_R, 300.0, 3000.0)
+    V = epi_gaussian(4, 4, 20.0, 1)
+
+    def make(r):
+        n = int(edges[r])
+        lat = smcx.Lattice(smcx.BCC, (n, n, n), 4, equiatomic(4), init_seed=1000 + r, storage=smcx.INT8,
+                           stream=stream)
+        lat.set_replica(r)
+        lat.set_epi(V)
+        return lat
+
+    lats = [make(r) for r in range(BATCH_R)]
+    sites = sum(l.N for l in lats)
+    b = smcx.Batch(lats, stream)
+    threads = b.autotune(T, trial_sweeps=2)
+    scheds = [l.schedule() for l in lats]
+    plain = [make(r) for r in range(BATCH_R)]
+    for p, sc in zip(plain, scheds):
+        p.set_schedule(sc)
+        p.set_block(threads)
+    b.sweep(T, 2, SEED)
+    for r, p in enumerate(plain):
+        p.sweep(T[r], 2, SEED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.sweep(T, BATCH_SWEEPS, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    info = b.info()
+    e0.record(stream)
+    for r, p in enumerate(plain):
+        p.sweep(T[r], BATCH_SWEEPS, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    exact = all((l.get_config() == p.get_config()).all() and
+                l.state()[1].tolist() == p.state()[1].tolist() for l, p in zip(lats, plain))
+    b.close()
+    for l in lats + plain:
+        l.close()
+    att = sites * BATCH_SWEEPS
+    return {"value": att / (ms_b / 1e3), "unit": UNIT, "plain_value": att / (ms_p / 1e3),
+            "speedup_vs_plain": ms_p / ms_b, "replicas": BATCH_R, "sites": sites, "sweeps": BATCH_SWEEPS,
+            "ms_batched": ms_b, "ms_plain": ms_p, "graph": info["graph"], "grid": info["grid"],
+            "threads": info["threads"], "bit_exact_vs_plain": bool(exact),
+            "plain": "64 handles, one smcx_sweep call each (8 tile-colour launches per sweep)",
+            "workload": "64 BCC cubic lattices, edges U{24..96} (seed 1), 4 species, shared 4-shell EPI, "
+                        "T log-spaced 300-3000 K, int8 storage"}
+
+
 def run_smcx(args, rank, world, local_rank):
     import torch
 
@@ -298,6 +365,8 @@ def run_smcx(args, rank, world, local_rank):
     }
     if e2e is not None:
         out["e2e"] = e2e
+    if not args.no_batched and world == 1:
+        out["batched"] = run_batched(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -159,6 +159,16 @@ int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V);
 #define SMCX_KERNEL_GENERIC 1
 int smcx_set_kernel(smcx_lattice* h, int which);
 
+/* Philox replica id of the handle (0..65535, default 0): counter word 1
+ * carries it in bits 16..31, so replicas with equal seeds draw independent
+ * streams.  A handle swept alone with replica id r follows exactly the
+ * trajectory it follows as replica r of a batch. */
+int smcx_set_replica(smcx_lattice* h, int replica);
+
+/* Threads per CTA of the BCC shared-memory kernel (0 = one thread per
+ * link-cell slot; else a multiple of 32 up to 512).  Performance only. */
+int smcx_set_block(smcx_lattice* h, int threads);
+
 /* Replace the schedule (NULL = library's choice).  The trajectory depends on
  * it: equal schedules give bit-identical results. */
 int smcx_set_schedule(smcx_lattice* h, const smcx_sched* sched);
@@ -214,6 +224,44 @@ int smcx_lattice_info(const smcx_lattice* h, int* kind, int* dims /*[3]*/, int* 
  * Needs no GPU.
  */
 int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
+
+/*
+ * Batched replicas (temperature parallelism, Supplementary "Parallelization
+ * opportunities"): independent BCC lattices of any sizes, each at its own
+ * temperature and with its own schedule, sweep counter and replica id, swept
+ * together in one persistent cooperative launch (captured in a CUDA graph and
+ * replayed on later calls with the same sweep count).  Every replica's
+ * trajectory equals the one smcx_sweep gives it alone.
+ *   smcx_batch_create   references R existing handles (not owned; they must
+ *                       outlive the batch), which must share M, the EPI table
+ *                       (4 shells, set with smcx_set_epi) and `stream`, and
+ *                       have schedules with tiles of at most 20 cells.
+ *   smcx_batch_sweep    n_sweeps at temperatures T[R] with Philox seed `seed`;
+ *                       returns after the launch has finished; SMCX_E_TIMEOUT
+ *                       if a grid barrier waited longer than its limit.
+ *   smcx_batch_autotune times `trial_sweeps` batched sweeps for every
+ *                       candidate (link cell 3 or 4, tiles of about 12/16/20
+ *                       cells, 3 block sizes) on snapshots of the
+ *                       configurations, restores them, and installs the
+ *                       fastest candidate's schedules (read them back with
+ *                       smcx_get_schedule) and block size (*threads).
+ *   smcx_batch_energy   E[R], one smcx_energy per replica.
+ *   smcx_batch_info     grid size, threads per CTA and whether the last call
+ *                       replayed a graph.
+ *   smcx_batch_set_fault test hook: CTA `skip_cta` (>= 0) skips the first grid
+ *                       barrier, which then times out after timeout_ms and the
+ *                       next smcx_batch_sweep returns SMCX_E_TIMEOUT; -1 turns
+ *                       it off.  timeout_ms (1..60000, default 2000) bounds
+ *                       every barrier wait.
+ */
+typedef struct smcx_batch smcx_batch;
+int smcx_batch_create(smcx_batch** out, int R, smcx_lattice* const* lattices, void* stream);
+int smcx_batch_destroy(smcx_batch* b);
+int smcx_batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed);
+int smcx_batch_autotune(smcx_batch* b, const double* T, int trial_sweeps, int* threads);
+int smcx_batch_energy(smcx_batch* b, int64_t* E);
+int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_graph);
+int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
 
 /*
  * Energy of a device-resident configuration without allocating device memory.

@@ -96,6 +96,10 @@ void upload_thresholds(smcx_lattice* h, double T) {
 
 }  // namespace
 
+namespace smcx {
+void upload_thresholds_for(smcx_lattice* h, double T) { upload_thresholds(h, T); }
+}  // namespace smcx
+
 extern "C" {
 
 const char* smcx_last_error(void) { return last_error().c_str(); }
@@ -223,6 +227,23 @@ int smcx_set_kernel(smcx_lattice* h, int which) {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
     need(which == SMCX_KERNEL_AUTO || which == SMCX_KERNEL_GENERIC, SMCX_E_INVALID_ARG, "unknown kernel family");
     h->kernel_choice = which;
+  });
+}
+
+int smcx_set_replica(smcx_lattice* h, int replica) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(replica >= 0 && replica < 65536, SMCX_E_INVALID_ARG, "replica id must be in 0..65535");
+    h->replica = replica;
+  });
+}
+
+int smcx_set_block(smcx_lattice* h, int threads) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(threads == 0 || (threads >= 32 && threads <= 512 && threads % 32 == 0), SMCX_E_INVALID_ARG,
+         "threads must be 0 or a multiple of 32 in 32..512");
+    h->bcc_threads = threads;
   });
 }
 

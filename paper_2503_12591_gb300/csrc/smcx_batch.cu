@@ -1,0 +1,492 @@
+// Batched replicas: many independent BCC lattices (uneven sizes, one
+// temperature each, shared EPI) swept in ONE persistent cooperative launch.
+//
+// Temperature parallelism is one of the paper's parallel opportunities
+// (Supplementary "Parallelization opportunities": simulations at different
+// temperatures are independent); the paper runs them on separate GPUs, here
+// they share one GPU and one launch.  Every replica keeps its own schedule,
+// sweep counter and Philox replica id, so its trajectory is bit-identical to
+// sweeping it alone through smcx_sweep.
+//
+// The kernel loops over sweeps and tile colours; in each colour the CTAs take
+// the pooled list of (replica, tile) work items of that colour, then meet at
+// a grid barrier.  The barrier waits at most `timeout_ns`: a CTA that gives
+// up writes SMCX_E_TIMEOUT into a device status word and returns, and so does
+// every other CTA once it sees the status, so the context stays usable.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "smcx_bcc_tile.cuh"
+
+struct smcx_batch {
+  std::vector<smcx_lattice*> lat;
+  cudaStream_t stream = nullptr;
+  smcx::bccfast::LatDesc* d_desc = nullptr;
+  int2* d_items = nullptr;  // (replica, tile index within its colour)
+  int n_items = 0;
+  unsigned* d_bar = nullptr;
+  int* d_status = nullptr;
+  int threads = 0, slots = 1;
+  long long timeout_ns = 2000000000ll;
+  int skip_cta = -1;  // fault injection: this CTA never arrives at the barrier
+  bool use_graph = true;
+  std::map<long long, cudaGraphExec_t> graphs;  // keyed by (sweeps, table size)
+  std::vector<int32_t> graph_V;                 // EPI baked into the graphs
+  bool items_dirty = true;
+  int last_grid = 0;
+  bool last_graph = false;
+};
+
+namespace smcx {
+
+int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
+
+namespace bccfast {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier with a time limit; returns false if the grid must stop.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* status, long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+      const unsigned v = *((volatile unsigned*)bar);
+      if (v >= target) break;
+      if (*((volatile int*)status) != 0) {
+        ok = 0;
+        break;
+      }
+      if ((long long)(global_ns() - t0) > timeout_ns) {
+        atomicCAS(status, 0, SMCX_E_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int K, int NW, int PL, int SLOTS>
+__global__ void __launch_bounds__(512, 2)
+    k_bcc_batch(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
+                int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_stat[3];
+  uint8_t* box = smem;
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
+  uint32_t* sB = sA + max_nA;
+  unsigned epoch = 0;
+  for (int s = 0; s < n_sweeps; s++)
+    for (int tc = 0; tc < 8; tc++) {
+      for (int e = blockIdx.x; e < n_items; e += gridDim.x) {
+        const int2 it = items[e];
+        const LatDesc D = descs[it.x];
+        bcc_tile_pass<K, NW, PL, SLOTS>(D, Q, tc, it.y, D.sweep + (unsigned long long)s, box, sA, sB, s_stat);
+      }
+      if ((int)blockIdx.x == skip_cta) return;
+      epoch++;
+      if (!grid_barrier(bar, epoch * gridDim.x, status, timeout_ns)) return;
+    }
+}
+
+}  // namespace bccfast
+
+namespace {
+
+void check_batch(const smcx_batch* b) {
+  if (b->lat.empty()) fail(SMCX_E_INVALID_ARG, "empty batch");
+  const smcx_lattice* h0 = b->lat[0];
+  for (const smcx_lattice* h : b->lat) {
+    if (!h->have_epi) fail(SMCX_E_NO_EPI, "every replica needs smcx_set_epi");
+    if (h->kind != kBCC) fail(SMCX_E_UNSUPPORTED, "batched sweeps run BCC lattices");
+    if (h->M != h0->M || h->shells.K != h0->shells.K || h->V != h0->V)
+      fail(SMCX_E_INVALID_ARG, "replicas must share M and the EPI table");
+    if (h->stream != b->stream) fail(SMCX_E_INVALID_ARG, "replicas must share the batch stream");
+    if (!bcc_fast_usable(h))
+      fail(SMCX_E_UNSUPPORTED, "replica schedule needs tiles of at most 20 cells (BCC, M <= 8)");
+  }
+  if (h0->shells.K != 4) fail(SMCX_E_UNSUPPORTED, "batched sweeps run 4-shell EPI tables");
+}
+
+void rebuild_items(smcx_batch* b) {
+  std::vector<int2> items;
+  int nq = 0;
+  for (size_t r = 0; r < b->lat.size(); r++) {
+    const smcx_lattice* h = b->lat[r];
+    const int per_colour = (h->sched.nt[0] / 2) * (h->sched.nt[1] / 2) * (h->sched.nt[2] / 2);
+    for (int j = 0; j < per_colour; j++) items.push_back(make_int2((int)r, j));
+    nq = std::max(nq, bcc_slots_per_axis(h->n, h->sched));
+  }
+  // largest replicas first, so the tail of each colour pass holds small tiles
+  std::stable_sort(items.begin(), items.end(), [&](const int2& a, const int2& c) {
+    const smcx_lattice* ha = b->lat[a.x];
+    const smcx_lattice* hc = b->lat[c.x];
+    return (long long)ha->N / ((long long)ha->sched.nt[0] * ha->sched.nt[1] * ha->sched.nt[2]) >
+           (long long)hc->N / ((long long)hc->sched.nt[0] * hc->sched.nt[1] * hc->sched.nt[2]);
+  });
+  cudaFree(b->d_items);
+  b->d_items = nullptr;
+  check_cuda(cudaMalloc(&b->d_items, items.size() * sizeof(int2)), "batch work list");
+  check_cuda(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                             b->stream),
+             "batch work list upload");
+  check_cuda(cudaStreamSynchronize(b->stream), "batch work list sync");
+  b->n_items = (int)items.size();
+  int threads, slots;
+  bcc_block_shape(nq, b->threads, &threads, &slots);
+  b->threads = threads;
+  b->slots = slots;
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+  b->graphs.clear();
+  b->items_dirty = false;
+}
+
+using KernelFn = void (*)(const bccfast::Planes, const bccfast::LatDesc*, const int2*, int, int, unsigned*, int*,
+                          long long, int, int);
+
+KernelFn pick_kernel(int nw, int pl, int slots) {
+  using namespace bccfast;
+  if (nw == 1 && pl == 2 && slots == 1) return k_bcc_batch<4, 1, 2, 1>;
+  if (nw == 1 && pl == 2) return k_bcc_batch<4, 1, 2, 2>;
+  if (nw == 1 && slots == 1) return k_bcc_batch<4, 1, 3, 1>;
+  if (nw == 1) return k_bcc_batch<4, 1, 3, 2>;
+  if (pl == 2 && slots == 1) return k_bcc_batch<4, 2, 2, 1>;
+  if (pl == 2) return k_bcc_batch<4, 2, 2, 2>;
+  if (slots == 1) return k_bcc_batch<4, 2, 3, 1>;
+  return k_bcc_batch<4, 2, 3, 2>;
+}
+
+}  // namespace
+
+void upload_thresholds_for(smcx_lattice* h, double T);  // smcx_api.cu
+
+// Enqueue n sweeps of every replica (temperatures T[r]); returns after the
+// launch completed and its status was read.
+static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed);
+
+void batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed) {
+  check_batch(b);
+  // at most 2^16 sweeps per launch keep the barrier counter far from overflow
+  for (int64_t done = 0; done < n_sweeps;) {
+    const int64_t n = std::min<int64_t>(n_sweeps - done, 1 << 16);
+    batch_sweep_launch(b, T, n, seed);
+    done += n;
+  }
+}
+
+static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed) {
+  if (b->items_dirty) rebuild_items(b);
+  const size_t R = b->lat.size();
+  std::vector<bccfast::LatDesc> desc(R);
+  int max_nA = 0;
+  for (size_t r = 0; r < R; r++) {
+    smcx_lattice* h = b->lat[r];
+    if (!(T[r] > 0.0) || !std::isfinite(T[r])) fail(SMCX_E_INVALID_ARG, "temperatures must be finite and > 0");
+    if (h->sweep_cum + (uint64_t)n_sweeps >= (1ull << 63)) fail(SMCX_E_INVALID_ARG, "sweep counter overflow");
+    upload_thresholds_for(h, T[r]);
+    bccfast::LatDesc& D = desc[r];
+    memset(&D, 0, sizeof(D));
+    D.sites = h->d_sites;
+    D.thr = h->d_thr;
+    D.stats = h->d_stats;
+    for (int a = 0; a < 3; a++) {
+      D.n[a] = h->n[a];
+      D.nt[a] = h->sched.nt[a];
+    }
+    D.L = h->sched.L;
+    D.NQ = bcc_slots_per_axis(h->n, h->sched);
+    D.nA = h->thr_nA;
+    D.storage = h->storage;
+    D.replica = h->replica;
+    D.seed_lo = (uint32_t)seed;
+    D.seed_hi = (uint32_t)(seed >> 32);
+    D.sweep = h->sweep_cum;
+    max_nA = std::max(max_nA, D.nA);
+  }
+  if (!b->d_desc) check_cuda(cudaMalloc(&b->d_desc, R * sizeof(bccfast::LatDesc)), "batch descriptors");
+  check_cuda(cudaMemcpyAsync(b->d_desc, desc.data(), R * sizeof(bccfast::LatDesc), cudaMemcpyHostToDevice, b->stream),
+             "batch descriptor upload");
+  bccfast::Planes Q;
+  const int PL = build_planes(b->lat[0], &Q, 2);
+  const int nw = b->lat[0]->M <= 4 ? 1 : 2;
+  KernelFn fn = pick_kernel(nw, PL, b->slots);
+  // shared memory for the largest table of this call, rounded up so that a
+  // graph instantiated for it serves nearby temperature sets as well
+  const int nA_cap = std::min(kNA, ((max_nA + 255) / 256) * 256);
+  const size_t smem = bccfast::smem_bytes(nA_cap);
+  check_cuda(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+             "batch smem attribute");
+  int dev = 0, nsm = 0, per_sm = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, b->threads, smem), "occupancy");
+  if (per_sm < 1) fail(SMCX_E_UNSUPPORTED, "batch kernel does not fit an SM");
+  const int grid = std::min(b->n_items, per_sm * nsm);
+  if (!b->d_bar) {
+    check_cuda(cudaMalloc(&b->d_bar, sizeof(unsigned)), "barrier word");
+    check_cuda(cudaMalloc(&b->d_status, sizeof(int)), "status word");
+  }
+  int n_int = (int)n_sweeps;
+  int max_nA_arg = nA_cap;
+  void* args[] = {(void*)&Q, (void*)&b->d_desc, (void*)&b->d_items, (void*)&b->n_items, (void*)&n_int,
+                  (void*)&b->d_bar, (void*)&b->d_status, (void*)&b->timeout_ns, (void*)&b->skip_cta,
+                  (void*)&max_nA_arg};
+  if (b->graph_V != b->lat[0]->V) {
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    b->graph_V = b->lat[0]->V;
+  }
+  auto enqueue = [&]() {
+    check_cuda(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream), "barrier reset");
+    check_cuda(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream), "status reset");
+    check_cuda(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(b->threads), args, smem, b->stream),
+               "batch cooperative launch");
+  };
+  bool launched = false;
+  if (b->use_graph && b->skip_cta < 0) {
+    // one instantiated graph per sweep count; planes, seed and descriptors
+    // are read from memory or baked parameters that do not change between
+    // calls of one batch (the EPI is fixed once the batch sweeps)
+    const long long key = (long long)n_sweeps * 8192 + nA_cap;
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream);
+        cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+        cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(b->threads), args, smem, b->stream);
+        ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess && g != nullptr;
+      }
+      if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();  // clear a failed capture's sticky-free error
+      if (ok) it = b->graphs.emplace(key, ge).first;
+      else b->use_graph = false;
+    }
+    if (b->use_graph) {
+      check_cuda(cudaGraphLaunch(it->second, b->stream), "batch graph launch");
+      launched = true;
+    }
+  }
+  if (!launched) enqueue();
+  b->last_grid = grid;
+  b->last_graph = launched;
+  int status = 0;
+  check_cuda(cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "status read");
+  check_cuda(cudaStreamSynchronize(b->stream), "batch sync");
+  if (status != 0) fail(status, "batched sweep stopped: a grid barrier timed out");
+  for (smcx_lattice* h : b->lat) h->sweep_cum += (uint64_t)n_sweeps;
+}
+
+void batch_release(smcx_batch* b) {
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_items);
+  cudaFree(b->d_bar);
+  cudaFree(b->d_status);
+}
+
+// Autotuner: for each candidate (link cell L, tile target, threads per CTA)
+// assign every replica the schedule the candidate implies, time `trial`
+// batched sweeps on a copy of the configurations, restore them, and keep the
+// fastest candidate.  The schedule defines the trajectory, so the choice is
+// reported (smcx_get_schedule on each replica) and a run can be reproduced.
+void batch_autotune(smcx_batch* b, const double* T, int trial, int* best_threads) {
+  check_batch(b);
+  const size_t R = b->lat.size();
+  struct Saved {
+    uint8_t* d_copy = nullptr;
+    smcx_sched sched;
+    uint64_t sweep;
+    unsigned long long stats[4];
+  };
+  std::vector<Saved> saved(R);
+  for (size_t r = 0; r < R; r++) {
+    smcx_lattice* h = b->lat[r];
+    check_cuda(cudaMalloc(&saved[r].d_copy, h->site_bytes), "autotune snapshot");
+    check_cuda(cudaMemcpyAsync(saved[r].d_copy, h->d_sites, h->site_bytes, cudaMemcpyDeviceToDevice, b->stream),
+               "autotune snapshot copy");
+    check_cuda(cudaMemcpyAsync(saved[r].stats, h->d_stats, sizeof(saved[r].stats), cudaMemcpyDeviceToHost, b->stream),
+               "autotune stats snapshot");
+    saved[r].sched = h->sched;
+    saved[r].sweep = h->sweep_cum;
+  }
+  check_cuda(cudaStreamSynchronize(b->stream), "autotune snapshot sync");
+  struct Cand {
+    int L, target, threads;
+  };
+  std::vector<Cand> cands;
+  for (int L : {3, 4})
+    for (int target : {12, 16, 20})
+      for (int th : {0, 128, 256}) cands.push_back({L, target, th});
+  double best = 1e300;
+  Cand bestc = cands[0];
+  std::vector<smcx_sched> best_sched(R);
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "event");
+  check_cuda(cudaEventCreate(&e1), "event");
+  for (const Cand& c : cands) {
+    bool ok = true;
+    std::vector<smcx_sched> sc(R);
+    for (size_t r = 0; r < R && ok; r++) {
+      smcx_lattice* h = b->lat[r];
+      sc[r].L = c.L;
+      for (int a = 0; a < 3; a++) {
+        int nt = 2;
+        while ((h->n[a] + nt - 1) / nt > c.target) nt += 2;
+        sc[r].nt[a] = nt;
+      }
+      if (!schedule_problem(h->shells, h->n, sc[r]).empty()) ok = false;
+    }
+    if (!ok) continue;
+    for (size_t r = 0; r < R; r++) b->lat[r]->sched = sc[r];
+    b->threads = c.threads;
+    b->items_dirty = true;
+    bool usable = true;
+    for (size_t r = 0; r < R; r++) usable = usable && bcc_fast_usable(b->lat[r]);
+    if (!usable) continue;
+    try {
+      batch_sweep(b, T, 1, 0x5eedull);  // warm-up: instantiate, load tables
+      check_cuda(cudaEventRecord(e0, b->stream), "event");
+      batch_sweep(b, T, trial, 0x5eedull);
+      check_cuda(cudaEventRecord(e1, b->stream), "event");
+      check_cuda(cudaEventSynchronize(e1), "event sync");
+    } catch (const SmcxException&) {
+      continue;
+    }
+    float ms = 0;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+    if (ms < best) {
+      best = ms;
+      bestc = c;
+      best_sched = sc;
+    }
+    // restore configurations and counters before the next candidate
+    for (size_t r = 0; r < R; r++) {
+      smcx_lattice* h = b->lat[r];
+      check_cuda(cudaMemcpyAsync(h->d_sites, saved[r].d_copy, h->site_bytes, cudaMemcpyDeviceToDevice, b->stream),
+                 "autotune restore");
+      h->sweep_cum = saved[r].sweep;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t r = 0; r < R; r++) {
+    smcx_lattice* h = b->lat[r];
+    check_cuda(cudaMemcpyAsync(h->d_sites, saved[r].d_copy, h->site_bytes, cudaMemcpyDeviceToDevice, b->stream),
+               "autotune restore");
+    check_cuda(cudaMemcpyAsync(h->d_stats, saved[r].stats, sizeof(saved[r].stats), cudaMemcpyHostToDevice, b->stream),
+               "autotune stats restore");
+    h->sweep_cum = saved[r].sweep;
+    h->sched = best < 1e300 ? best_sched[r] : saved[r].sched;
+    h->sched_auto = false;
+  }
+  check_cuda(cudaStreamSynchronize(b->stream), "autotune restore sync");
+  for (auto& s : saved) cudaFree(s.d_copy);
+  if (best >= 1e300) fail(SMCX_E_SCHEDULE, "no autotuner candidate fits these lattices");
+  b->threads = bestc.threads;
+  b->items_dirty = true;
+  if (best_threads) *best_threads = bestc.threads;
+}
+
+}  // namespace smcx
+
+namespace {
+void need_(bool ok, int code, const char* msg) {
+  if (!ok) smcx::fail(code, msg);
+}
+}  // namespace
+
+using namespace smcx;
+
+extern "C" {
+
+int smcx_batch_create(smcx_batch** out, int R, smcx_lattice* const* lattices, void* stream) {
+  return guarded_call([&] {
+    need_(out && lattices && R >= 1, SMCX_E_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    smcx_batch* b = new smcx_batch();
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    for (int r = 0; r < R; r++) {
+      if (!lattices[r]) {
+        delete b;
+        fail(SMCX_E_INVALID_ARG, "NULL lattice in batch");
+      }
+      b->lat.push_back(lattices[r]);
+    }
+    *out = b;
+  });
+}
+
+int smcx_batch_destroy(smcx_batch* b) {
+  if (!b) return SMCX_OK;
+  return guarded_call([&] {
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+  });
+}
+
+int smcx_batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed) {
+  return guarded_call([&] {
+    need_(b && T, SMCX_E_INVALID_ARG, "NULL argument");
+    need_(n_sweeps >= 0, SMCX_E_INVALID_ARG, "negative sweep count");
+    batch_sweep(b, T, n_sweeps, seed);
+  });
+}
+
+int smcx_batch_autotune(smcx_batch* b, const double* T, int trial_sweeps, int* threads) {
+  return guarded_call([&] {
+    need_(b && T, SMCX_E_INVALID_ARG, "NULL argument");
+    need_(trial_sweeps >= 1, SMCX_E_INVALID_ARG, "trial_sweeps must be >= 1");
+    batch_autotune(b, T, trial_sweeps, threads);
+  });
+}
+
+int smcx_batch_energy(smcx_batch* b, int64_t* E) {
+  return guarded_call([&] {
+    need_(b && E, SMCX_E_INVALID_ARG, "NULL argument");
+    for (size_t r = 0; r < b->lat.size(); r++) {
+      int rc = smcx_energy(b->lat[r], E + r);
+      if (rc != SMCX_OK) fail(rc, last_error());
+    }
+  });
+}
+
+int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_graph) {
+  return guarded_call([&] {
+    need_(b != nullptr, SMCX_E_INVALID_ARG, "NULL batch");
+    if (grid) *grid = b->last_grid;
+    if (threads) *threads = b->threads;
+    if (used_graph) *used_graph = b->last_graph ? 1 : 0;
+  });
+}
+
+int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms) {
+  return guarded_call([&] {
+    need_(b != nullptr, SMCX_E_INVALID_ARG, "NULL batch");
+    need_(timeout_ms >= 1 && timeout_ms <= 60000, SMCX_E_INVALID_ARG, "timeout must be 1..60000 ms");
+    b->skip_cta = skip_cta < 0 ? -1 : skip_cta;
+    b->timeout_ns = (long long)timeout_ms * 1000000ll;
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+// BCC tile pass specialised for throughput (M <= 8 species, K <= 4 shells,
+// tiles up to 20 cells so that tile + 2-cell halo fits a 24^3 box).  Used by
+// the single-lattice sweep (smcx_sweep_bcc.cu) and the batched persistent
+// sweep (smcx_batch.cu).
+//
+// Same trials, same order of phases, same Philox words and the same integer
+// arithmetic as k_tile_sweep in smcx_sweep.cu: the result is bit-identical;
+// only the data layout and the instruction mix differ.
+//
+//  * Shared memory holds one byte per site, the species id times 8, in two
+//    sublattice arrays with padded pitches (27 x 24 cells per plane) that
+//    spread a phase's lanes over the banks.  The box pitches are compile-time
+//    constants, so every neighbour load is a single LDS with an immediate
+//    offset from the centre (or partner) address.
+//  * Each neighbour adds 1 << (8 sigma) to a per-shell register of byte
+//    counters (biased by 0x80 per byte): the s environment adds, the s'
+//    environment subtracts, so byte c ends as 0x80 + n_k(s)[c] - n_k(s')[c].
+//  * dE = G_b - G_a with G_p = sum_k sum_c V_k[p][c] D_k[c]: dp4a against the
+//    byte planes of V held in the kernel parameter bank (uniform operands).
+//  * A thread owns SLOTS link-cell slots of the tile for the whole pass; the
+//    Philox block of a cell (two sites) is drawn once in the b = 0 phase and
+//    its second half used in the b = 1 phase that immediately follows.
+#pragma once
+
+#include "smcx_device.cuh"
+
+namespace smcx {
+
+namespace bccfast {
+
+constexpr int PX = 27;             // row pitch (cells)
+constexpr int PY = 24;             // rows per plane
+constexpr int PZ = 24;             // planes
+constexpr int SUB = PX * PY * PZ;  // bytes per sublattice array
+constexpr int BOX = 24;            // usable box edge (tile <= 20 with halo 2)
+constexpr int MAXPLANES = 3;
+
+// Byte planes of the EPI table, shared by every lattice of a launch:
+// P[j][k][p][w] holds bytes j of V_k[p][4w .. 4w+3] (planes below the top one
+// unsigned, the top plane signed).
+struct Planes {
+  uint32_t P[MAXPLANES][kMaxShells][kMaxSweepM][2];
+};
+
+// One lattice as the tile pass sees it.
+struct LatDesc {
+  uint8_t* sites;
+  const uint32_t* thr;          // A[kNA] then B[kNB] at this lattice's temperature
+  unsigned long long* stats;    // trials, accepts, same-species, sum dE
+  int n[3], nt[3];
+  int L, NQ;                    // link-cell edge; link-cell slots per tile axis
+  int nA, storage, replica;
+  uint32_t seed_lo, seed_hi;
+  unsigned long long sweep;     // cumulative index of the first sweep of the call
+};
+
+// 50 BCC neighbour vectors (half units) of shells 1..4 with their shell.
+struct Vec {
+  int x, y, z, k;
+};
+__host__ __device__ constexpr int bcc_shell_of(int x, int y, int z) {
+  return (x * x + y * y + z * z) == 3 ? 0 : (x * x + y * y + z * z) == 4 ? 1 : (x * x + y * y + z * z) == 8 ? 2
+         : (x * x + y * y + z * z) == 11 ? 3 : -1;
+}
+struct VecTable {
+  Vec v[50];
+  int n;
+};
+__host__ __device__ constexpr VecTable make_vecs() {
+  VecTable t{};
+  t.n = 0;
+  for (int x = -3; x <= 3; x++)
+    for (int y = -3; y <= 3; y++)
+      for (int z = -3; z <= 3; z++) {
+        const bool odd = (x & 1) && (y & 1) && (z & 1);
+        const bool even = !(x & 1) && !(y & 1) && !(z & 1);
+        if (!(odd || even)) continue;
+        const int k = bcc_shell_of(x, y, z);
+        if (k < 0) continue;
+        t.v[t.n] = Vec{x, y, z, k};
+        t.n++;
+      }
+  return t;
+}
+__host__ __device__ constexpr int floor2(int p) { return p >= 0 ? p / 2 : -((1 - p) / 2); }
+// byte offset (in the box) from a site of sublattice B to its neighbour along v
+__host__ __device__ constexpr int nb_offset(int B, int x, int y, int z) {
+  return (((B + x) & 1) - B) * SUB + (floor2(B + z) * PY + floor2(B + y)) * PX + floor2(B + x);
+}
+
+__device__ __forceinline__ int dp4a_su(int a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ int dp4a_ss(int a, uint32_t b, int c) {
+  int d;
+  asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Accumulate the environment of a site of sublattice B at box index `c`
+// into the per-shell byte counters (SIGN = +1 for s, -1 for s').
+template <int B, int K, int NW, int SIGN>
+__device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[kMaxShells][2]) {
+  constexpr VecTable T = make_vecs();
+#pragma unroll
+  for (int j = 0; j < T.n; j++) {
+    const int k = T.v[j].k;
+    if (k >= K) continue;
+    const uint32_t v = box[c + nb_offset(B, T.v[j].x, T.v[j].y, T.v[j].z)];
+    if (NW == 1) {
+      const uint32_t one = 1u << v;
+      if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
+    } else {
+      uint32_t lo, hi;
+      asm("shl.b32 %0, 1, %1;" : "=r"(lo) : "r"(v));
+      asm("shl.b32 %0, 1, %1;" : "=r"(hi) : "r"(v - 32u));
+      if (SIGN > 0) {
+        h[k][0] += lo;
+        h[k][1] += hi;
+      } else {
+        h[k][0] -= lo;
+        h[k][1] -= hi;
+      }
+    }
+  }
+}
+
+template <int NW>
+__device__ __forceinline__ void add_one(uint32_t (&h)[2], uint32_t v, int sign) {
+  uint32_t lo, hi;
+  asm("shl.b32 %0, 1, %1;" : "=r"(lo) : "r"(v));
+  if (NW == 1) {
+    h[0] += sign > 0 ? lo : (uint32_t)(-(int)lo);
+  } else {
+    asm("shl.b32 %0, 1, %1;" : "=r"(hi) : "r"(v - 32u));
+    h[0] += sign > 0 ? lo : (uint32_t)(-(int)lo);
+    h[1] += sign > 0 ? hi : (uint32_t)(-(int)hi);
+  }
+}
+
+// One trial at box index s (sublattice B) with Philox words (rd, ru).
+template <int B, int K, int NW, int PL>
+__device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t ru, const Planes& P, int nA,
+                                      const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
+                                      long long& dsum) {
+  const int dir = (int)(rd >> 29);  // floor(rd * 8 / 2^32)
+  // shell-1 vector (+-1,+-1,+-1): bit 2 -> x, bit 1 -> y, bit 0 -> z
+  const int dx = ((dir >> 2) & 1) - 1 + B, dy = ((dir >> 1) & 1) - 1 + B, dz = (dir & 1) - 1 + B;
+  const int sp = s + (1 - 2 * B) * SUB + (dz * PY + dy) * PX + dx;
+  const uint32_t a8 = box[s], b8 = box[sp];
+  if (a8 == b8) {
+    same++;
+    return;
+  }
+  uint32_t h[kMaxShells][2];
+#pragma unroll
+  for (int k = 0; k < kMaxShells; k++) {
+    h[k][0] = 0x80808080u;
+    h[k][1] = 0x80808080u;
+  }
+  gather<B, K, NW, +1>(box, s, h);
+  gather<1 - B, K, NW, -1>(box, sp, h);
+  // the s-s' bond is not part of either environment after the swap
+  add_one<NW>(h[0], b8, -1);
+  add_one<NW>(h[0], a8, +1);
+  // G_p = sum_k sum_c V_k[p][c] D_k[c]
+  const int a = (int)(a8 >> 3), b = (int)(b8 >> 3);
+  int Ga = 0, Gb = 0;
+#pragma unroll
+  for (int p = 0; p < 4 * NW; p++) {
+    int acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+#pragma unroll
+      for (int w = 0; w < NW; w++) {
+        const int d = (int)(h[k][w] ^ 0x80808080u);
+        if (PL == 1) {
+          acc0 = dp4a_ss(d, P.P[0][k][p][w], acc0);
+        } else {
+          acc0 = dp4a_su(d, P.P[0][k][p][w], acc0);
+          if (PL == 2) {
+            acc1 = dp4a_ss(d, P.P[1][k][p][w], acc1);
+          } else {
+            acc1 = dp4a_su(d, P.P[1][k][p][w], acc1);
+            acc2 = dp4a_ss(d, P.P[2][k][p][w], acc2);
+          }
+        }
+      }
+    }
+    const int G = acc0 + (acc1 << 8) + (acc2 << 16);
+    Ga = (p == a) ? G : Ga;
+    Gb = (p == b) ? G : Gb;
+  }
+  const int dE = Gb - Ga;
+  if (metropolis_accept(dE, ru, sA, nA, sB)) {
+    box[s] = (uint8_t)b8;
+    box[sp] = (uint8_t)a8;
+    acc++;
+    dsum += dE;
+  }
+}
+
+// One tile pass: stage the tile of colour `tc` with index `jt` among the
+// tiles of that colour (plus its 2-cell halo) into shared memory, run every
+// intra-colour phase of the tile, write the tile and its 1-cell partner ring
+// back, add the statistics.  Every thread of the CTA must call it.
+// Shared memory: box (2 * SUB bytes), sA (nA words), sB (kNB words), s_stat[3].
+template <int K, int NW, int PL, int SLOTS>
+__device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q, int tc, int jt,
+                                              unsigned long long sweep, uint8_t* box, uint32_t* sA, uint32_t* sB,
+                                              unsigned long long* s_stat) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int ntc0 = D.nt[0] / 2, ntc1 = D.nt[1] / 2;
+  const int jx = jt % ntc0, jy = (jt / ntc0) % ntc1, jz = jt / (ntc0 * ntc1);
+  const int ti[3] = {2 * jx + (tc & 1), 2 * jy + ((tc >> 1) & 1), 2 * jz + ((tc >> 2) & 1)};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = D.n[a] / D.nt[a], rem = D.n[a] % D.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+  __syncthreads();  // the previous pass of this CTA is done with the tables
+  if (tid < 3) s_stat[tid] = 0;
+  for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
+  for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+
+  // stage tile + 2-cell halo: one box row (fixed y, z) per warp iteration
+  constexpr int h = 2;
+  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  for (int row = warp; row < ey * ez; row += nwarp) {
+    const int ys = row % ey, zs = row / ey;
+    const int gy = wrap_add(t0[1] - h, ys, ny), gz = wrap_add(t0[2] - h, zs, nz);
+    const long long rbase = ((long long)gz * ny + gy) * nx;
+    for (int xs = lane; xs < ex; xs += 32) {
+      const int gx = wrap_add(t0[0] - h, xs, nx);
+      const long long cell = rbase + gx;
+      uint32_t s0, s1;
+      if (D.storage == SMCX_INT8) {
+        s0 = D.sites[2 * cell];
+        s1 = D.sites[2 * cell + 1];
+      } else {
+        const uint32_t byte = D.sites[cell];
+        s0 = byte & 15u;
+        s1 = byte >> 4;
+      }
+      const int bi = (zs * PY + ys) * PX + xs;
+      box[bi] = (uint8_t)(s0 << 3);
+      box[SUB + bi] = (uint8_t)(s1 << 3);
+    }
+  }
+  __syncthreads();
+
+  // link-cell slots of this thread: q = tid + j * nth
+  const int NQ = D.NQ, L = D.L;
+  int qx[SLOTS], qy[SLOTS], qz[SLOTS];
+  bool slot[SLOTS];
+#pragma unroll
+  for (int j = 0; j < SLOTS; j++) {
+    const int q = tid + j * nth;
+    qx[j] = q % NQ;
+    qy[j] = (q / NQ) % NQ;
+    qz[j] = q / (NQ * NQ);
+    slot[j] = q < NQ * NQ * NQ;
+  }
+  unsigned acc = 0, same = 0;
+  long long dsum = 0;
+  for (int cz = 0; cz < L; cz++)
+    for (int cy = 0; cy < L; cy++)
+      for (int cx = 0; cx < L; cx++) {
+        uint32_t keep_d[SLOTS], keep_u[SLOTS];
+#pragma unroll
+        for (int j = 0; j < SLOTS; j++) {
+          const int xr = cx + L * qx[j], yr = cy + L * qy[j], zr = cz + L * qz[j];
+          keep_d[j] = 0;
+          keep_u[j] = 0;
+          if (slot[j] && xr < ts[0] && yr < ts[1] && zr < ts[2]) {
+            const unsigned long long cell =
+                ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
+            const uint4 rw = attempt_block(cell * 2, sweep, D.replica, D.seed_lo, D.seed_hi);
+            keep_d[j] = rw.z;
+            keep_u[j] = rw.w;
+            const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+            trial<0, K, NW, PL>(box, s, rw.x, rw.y, Q, D.nA, sA, sB, acc, same, dsum);
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < SLOTS; j++) {
+          const int xr = cx + L * qx[j], yr = cy + L * qy[j], zr = cz + L * qz[j];
+          if (slot[j] && xr < ts[0] && yr < ts[1] && zr < ts[2]) {
+            const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+            trial<1, K, NW, PL>(box, SUB + s, keep_d[j], keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
+          }
+        }
+        __syncthreads();
+      }
+
+  // write back tile + 1-cell partner ring
+  const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
+  for (int row = warp; row < wy * wz; row += nwarp) {
+    const int yw = row % wy, zw = row / wy;
+    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
+    const long long rbase = ((long long)gz * ny + gy) * nx;
+    for (int xw = lane; xw < wx; xw += 32) {
+      const int gx = wrap_add(t0[0] - 1, xw, nx);
+      const long long cell = rbase + gx;
+      const int bi = ((zw + h - 1) * PY + (yw + h - 1)) * PX + (xw + h - 1);
+      const uint32_t s0 = box[bi] >> 3, s1 = box[SUB + bi] >> 3;
+      if (D.storage == SMCX_INT8) {
+        D.sites[2 * cell] = (uint8_t)s0;
+        D.sites[2 * cell + 1] = (uint8_t)s1;
+      } else {
+        D.sites[cell] = (uint8_t)(s0 | (s1 << 4));
+      }
+    }
+  }
+
+  atomicAdd(&s_stat[0], (unsigned long long)acc);
+  atomicAdd(&s_stat[1], (unsigned long long)same);
+  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&D.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 2);
+    atomicAdd(&D.stats[1], s_stat[0]);
+    atomicAdd(&D.stats[2], s_stat[1]);
+    atomicAdd(&D.stats[3], s_stat[2]);
+  }
+}
+
+// Shared-memory bytes of one CTA running tile passes with tables of up to nA
+// high-part entries.
+__host__ __device__ constexpr size_t smem_bytes(int nA) { return 2 * SUB + (size_t)(nA + kNB) * 4; }
+
+}  // namespace bccfast
+
+}  // namespace smcx

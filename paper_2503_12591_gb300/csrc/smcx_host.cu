@@ -131,8 +131,7 @@ smcx_sched choose_schedule(const Shells& s, const int n[3]) {
   const int target = 20;
   bool ok = true;
   for (int a = 0; a < 3; a++) {
-    int nt = (int)lround((double)n[a] / target);
-    if (nt < 2) nt = 2;
+    int nt = std::max(2, (n[a] + target - 1) / target);  // tiles of at most `target` cells
     if (nt % 2) nt++;
     while (nt > 2 && n[a] / nt < std::max(min_tile(s), 4)) nt -= 2;
     if (n[a] / nt < min_tile(s)) ok = false;

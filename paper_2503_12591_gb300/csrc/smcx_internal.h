@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -34,6 +36,25 @@ void set_error(const std::string& msg);
 const std::string& last_error();
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+
+// Run f, turning failures into an SMCX_E_* status and a per-thread message.
+template <class F>
+int guarded_call(F&& f) {
+  try {
+    set_error("");
+    f();
+    return SMCX_OK;
+  } catch (const SmcxException& e) {
+    set_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return SMCX_E_OOM;
+  } catch (...) {
+    set_error("unknown failure");
+    return SMCX_E_INVALID_ARG;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Host geometry.
@@ -74,6 +95,8 @@ int threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
 // ---------------------------------------------------------------------------
 }  // namespace smcx
 
+struct smcx_batch;  // smcx_batch.cu
+
 struct smcx_lattice {
   int kind = 0, m = 0, M = 0, storage = 0;
   int n[3] = {0, 0, 0};
@@ -97,6 +120,8 @@ struct smcx_lattice {
   size_t stage_bytes = 0;
 
   int kernel_choice = 0;  // 0 = fastest usable, 1 = generic tile/link-cell kernels
+  int replica = 0;        // Philox replica id (counter word 1, bits 16..31)
+  int bcc_threads = 0;    // tuned block size of the BCC tile kernel (0 = default)
   double thr_T = -1.0;
   int thr_nA = 0;
   uint64_t sweep_cum = 0;
@@ -113,6 +138,8 @@ void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
 void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
 void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
 bool bcc_fast_usable(const smcx_lattice* h);
+int bcc_slots_per_axis(const int n[3], const smcx_sched& sc);
+void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots);
 void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
 void species_counts(int M, const double* comp, int64_t N, int64_t* counts);
 

@@ -372,7 +372,7 @@ void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
   P.M = hd->M;
   P.nA = nA;
   P.storage = hd->storage;
-  P.replica = 0;
+  P.replica = hd->replica;
   P.seed_lo = (uint32_t)seed;
   P.seed_hi = (uint32_t)(seed >> 32);
   fill_offsets(hd, P, P.BX, P.BY);

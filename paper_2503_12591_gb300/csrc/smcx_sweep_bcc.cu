@@ -1,315 +1,48 @@
-// BCC tile sweep specialised for throughput (M <= 8 species, K <= 4 shells,
-// tiles up to 20 cells so that tile + 2-cell halo fits a 24^3 box).
-//
-// Same trials, same order of phases, same Philox words and the same integer
-// arithmetic as k_tile_sweep (see smcx_sweep.cu): the result is bit-identical;
-// only the data layout and the instruction mix differ.
-//
-//  * Shared memory holds one byte per site, the species id times 8, in two
-//    sublattice arrays with padded pitches (27 x 24 cells per plane) that
-//    spread a phase's lanes over the banks.  The box pitches are compile-time
-//    constants, so every neighbour load is a single LDS with an immediate
-//    offset from the centre (or partner) address.
-//  * Each neighbour adds 1 << (8 sigma) to a per-shell register of byte
-//    counters (biased by 0x80 per byte): the s environment adds, the s'
-//    environment subtracts, so byte c ends as 0x80 + n_k(s)[c] - n_k(s')[c].
-//  * dE = G_b - G_a with G_p = sum_k sum_c V_k[p][c] D_k[c]: dp4a against the
-//    byte planes of V held in the kernel parameter bank (uniform operands).
-//  * A thread owns one link-cell slot of the tile for the whole pass; the
-//    Philox block of a cell (two sites) is drawn once in the b = 0 phase and
-//    its second half used in the b = 1 phase that immediately follows.
-#include "smcx_device.cuh"
+// Single-lattice BCC sweep on the specialised tile pass (smcx_bcc_tile.cuh):
+// one launch per tile colour, one CTA per tile of that colour.
+#include "smcx_bcc_tile.cuh"
 
 namespace smcx {
 
 namespace bccfast {
 
-constexpr int PX = 27;             // row pitch (cells)
-constexpr int PY = 24;             // rows per plane
-constexpr int PZ = 24;             // planes
-constexpr int SUB = PX * PY * PZ;  // bytes per sublattice array
-constexpr int BOX = 24;            // usable box edge (tile <= 20 with halo 2)
-constexpr int MAXPLANES = 3;
-
-struct Params {
-  uint8_t* sites;
-  const uint32_t* thr;            // A[kNA] then B[kNB]
-  unsigned long long* stats;
-  int n[3], nt[3], ntc[3], tc;
-  int L, NQ;                      // link-cell edge; slots per axis
-  int nA, storage, replica;
-  uint32_t seed_lo, seed_hi;
-  unsigned long long sweep;
-  // byte planes of V: P[j][k][p][w] = bytes of V_k[p][4w .. 4w+3], plane j
-  uint32_t P[MAXPLANES][kMaxShells][kMaxSweepM][2];
-};
-
-// 50 BCC neighbour vectors (half units) of shells 1..4 with their shell.
-struct Vec {
-  int x, y, z, k;
-};
-__host__ __device__ constexpr int bcc_shell_of(int x, int y, int z) {
-  return (x * x + y * y + z * z) == 3 ? 0 : (x * x + y * y + z * z) == 4 ? 1 : (x * x + y * y + z * z) == 8 ? 2
-         : (x * x + y * y + z * z) == 11 ? 3 : -1;
-}
-struct VecTable {
-  Vec v[50];
-  int n;
-};
-__host__ __device__ constexpr VecTable make_vecs() {
-  VecTable t{};
-  t.n = 0;
-  for (int x = -3; x <= 3; x++)
-    for (int y = -3; y <= 3; y++)
-      for (int z = -3; z <= 3; z++) {
-        const bool odd = (x & 1) && (y & 1) && (z & 1);
-        const bool even = !(x & 1) && !(y & 1) && !(z & 1);
-        if (!(odd || even)) continue;
-        const int k = bcc_shell_of(x, y, z);
-        if (k < 0) continue;
-        t.v[t.n] = Vec{x, y, z, k};
-        t.n++;
-      }
-  return t;
-}
-__host__ __device__ constexpr int floor2(int p) { return p >= 0 ? p / 2 : -((1 - p) / 2); }
-// byte offset (in the box) from a site of sublattice B to its neighbour along v
-__host__ __device__ constexpr int nb_offset(int B, int x, int y, int z) {
-  return (((B + x) & 1) - B) * SUB + (floor2(B + z) * PY + floor2(B + y)) * PX + floor2(B + x);
-}
-
-__device__ __forceinline__ int dp4a_su(int a, uint32_t b, int c) {
-  int d;
-  asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-__device__ __forceinline__ int dp4a_ss(int a, uint32_t b, int c) {
-  int d;
-  asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-
-// Accumulate the environment of a site of sublattice B at box index `c`
-// into the per-shell byte counters (SIGN = +1 for s, -1 for s').
-template <int B, int K, int NW, int SIGN>
-__device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[kMaxShells][2]) {
-  constexpr VecTable T = make_vecs();
-#pragma unroll
-  for (int j = 0; j < T.n; j++) {
-    const int k = T.v[j].k;
-    if (k >= K) continue;
-    const uint32_t v = box[c + nb_offset(B, T.v[j].x, T.v[j].y, T.v[j].z)];
-    if (NW == 1) {
-      const uint32_t one = 1u << v;
-      if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
-    } else {
-      uint32_t lo, hi;
-      asm("shl.b32 %0, 1, %1;" : "=r"(lo) : "r"(v));
-      asm("shl.b32 %0, 1, %1;" : "=r"(hi) : "r"(v - 32u));
-      if (SIGN > 0) {
-        h[k][0] += lo;
-        h[k][1] += hi;
-      } else {
-        h[k][0] -= lo;
-        h[k][1] -= hi;
-      }
-    }
-  }
-}
-
-template <int NW>
-__device__ __forceinline__ void add_one(uint32_t (&h)[2], uint32_t v, int sign) {
-  uint32_t lo, hi;
-  asm("shl.b32 %0, 1, %1;" : "=r"(lo) : "r"(v));
-  if (NW == 1) {
-    h[0] += sign > 0 ? lo : (uint32_t)(-(int)lo);
-  } else {
-    asm("shl.b32 %0, 1, %1;" : "=r"(hi) : "r"(v - 32u));
-    h[0] += sign > 0 ? lo : (uint32_t)(-(int)lo);
-    h[1] += sign > 0 ? hi : (uint32_t)(-(int)hi);
-  }
-}
-
-// One trial at box index s (sublattice B) with Philox words (rd, ru).
-template <int B, int K, int NW, int PL>
-__device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t ru, const Params& P,
-                                      const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
-                                      long long& dsum) {
-  const int dir = (int)(rd >> 29);  // floor(rd * 8 / 2^32)
-  // shell-1 vector (+-1,+-1,+-1): bit 2 -> x, bit 1 -> y, bit 0 -> z
-  const int dx = ((dir >> 2) & 1) - 1 + B, dy = ((dir >> 1) & 1) - 1 + B, dz = (dir & 1) - 1 + B;
-  const int sp = s + (1 - 2 * B) * SUB + (dz * PY + dy) * PX + dx;
-  const uint32_t a8 = box[s], b8 = box[sp];
-  if (a8 == b8) {
-    same++;
-    return;
-  }
-  uint32_t h[kMaxShells][2];
-#pragma unroll
-  for (int k = 0; k < kMaxShells; k++) {
-    h[k][0] = 0x80808080u;
-    h[k][1] = 0x80808080u;
-  }
-  gather<B, K, NW, +1>(box, s, h);
-  gather<1 - B, K, NW, -1>(box, sp, h);
-  // the s-s' bond is not part of either environment after the swap
-  add_one<NW>(h[0], b8, -1);
-  add_one<NW>(h[0], a8, +1);
-  // G_p = sum_k sum_c V_k[p][c] D_k[c]
-  const int a = (int)(a8 >> 3), b = (int)(b8 >> 3);
-  int Ga = 0, Gb = 0;
-#pragma unroll
-  for (int p = 0; p < 4 * NW; p++) {
-    int acc0 = 0, acc1 = 0, acc2 = 0;
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-#pragma unroll
-      for (int w = 0; w < NW; w++) {
-        const int d = (int)(h[k][w] ^ 0x80808080u);
-        if (PL == 1) {
-          acc0 = dp4a_ss(d, P.P[0][k][p][w], acc0);
-        } else {
-          acc0 = dp4a_su(d, P.P[0][k][p][w], acc0);
-          if (PL == 2) {
-            acc1 = dp4a_ss(d, P.P[1][k][p][w], acc1);
-          } else {
-            acc1 = dp4a_su(d, P.P[1][k][p][w], acc1);
-            acc2 = dp4a_ss(d, P.P[2][k][p][w], acc2);
-          }
-        }
-      }
-    }
-    const int G = acc0 + (acc1 << 8) + (acc2 << 16);
-    Ga = (p == a) ? G : Ga;
-    Gb = (p == b) ? G : Gb;
-  }
-  const int dE = Gb - Ga;
-  if (metropolis_accept(dE, ru, sA, P.nA, sB)) {
-    box[s] = (uint8_t)b8;
-    box[sp] = (uint8_t)a8;
-    acc++;
-    dsum += dE;
-  }
-}
-
-template <int K, int NW, int PL>
-__global__ void __launch_bounds__(512, 2) k_bcc_tile_sweep(const Params P) {
+template <int K, int NW, int PL, int SLOTS>
+__global__ void __launch_bounds__(512, 2) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
-  uint8_t* box = smem;                                         // 2 * SUB bytes
-  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);  // nA entries
-  uint32_t* sB = sA + P.nA;                                    // kNB entries
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-
-  int bid = blockIdx.x;
-  const int jx = bid % P.ntc[0];
-  bid /= P.ntc[0];
-  const int jy = bid % P.ntc[1];
-  const int jz = bid / P.ntc[1];
-  const int ti[3] = {2 * jx + (P.tc & 1), 2 * jy + ((P.tc >> 1) & 1), 2 * jz + ((P.tc >> 2) & 1)};
-  int t0[3], ts[3];
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    const int base = P.n[a] / P.nt[a], rem = P.n[a] % P.nt[a];
-    ts[a] = base + (ti[a] < rem ? 1 : 0);
-    t0[a] = ti[a] * base + min(ti[a], rem);
-  }
-  if (tid < 3) s_stat[tid] = 0;
-  for (int i = tid; i < P.nA; i += nth) sA[i] = P.thr[i];
-  for (int i = tid; i < kNB; i += nth) sB[i] = P.thr[kNA + i];
-
-  // stage tile + 2-cell halo: one box row (fixed y, z) per warp iteration
-  constexpr int h = 2;
-  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
-  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  for (int row = warp; row < ey * ez; row += nwarp) {
-    const int ys = row % ey, zs = row / ey;
-    const int gy = wrap_add(t0[1] - h, ys, ny), gz = wrap_add(t0[2] - h, zs, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xs = lane; xs < ex; xs += 32) {
-      const int gx = wrap_add(t0[0] - h, xs, nx);
-      const long long cell = rbase + gx;
-      uint32_t s0, s1;
-      if (P.storage == SMCX_INT8) {
-        s0 = P.sites[2 * cell];
-        s1 = P.sites[2 * cell + 1];
-      } else {
-        const uint32_t byte = P.sites[cell];
-        s0 = byte & 15u;
-        s1 = byte >> 4;
-      }
-      const int bi = (zs * PY + ys) * PX + xs;
-      box[bi] = (uint8_t)(s0 << 3);
-      box[SUB + bi] = (uint8_t)(s1 << 3);
-    }
-  }
-  __syncthreads();
-
-  // this thread's link-cell slot
-  const int NQ = P.NQ, L = P.L;
-  const int qx = tid % NQ, qy = (tid / NQ) % NQ, qz = tid / (NQ * NQ);
-  const bool slot = tid < NQ * NQ * NQ;
-  unsigned acc = 0, same = 0;
-  long long dsum = 0;
-  for (int cz = 0; cz < L; cz++)
-    for (int cy = 0; cy < L; cy++)
-      for (int cx = 0; cx < L; cx++) {
-        const int xr = cx + L * qx, yr = cy + L * qy, zr = cz + L * qz;
-        const bool live = slot && xr < ts[0] && yr < ts[1] && zr < ts[2];
-        const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
-        uint4 rw = make_uint4(0, 0, 0, 0);
-        if (live) {
-          const unsigned long long cell =
-              ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
-          rw = attempt_block(cell * 2, P.sweep, P.replica, P.seed_lo, P.seed_hi);
-          trial<0, K, NW, PL>(box, s, rw.x, rw.y, P, sA, sB, acc, same, dsum);
-        }
-        __syncthreads();
-        if (live) trial<1, K, NW, PL>(box, SUB + s, rw.z, rw.w, P, sA, sB, acc, same, dsum);
-        __syncthreads();
-      }
-
-  // write back tile + 1-cell partner ring
-  const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
-  for (int row = warp; row < wy * wz; row += nwarp) {
-    const int yw = row % wy, zw = row / wy;
-    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xw = lane; xw < wx; xw += 32) {
-      const int gx = wrap_add(t0[0] - 1, xw, nx);
-      const long long cell = rbase + gx;
-      const int bi = ((zw + h - 1) * PY + (yw + h - 1)) * PX + (xw + h - 1);
-      const uint32_t s0 = box[bi] >> 3, s1 = box[SUB + bi] >> 3;
-      if (P.storage == SMCX_INT8) {
-        P.sites[2 * cell] = (uint8_t)s0;
-        P.sites[2 * cell + 1] = (uint8_t)s1;
-      } else {
-        P.sites[cell] = (uint8_t)(s0 | (s1 << 4));
-      }
-    }
-  }
-
-  atomicAdd(&s_stat[0], (unsigned long long)acc);
-  atomicAdd(&s_stat[1], (unsigned long long)same);
-  atomicAdd(&s_stat[2], (unsigned long long)dsum);
-  __syncthreads();
-  if (tid == 0) {
-    atomicAdd(&P.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 2);
-    atomicAdd(&P.stats[1], s_stat[0]);
-    atomicAdd(&P.stats[2], s_stat[1]);
-    atomicAdd(&P.stats[3], s_stat[2]);
-  }
+  uint8_t* box = smem;
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
+  uint32_t* sB = sA + D.nA;
+  bcc_tile_pass<K, NW, PL, SLOTS>(D, Q, tc, blockIdx.x, D.sweep, box, sA, sB, s_stat);
 }
 
 }  // namespace bccfast
 
-// Usable when the lattice is BCC, M <= 8, the tiles fit the 24^3 box and
-// one link-cell slot per thread covers a tile.
+// Byte planes of V: the fewest that hold every entry (2 at least, which
+// covers |V| < 2^15), or more if the caller asks (min_planes).  Planes below
+// the top one hold unsigned bytes, the top plane the signed high byte.
+int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes) {
+  memset(Q, 0, sizeof(*Q));
+  const int K = hd->shells.K, M = hd->M;
+  long long vmax = 0;
+  for (int32_t v : hd->V) vmax = std::max(vmax, std::llabs((long long)v));
+  const int PL = std::max(min_planes, vmax < 32768 ? 2 : 3);
+  for (int k = 0; k < K; k++)
+    for (int p = 0; p < M; p++)
+      for (int c = 0; c < M; c++) {
+        const uint32_t v = (uint32_t)hd->V[((size_t)k * M + p) * M + c];
+        const int w = c / 4, sh = 8 * (c % 4);
+        for (int j = 0; j < PL; j++) Q->P[j][k][p][w] |= ((v >> (8 * j)) & 0xFFu) << sh;
+      }
+  return PL;
+}
+
+// Usable when the lattice is BCC, M <= 8, |V| < 2^23, the tiles fit the
+// 24^3 box and two link-cell slots per thread cover a tile.
 bool bcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;
-  if (hd->kind != kBCC || hd->M > kMaxSweepM) return false;
-  if (sc.nt[0] == 1 && sc.nt[1] == 1 && sc.nt[2] == 1) return false;
+  if (hd->kind != kBCC || hd->M > kMaxSweepM || !hd->have_epi) return false;
+  if (sc.L == 0 || (sc.nt[0] == 1 && sc.nt[1] == 1 && sc.nt[2] == 1)) return false;
   if (halo_cells(hd->shells) != 2 || ring_cells(hd->shells) != 1) return false;
   for (int32_t v : hd->V)
     if (v >= (1 << 23) || v <= -(1 << 23)) return false;  // three byte planes at most
@@ -319,89 +52,97 @@ bool bcc_fast_usable(const smcx_lattice* hd) {
     if (tmax + 4 > bccfast::BOX) return false;
     nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
   }
-  return nq * nq * nq <= 512;
+  return nq * nq * nq <= 1024;
 }
 
-template <int K, int NW, int PL>
-static void launch_bcc(smcx_lattice* hd, bccfast::Params& P, int64_t n_sweeps) {
-  const int threads = ((P.NQ * P.NQ * P.NQ + 31) / 32) * 32;
-  const size_t smem = 2 * bccfast::SUB + (size_t)(P.nA + kNB) * 4;
-  check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL>,
+int bcc_slots_per_axis(const int n[3], const smcx_sched& sc) {
+  int nq = 0;
+  for (int a = 0; a < 3; a++) nq = std::max(nq, ((n[a] + sc.nt[a] - 1) / sc.nt[a] + sc.L - 1) / sc.L);
+  return nq;
+}
+
+// Threads per CTA and slots per thread for NQ^3 link-cell slots: the
+// handle's tuned block size if set, else one slot per thread.
+void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots) {
+  const int ns = nq * nq * nq;
+  int t = tuned_threads > 0 ? tuned_threads : std::min(512, ((ns + 31) / 32) * 32);
+  int s = (ns + t - 1) / t;
+  if (s > 2) {
+    s = 2;
+    t = std::min(512, ((ns + 2 * 32 - 1) / (2 * 32)) * 32);
+    s = (ns + t - 1) / t;
+  }
+  *threads = t;
+  *slots = s;
+}
+
+template <int K, int NW, int PL, int SLOTS>
+static void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads,
+                       int64_t n_sweeps) {
+  const size_t smem = bccfast::smem_bytes(D.nA);
+  check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
              "bcc sweep smem attribute");
-  const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
+  const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
+  const unsigned long long first = D.sweep;
   for (int64_t s = 0; s < n_sweeps; s++) {
-    P.sweep = hd->sweep_cum + (uint64_t)s;
-    for (int tc = 0; tc < 8; tc++) {
-      P.tc = tc;
-      bccfast::k_bcc_tile_sweep<K, NW, PL><<<grid, threads, smem, hd->stream>>>(P);
-    }
+    D.sweep = first + (unsigned long long)s;
+    for (int tc = 0; tc < 8; tc++)
+      bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS><<<grid, threads, smem, hd->stream>>>(D, Q, tc);
   }
   check_cuda(cudaGetLastError(), "bcc sweep launch");
 }
 
-template <int K>
-static void dispatch_planes(smcx_lattice* hd, bccfast::Params& P, int nw, int pl, int64_t n) {
-  if (nw == 1) {
-    if (pl == 1) launch_bcc<K, 1, 1>(hd, P, n);
-    else if (pl == 2) launch_bcc<K, 1, 2>(hd, P, n);
-    else launch_bcc<K, 1, 3>(hd, P, n);
-  } else {
-    if (pl == 1) launch_bcc<K, 2, 1>(hd, P, n);
-    else if (pl == 2) launch_bcc<K, 2, 2>(hd, P, n);
-    else launch_bcc<K, 2, 3>(hd, P, n);
+static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int nw, int pl,
+                     int threads, int slots, int64_t n) {
+  const int K = hd->shells.K;
+  if (K == 4) {
+    if (nw == 1 && pl == 2 && slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n);
+    if (nw == 1 && pl == 2) return launch_bcc<4, 1, 2, 2>(hd, D, Q, threads, n);
+    if (nw == 1 && slots == 1) return launch_bcc<4, 1, 3, 1>(hd, D, Q, threads, n);
+    if (nw == 1) return launch_bcc<4, 1, 3, 2>(hd, D, Q, threads, n);
+    if (pl == 2 && slots == 1) return launch_bcc<4, 2, 2, 1>(hd, D, Q, threads, n);
+    if (pl == 2) return launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n);
+    if (slots == 1) return launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n);
+    return launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n);
   }
+  // fewer shells: one general variant each (any M <= 8, three planes)
+  if (slots != 1) fail(SMCX_E_UNSUPPORTED, "block shape");
+  if (K == 3) return launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n);
+  if (K == 2) return launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n);
+  return launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n);
 }
 
 void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
-  bccfast::Params P;
-  memset(&P, 0, sizeof(P));
+  bccfast::LatDesc D;
+  memset(&D, 0, sizeof(D));
   const smcx_sched& sc = hd->sched;
-  P.sites = hd->d_sites;
-  P.thr = hd->d_thr;
-  P.stats = hd->d_stats;
-  int nq = 0;
+  D.sites = hd->d_sites;
+  D.thr = hd->d_thr;
+  D.stats = hd->d_stats;
   for (int a = 0; a < 3; a++) {
-    P.n[a] = hd->n[a];
-    P.nt[a] = sc.nt[a];
-    P.ntc[a] = sc.nt[a] / 2;
-    nq = std::max(nq, ((hd->n[a] + sc.nt[a] - 1) / sc.nt[a] + sc.L - 1) / sc.L);
+    D.n[a] = hd->n[a];
+    D.nt[a] = sc.nt[a];
   }
-  P.L = sc.L;
-  P.NQ = nq;
-  P.nA = nA;
-  P.storage = hd->storage;
-  P.replica = 0;
-  P.seed_lo = (uint32_t)seed;
-  P.seed_hi = (uint32_t)(seed >> 32);
-  // byte planes of V: the fewest planes that hold every entry
-  const int K = hd->shells.K, M = hd->M;
-  long long vmax = 0;
-  for (int32_t v : hd->V) vmax = std::max(vmax, std::llabs((long long)v));
-  const int PL = vmax < 128 ? 1 : (vmax < 32768 ? 2 : 3);
-  for (int k = 0; k < K; k++)
-    for (int p = 0; p < M; p++)
-      for (int c = 0; c < M; c++) {
-        const int32_t v = hd->V[((size_t)k * M + p) * M + c];
-        const int w = c / 4, sh = 8 * (c % 4);
-        uint32_t bytes[3];
-        if (PL == 1) {
-          bytes[0] = (uint32_t)(v & 0xFF);
-        } else {
-          bytes[0] = (uint32_t)v & 0xFFu;
-          bytes[1] = ((uint32_t)v >> 8) & 0xFFu;
-          bytes[2] = ((uint32_t)v >> 16) & 0xFFu;
-        }
-        for (int j = 0; j < PL; j++) P.P[j][k][p][w] |= bytes[j] << sh;
-      }
-  const int nw = M <= 4 ? 1 : 2;
-  switch (K) {
-    case 1: dispatch_planes<1>(hd, P, nw, PL, n_sweeps); break;
-    case 2: dispatch_planes<2>(hd, P, nw, PL, n_sweeps); break;
-    case 3: dispatch_planes<3>(hd, P, nw, PL, n_sweeps); break;
-    case 4: dispatch_planes<4>(hd, P, nw, PL, n_sweeps); break;
-    default: fail(SMCX_E_UNSUPPORTED, "shell count");
+  D.L = sc.L;
+  D.NQ = bcc_slots_per_axis(hd->n, sc);
+  D.nA = nA;
+  D.storage = hd->storage;
+  D.replica = hd->replica;
+  D.seed_lo = (uint32_t)seed;
+  D.seed_hi = (uint32_t)(seed >> 32);
+  D.sweep = hd->sweep_cum;
+  bccfast::Planes Q;
+  // fewer than 4 shells: one general variant (three planes, two words)
+  const int PL = build_planes(hd, &Q, hd->shells.K == 4 ? 2 : 3);
+  const int nw = hd->M <= 4 ? 1 : 2;
+  int threads, slots;
+  bcc_block_shape(D.NQ, hd->bcc_threads, &threads, &slots);
+  if (hd->shells.K != 4) {
+    bcc_block_shape(D.NQ, 0, &threads, &slots);
+    if (slots != 1) fail(SMCX_E_UNSUPPORTED, "tile too large for the fewer-shell kernel");
   }
+  dispatch(hd, D, Q, hd->shells.K == 4 ? nw : 2, PL, threads, slots, n_sweeps);
 }
 
 }  // namespace smcx

@@ -43,6 +43,15 @@ _SIGS = {
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
     "smcx_set_epi": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "smcx_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
+    "smcx_set_replica": (C.c_int, [C.c_void_p, C.c_int]),
+    "smcx_set_block": (C.c_int, [C.c_void_p, C.c_int]),
+    "smcx_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_batch_destroy": (C.c_int, [C.c_void_p]),
+    "smcx_batch_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64]),
+    "smcx_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "smcx_batch_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smcx_batch_set_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "smcx_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64]),
@@ -165,6 +174,12 @@ class Lattice:
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))
 
+    def set_replica(self, r):
+        _check(lib().smcx_set_replica(self._h, int(r)))
+
+    def set_block(self, threads):
+        _check(lib().smcx_set_block(self._h, int(threads)))
+
     def set_schedule(self, sched):
         if sched is None:
             _check(lib().smcx_set_schedule(self._h, None))
@@ -232,3 +247,50 @@ class Lattice:
 
     def synchronize(self):
         _check(lib().smcx_synchronize(self._h))
+
+
+class Batch:
+    """Replicas swept together in one persistent launch (smcx_batch).  Holds
+    references to the Lattice objects so they outlive the batch."""
+
+    def __init__(self, lattices, stream=None):
+        self.lattices = list(lattices)
+        arr = (C.c_void_p * len(self.lattices))(*[l._h.value for l in self.lattices])
+        h = C.c_void_p()
+        _check(lib().smcx_batch_create(C.byref(h), len(self.lattices), arr, _stream_ptr(stream)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().smcx_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, T, n_sweeps, seed):
+        T = np.ascontiguousarray(T, np.float64)
+        assert T.size == len(self.lattices)
+        _check(lib().smcx_batch_sweep(self._h, _p(T), int(n_sweeps), int(seed)))
+
+    def autotune(self, T, trial_sweeps=2):
+        T = np.ascontiguousarray(T, np.float64)
+        th = np.zeros(1, np.int32)
+        _check(lib().smcx_batch_autotune(self._h, _p(T), int(trial_sweeps), _p(th)))
+        return int(th[0])
+
+    def energy(self):
+        e = np.zeros(len(self.lattices), np.int64)
+        _check(lib().smcx_batch_energy(self._h, _p(e)))
+        return e
+
+    def info(self):
+        v = np.zeros(3, np.int32)
+        _check(lib().smcx_batch_info(self._h, _p(v[0:]), _p(v[1:]), _p(v[2:])))
+        return {"grid": int(v[0]), "threads": int(v[1]), "graph": bool(v[2])}
+
+    def set_fault(self, skip_cta, timeout_ms):
+        _check(lib().smcx_batch_set_fault(self._h, int(skip_cta), int(timeout_ms)))

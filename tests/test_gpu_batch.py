@@ -1,0 +1,105 @@
+"""Batched replicas in one persistent launch versus one-replica-per-launch
+sweeps and the oracle (temperature parallelism: Supplementary
+"Parallelization opportunities").  Configurations and trial statistics must
+match bit for bit."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_12591_gb300 import smcx
+from paper_2503_12591_gb300.inputs import epi_gaussian, log_temperatures
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DIMS = [(12, 12, 12), (24, 14, 16), (13, 20, 18), (30, 30, 26), (16, 24, 12), (40, 12, 20)]
+
+
+def _sched(dims, L=3, target=20):
+    nt = []
+    for n in dims:
+        t = 2
+        while (n + t - 1) // t > target:
+            t += 2
+        nt.append(t)
+    return (L, tuple(nt))
+
+
+def _make(dims, r, V, stream, sched, storage=smcx.PACKED4):
+    lat = smcx.Lattice(smcx.BCC, dims, 4, [0.25] * 4, init_seed=100 + r, storage=storage, sched=sched,
+                       stream=stream)
+    lat.set_replica(r)
+    lat.set_epi(V)
+    return lat
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.current_stream()
+
+
+def test_batch_equals_plain_and_oracle(stream):
+    V = epi_gaussian(4, 4, 20.0, 1)
+    T = log_temperatures(len(DIMS), 300.0, 3000.0)
+    scheds = [_sched(d, L=3 + (i % 2)) for i, d in enumerate(DIMS)]
+    batch_lat = [_make(d, r, V, stream, scheds[r]) for r, d in enumerate(DIMS)]
+    b = smcx.Batch(batch_lat, stream)
+    b.sweep(T, 3, 7)
+    b.sweep(T, 2, 7)  # second call replays the captured graph
+    info = b.info()
+    assert info["grid"] > 0 and info["threads"] > 0
+    for r, d in enumerate(DIMS):
+        plain = _make(d, r, V, stream, scheds[r], storage=smcx.INT8)
+        plain.sweep(T[r], 5, 7)
+        got = batch_lat[r].get_config()
+        assert (got == plain.get_config()).all(), f"replica {r} differs from its plain run"
+        assert batch_lat[r].state()[1].tolist() == plain.state()[1].tolist()
+        assert batch_lat[r].state()[0] == 5
+        if r < 3:
+            ref = O.init_config(O.BCC, d, 4, [0.25] * 4, 100 + r)
+            st = O.sweep(O.BCC, d, 4, 4, V, ref, T[r], 5, 7, replica=r, L=scheds[r][0], nt=scheds[r][1])
+            assert (got == ref).all()
+            assert batch_lat[r].state()[1].tolist() == st.tolist()
+    E = b.energy()
+    assert E.tolist() == [l.energy() for l in batch_lat]
+    b.close()
+
+
+def test_batch_autotune_then_oracle(stream):
+    V = epi_gaussian(4, 4, 20.0, 2)
+    dims = DIMS[:4]
+    T = log_temperatures(len(dims), 500.0, 2500.0)
+    lats = [_make(d, r, V, stream, _sched(d)) for r, d in enumerate(dims)]
+    before = [l.get_config() for l in lats]
+    b = smcx.Batch(lats, stream)
+    threads = b.autotune(T, trial_sweeps=1)
+    assert threads >= 0
+    for l, c in zip(lats, before):  # the autotuner restores the configurations
+        assert (l.get_config() == c).all()
+        assert l.state()[0] == 0
+    b.sweep(T, 3, 11)
+    for r, (l, d) in enumerate(zip(lats, dims)):
+        L, nt = l.schedule()
+        ref = O.init_config(O.BCC, d, 4, [0.25] * 4, 100 + r)
+        O.sweep(O.BCC, d, 4, 4, V, ref, T[r], 3, 11, replica=r, L=L, nt=nt)
+        assert (l.get_config() == ref).all(), f"replica {r} schedule {(L, nt)}"
+    b.close()
+
+
+def test_batch_barrier_timeout_reports_and_recovers(stream):
+    """A CTA that never arrives at the grid barrier: the other CTAs give up
+    after the time limit, the call returns SMCX_E_TIMEOUT, and the context
+    keeps working."""
+    V = epi_gaussian(4, 4, 20.0, 3)
+    lats = [_make(d, r, V, stream, _sched(d)) for r, d in enumerate(DIMS[:3])]
+    b = smcx.Batch(lats, stream)
+    b.set_fault(0, 200)
+    with pytest.raises(smcx.SmcxError) as e:
+        b.sweep([1000.0] * 3, 2, 1)
+    assert e.value.code == smcx.E_TIMEOUT
+    b.set_fault(-1, 2000)
+    b.sweep([1000.0] * 3, 1, 1)
+    torch.cuda.synchronize()
+    assert lats[0].energy() == lats[0].energy()
+    b.close()
