@@ -264,6 +264,40 @@ int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_grap
 int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
 
 /*
+ * Differentiation (all pointers are device pointers owned by the caller;
+ * work is enqueued on `stream`, nothing is synchronised).
+ *
+ * The pair energy is linear in V (Eq. Total_EPI): E = 1/2 sum V_i C_i, so
+ * dE/dV_i = C_i / 2 -- the backward pass of fitting V to reference energies
+ * by back-propagation (Results "Energy model").
+ *   smcx_pair_counts_batch  C[B][K][M][M] (int64) of B configurations of one
+ *                           geometry (int8 ids [B][N], canonical order; N up
+ *                           to ~200k sites).
+ *   smcx_epi_energy_batch   E[b] = 1/2 sum_i V[i] C[b][i] (float V, FP64 sum,
+ *                           float E), KMM = K*M*M.
+ *   smcx_epi_grad_batch     grad[i] = 1/2 sum_b g[b] C[b][i] (float).
+ * Thermal derivative of an observable A (Supplementary "Statistical
+ * mechanics": <O> under exp(-beta E)):
+ *   d<A>/dV_i = -beta (<A C_i/2> - <A><C_i/2>),  beta = 1 / (k_B T) in 1/meV.
+ *   smcx_fluct_accumulate   adds B weighted samples (weights d_weights[B], or
+ *                           1 when NULL) of A = the Warren-Cowley alpha of
+ *                           shell `shell` (M*M) and C to d_acc (FP64),
+ *                           layout [1 + MM + KMM + MM*KMM]: sum w, sum w A,
+ *                           sum w C, sum w A C^T (row-major [a][i]).
+ *   smcx_lattice_fluct_accumulate  one sample (weight 1) of the handle's
+ *                           current configuration, on the handle's stream.
+ *   smcx_fluct_gradient     grad[MM][KMM] = d<A_a>/dV_i in 1/meV from d_acc.
+ */
+int smcx_pair_counts_batch(int kind, int nx, int ny, int nz, int M, int K, const int8_t* d_configs, int64_t B,
+                           int64_t* d_counts, void* stream);
+int smcx_epi_energy_batch(const float* d_V, const int64_t* d_counts, int64_t B, int KMM, float* d_E, void* stream);
+int smcx_epi_grad_batch(const float* d_g, const int64_t* d_counts, int64_t B, int KMM, float* d_grad, void* stream);
+int smcx_fluct_accumulate(const int64_t* d_counts, int64_t B, const double* d_weights, int kind, int K, int M,
+                          int shell, int64_t n_sites, double* d_acc, void* stream);
+int smcx_lattice_fluct_accumulate(smcx_lattice* h, int shell, double* d_acc);
+int smcx_fluct_gradient(const double* d_acc, int K, int M, double T, double* d_grad, void* stream);
+
+/*
  * Energy of a device-resident configuration without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that may
  * not call cudaMalloc -- code that runs inside another framework's memory

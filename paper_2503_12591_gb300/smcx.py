@@ -67,6 +67,13 @@ _SIGS = {
     "smcx_lattice_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "smcx_threshold_tables": (C.c_int, [C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smcx_pair_counts_batch": (C.c_int, [C.c_int] * 6 + [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "smcx_epi_energy_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_epi_grad_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_fluct_accumulate": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int64, C.c_void_p, C.c_void_p]),
+    "smcx_lattice_fluct_accumulate": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "smcx_fluct_gradient": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "smcx_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -248,6 +255,9 @@ class Lattice:
     def synchronize(self):
         _check(lib().smcx_synchronize(self._h))
 
+    def fluct_accumulate(self, shell, d_acc_ptr):
+        _check(lib().smcx_lattice_fluct_accumulate(self._h, int(shell), C.c_void_p(int(d_acc_ptr))))
+
 
 class Batch:
     """Replicas swept together in one persistent launch (smcx_batch).  Holds
@@ -294,3 +304,32 @@ class Batch:
 
     def set_fault(self, skip_cta, timeout_ms):
         _check(lib().smcx_batch_set_fault(self._h, int(skip_cta), int(timeout_ms)))
+
+
+# ---- differentiation (device pointers; enqueued on `stream`) -------------
+def pair_counts_batch(kind, dims, M, K, d_configs, B, d_counts, stream=None):
+    _check(lib().smcx_pair_counts_batch(int(kind), *[int(d) for d in dims], int(M), int(K),
+                                        C.c_void_p(int(d_configs)), int(B), C.c_void_p(int(d_counts)),
+                                        _stream_ptr(stream)))
+
+
+def epi_energy_batch(d_V, d_counts, B, KMM, d_E, stream=None):
+    _check(lib().smcx_epi_energy_batch(C.c_void_p(int(d_V)), C.c_void_p(int(d_counts)), int(B), int(KMM),
+                                       C.c_void_p(int(d_E)), _stream_ptr(stream)))
+
+
+def epi_grad_batch(d_g, d_counts, B, KMM, d_grad, stream=None):
+    _check(lib().smcx_epi_grad_batch(C.c_void_p(int(d_g)), C.c_void_p(int(d_counts)), int(B), int(KMM),
+                                     C.c_void_p(int(d_grad)), _stream_ptr(stream)))
+
+
+def fluct_accumulate(d_counts, B, d_weights, kind, K, M, shell, n_sites, d_acc, stream=None):
+    _check(lib().smcx_fluct_accumulate(C.c_void_p(int(d_counts)), int(B),
+                                       C.c_void_p(int(d_weights)) if d_weights else None, int(kind), int(K),
+                                       int(M), int(shell), int(n_sites), C.c_void_p(int(d_acc)),
+                                       _stream_ptr(stream)))
+
+
+def fluct_gradient(d_acc, K, M, T, d_grad, stream=None):
+    _check(lib().smcx_fluct_gradient(C.c_void_p(int(d_acc)), int(K), int(M), float(T), C.c_void_p(int(d_grad)),
+                                     _stream_ptr(stream)))
