@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -253,6 +254,128 @@ def run_batched(stream):
                         "T log-spaced 300-3000 K, int8 storage"}
 
 
+def run_gradient(stream):
+    """Differentiation workloads.  (a) EPI fit: 4096 equiatomic BCC 8^3
+    configurations (1024 sites, seed = index), hidden 4-shell EPI N(0,20 meV)
+    (seed 7), FP32 per-site targets + N(0,1 meV) noise; pair counts batched
+    vs one configuration per launch, then forward + backward + Adam steps.
+    (b) Fluctuation gradient d<alpha_1>/dV: 64 replicas of BCC 48^3 at
+    1000 K, 2000 sweeps (500 burn-in), FP64 accumulation after every sweep,
+    against the same sweeps without accumulation."""
+    import torch
+    from paper_2503_12591_gb300 import diff, smcx
+
+    dev = torch.device("cuda")
+    out = {}
+    # (a) fitting step
+    B, dims, M, K = 4096, (8, 8, 8), 4, 4
+    N = 2 * 8 ** 3
+    rng_cfg = [np.random.default_rng(b).permutation(np.repeat(np.arange(M), N // M)) for b in range(B)]
+    cfg = torch.from_numpy(np.stack(rng_cfg).astype(np.int8)).to(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    C = diff.pair_counts(cfg, smcx.BCC, dims, M, K)
+    e0.record(stream)
+    C = diff.pair_counts(cfg, smcx.BCC, dims, M, K)
+    e1.record(stream)
+    e1.synchronize()
+    ms_batched = e0.elapsed_time(e1)
+    Cp = torch.empty_like(C)
+    e0.record(stream)
+    for b in range(B):
+        smcx.pair_counts_batch(smcx.BCC, dims, M, K, cfg[b].data_ptr(), 1, Cp[b].data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    exact = bool(torch.equal(C, Cp))
+    Vh = torch.tensor(epi_gaussian(K, M, 20.0, 7), dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    with torch.no_grad():
+        target = diff.epi_energy(Vh, C) / N / 100.0 + torch.randn(B, device=dev, generator=gen)
+    W = torch.zeros((K, M, M), device=dev, requires_grad=True)
+    opt = torch.optim.Adam([W], lr=5.0)
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        V = 0.5 * (W + W.transpose(1, 2))
+        pred = diff.epi_energy(V * 100.0, C) / N / 100.0
+        loss = torch.mean((pred - target) ** 2)
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(3):
+        step()
+    n_steps = 50
+    e0.record(stream)
+    for _ in range(n_steps):
+        loss = step()
+    e1.record(stream)
+    e1.synchronize()
+    ms_fit = e0.elapsed_time(e1) / n_steps
+    out["fit"] = {"configs_per_s_pair_counts_batched": B / (ms_batched / 1e3),
+                  "configs_per_s_pair_counts_plain": B / (ms_plain / 1e3),
+                  "speedup_vs_plain": ms_plain / ms_batched, "bit_exact_vs_plain": exact,
+                  "fit_step_ms": ms_fit, "fit_configs_per_s": B / (ms_fit / 1e3),
+                  "final_loss_meV2": float(loss.item()),
+                  "plain": "one configuration per smcx_pair_counts_batch launch",
+                  "workload": "4096 BCC 8^3 configs x 1024 sites, 4 species, 4-shell EPI fit (Adam)"}
+    # (b) fluctuation gradient
+    R, n, T, burn, total = 64, 48, 1000.0, 500, 2000
+    V = epi_gaussian(4, 4, 20.0, 1)
+
+    def make_set():
+        lats = []
+        for r in range(R):
+            l = smcx.Lattice(smcx.BCC, (n, n, n), 4, equiatomic(4), init_seed=500 + r, storage=smcx.INT8,
+                             stream=stream)
+            l.set_replica(r)
+            l.set_epi(V)
+            lats.append(l)
+        return lats
+
+    Ts = [T] * R
+    lats = make_set()
+    b = smcx.Batch(lats, stream)
+    b.sweep(Ts, burn, SEED)
+    ests = [diff.FluctuationEstimator(smcx.BCC, 4, 4, 0, l.N) for l in lats]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(total - burn):
+        b.sweep(Ts, 1, SEED)
+        for l, est in zip(lats, ests):
+            est.add_lattice(l)
+    torch.cuda.synchronize()
+    s_acc = time.perf_counter() - t0
+    grads = torch.stack([e.gradient(T) for e in ests])
+    g_mean = grads.mean(0)
+    g_se = grads.std(0) / np.sqrt(R)
+    b.close()
+    lats2 = make_set()
+    b2 = smcx.Batch(lats2, stream)
+    b2.sweep(Ts, burn, SEED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(total - burn):
+        b2.sweep(Ts, 1, SEED)
+    torch.cuda.synchronize()
+    s_plain = time.perf_counter() - t0
+    same = all((l.get_config() == l2.get_config()).all() for l, l2 in zip(lats, lats2))
+    b2.close()
+    for l in lats + lats2:
+        l.close()
+    k01 = g_mean[1, 0, 0, 1].item() + g_mean[1, 0, 1, 0].item()
+    out["fluctuation"] = {"sweeps_per_s_with_accumulation": (total - burn) / s_acc,
+                          "sweeps_per_s_without": (total - burn) / s_plain,
+                          "overhead": s_acc / s_plain,
+                          "configs_identical_with_and_without": bool(same),
+                          "dalpha1_AB_dV1_AB_per_meV": k01,
+                          "max_rel_stderr": float((g_se.abs() / g_mean.abs().clamp_min(1e-12)).median()),
+                          "workload": "64 x BCC 48^3, 1000 K, 2000 sweeps (500 burn-in), d<alpha_1>/dV FP64, "
+                                      "measured after every sweep; batched sweeps one call per sweep"}
+    return out
+
+
 def run_smcx(args, rank, world, local_rank):
     import torch
 
@@ -322,9 +445,17 @@ def run_smcx(args, rank, world, local_rank):
         if dist is not None:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dt = float(tt.item())
+        # breakdown of one e2e step
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat.set_config_ptr(host.data_ptr())
+        t2 = time.perf_counter()
+        lat.energy()
+        t3 = time.perf_counter()
         e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": WORK.sites,
                "d2h_bytes_per_step": 8, "steps": ne,
-               "step": "smcx_set_config (int8 ids, pinned host) + smcx_sweep (1 sweep) + smcx_energy"}
+               "step": "smcx_set_config (int8 ids, pinned host) + smcx_sweep (1 sweep) + smcx_energy",
+               "ms_set_config": (t2 - t1) * 1e3, "ms_energy": (t3 - t2) * 1e3}
         del host
 
     if rank != 0:
@@ -367,6 +498,8 @@ def run_smcx(args, rank, world, local_rank):
         out["e2e"] = e2e
     if not args.no_batched and world == 1:
         out["batched"] = run_batched(stream)
+    if not args.no_grad and world == 1:
+        out["gradient"] = run_gradient(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -90,6 +90,11 @@ void pair_counts_device(smcx_lattice* hd) {
   fill_offsets_global(hd, P);
   const int KMM = hd->shells.K * hd->M * hd->M;
   check_cuda(cudaMemsetAsync(hd->d_counts, 0, KMM * sizeof(unsigned long long), hd->stream), "memset counts");
+  int nt[3];
+  if (hd->kernel_choice != SMCX_KERNEL_GENERIC && bcc_counts_usable(hd, nt)) {
+    pair_counts_bcc_tiled(hd, nt);
+    return;
+  }
   const int K = hd->shells.K;
   if (hd->kind == kBCC) {
     switch (K) {

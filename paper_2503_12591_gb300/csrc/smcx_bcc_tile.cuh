@@ -52,6 +52,7 @@ struct LatDesc {
   int nA, storage, replica;
   uint32_t seed_lo, seed_hi;
   unsigned long long sweep;     // cumulative index of the first sweep of the call
+  int M;                        // species count (pair counting)
 };
 
 // 50 BCC neighbour vectors (half units) of shells 1..4 with their shell.

@@ -138,6 +138,8 @@ void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
 void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
 void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
 bool bcc_fast_usable(const smcx_lattice* h);
+bool bcc_counts_usable(const smcx_lattice* h, int nt[3]);
+void pair_counts_bcc_tiled(smcx_lattice* h, const int nt[3]);
 int bcc_slots_per_axis(const int n[3], const smcx_sched& sc);
 void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots);
 void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);

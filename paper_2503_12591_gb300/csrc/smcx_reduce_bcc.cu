@@ -1,0 +1,165 @@
+// Ordered pair counts of a BCC lattice (M <= 4) from shared-memory tiles.
+//
+// Same result as k_pair_counts (smcx_aux.cu): C[k][p][q] = number of (site
+// i, shell-k vector v) with s_i = p and s_{i+v} = q.  Each CTA stages one
+// tile plus its 2-cell halo exactly as the sweep does, and for every site of
+// the tile adds 1 << (8 s_{i+v}) over the shell-k vectors into a byte-packed
+// register, which is split into two 16-bit-field accumulators per (shell,
+// centre species).  At the end the warp sums each accumulator with a
+// reduce-add, lane 0 adds the unpacked counts to a shared histogram, and the
+// CTA adds that to the global int64 histogram.
+#include "smcx_bcc_tile.cuh"
+
+namespace smcx {
+
+namespace bccfast {
+
+template <int K>
+__global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int hist[kMaxShells * 16];
+  uint8_t* box = smem;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int ntx = D.nt[0], nty = D.nt[1];
+  const int t = blockIdx.x;
+  const int ti[3] = {t % ntx, (t / ntx) % nty, t / (ntx * nty)};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = D.n[a] / D.nt[a], rem = D.n[a] % D.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+  for (int i = tid; i < kMaxShells * 16; i += nth) hist[i] = 0;
+  constexpr int h = 2;
+  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  for (int row = warp; row < ey * ez; row += nwarp) {
+    const int ys = row % ey, zs = row / ey;
+    const int gy = wrap_add(t0[1] - h, ys, ny), gz = wrap_add(t0[2] - h, zs, nz);
+    const long long rbase = ((long long)gz * ny + gy) * nx;
+    for (int xs = lane; xs < ex; xs += 32) {
+      const long long cell = rbase + wrap_add(t0[0] - h, xs, nx);
+      uint32_t s0, s1;
+      if (D.storage == SMCX_INT8) {
+        s0 = D.sites[2 * cell];
+        s1 = D.sites[2 * cell + 1];
+      } else {
+        const uint32_t byte = D.sites[cell];
+        s0 = byte & 15u;
+        s1 = byte >> 4;
+      }
+      const int bi = (zs * PY + ys) * PX + xs;
+      box[bi] = (uint8_t)(s0 << 3);
+      box[SUB + bi] = (uint8_t)(s1 << 3);
+    }
+  }
+  __syncthreads();
+
+  // acc[k][p][0] holds bytes 0 and 2 of the per-site counters, acc[k][p][1]
+  // bytes 1 and 3, each in a 16-bit field (no overflow below 2700 sites)
+  uint32_t acc[K][4][2];
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int p = 0; p < 4; p++) acc[k][p][0] = acc[k][p][1] = 0;
+  const int ncell = ts[0] * ts[1] * ts[2];
+  constexpr VecTable T = make_vecs();
+  for (int c = tid; c < ncell; c += nth) {
+    const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
+    const int s0 = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+#pragma unroll
+    for (int B = 0; B < 2; B++) {
+      const int s = s0 + B * SUB;
+      const int p = box[s] >> 3;
+      uint32_t hk[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) hk[k] = 0;
+#pragma unroll
+      for (int j = 0; j < T.n; j++) {
+        const int k = T.v[j].k;
+        if (k >= K) continue;
+        const int off = B == 0 ? nb_offset(0, T.v[j].x, T.v[j].y, T.v[j].z) : nb_offset(1, T.v[j].x, T.v[j].y, T.v[j].z);
+        hk[k] += 1u << box[s + off];
+      }
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        const uint32_t lo = hk[k] & 0x00FF00FFu, hi = (hk[k] >> 8) & 0x00FF00FFu;
+#pragma unroll
+        for (int pp = 0; pp < 4; pp++)
+          if (p == pp) {
+            acc[k][pp][0] += lo;
+            acc[k][pp][1] += hi;
+          }
+      }
+    }
+  }
+  // warp sums (16-bit fields: at most 32 lanes x 32 cells x 2 sites x 24 = 49152 per field)
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+      for (int w = 0; w < 2; w++) {
+        const uint32_t v = __reduce_add_sync(0xffffffffu, acc[k][p][w]);
+        if (lane == 0) {
+          // field 0 -> species q = w, field 1 -> species q = w + 2
+          atomicAdd(&hist[(k * 4 + p) * 4 + w], v & 0xFFFFu);
+          atomicAdd(&hist[(k * 4 + p) * 4 + w + 2], v >> 16);
+        }
+      }
+  __syncthreads();
+  for (int i = tid; i < K * 16; i += nth) {
+    const int k = i / 16, p = (i / 4) % 4, q = i % 4;
+    if (p < D.M && q < D.M && hist[i]) atomicAdd(&counts[(k * D.M + p) * D.M + q], (unsigned long long)hist[i]);
+  }
+}
+
+}  // namespace bccfast
+
+// Usable for BCC, M <= 4, tiles (of the handle's schedule, or a default
+// tiling) that fit the 24^3 box.
+bool bcc_counts_usable(const smcx_lattice* hd, int nt[3]) {
+  if (hd->kind != kBCC || hd->M > 4 || !hd->have_epi) return false;
+  const smcx_sched& sc = hd->sched;
+  for (int a = 0; a < 3; a++) {
+    int t = (sc.L != 0 && sc.nt[a] >= 2) ? sc.nt[a] : std::max(1, (hd->n[a] + 19) / 20);
+    while ((hd->n[a] + t - 1) / t > 20) t++;
+    if (hd->n[a] / t < 1) return false;
+    nt[a] = t;
+    if ((hd->n[a] + t - 1) / t + 4 > bccfast::BOX) return false;
+  }
+  // a tile covering a whole axis would wrap its own halo: the generic kernel
+  // handles those small lattices
+  for (int a = 0; a < 3; a++)
+    if (nt[a] < 2 || hd->n[a] < 6) return false;
+  return true;
+}
+
+void pair_counts_bcc_tiled(smcx_lattice* hd, const int nt[3]) {
+  bccfast::LatDesc D;
+  memset(&D, 0, sizeof(D));
+  D.sites = hd->d_sites;
+  D.storage = hd->storage;
+  D.M = hd->M;
+  for (int a = 0; a < 3; a++) {
+    D.n[a] = hd->n[a];
+    D.nt[a] = nt[a];
+  }
+  const int grid = nt[0] * nt[1] * nt[2];
+  const size_t smem = 2 * bccfast::SUB;
+  auto go = [&](auto kern) {
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+    kern<<<grid, 256, smem, hd->stream>>>(D, hd->d_counts);
+  };
+  switch (hd->shells.K) {
+    case 1: go(bccfast::k_bcc_pair_counts<1>); break;
+    case 2: go(bccfast::k_bcc_pair_counts<2>); break;
+    case 3: go(bccfast::k_bcc_pair_counts<3>); break;
+    default: go(bccfast::k_bcc_pair_counts<4>); break;
+  }
+  check_cuda(cudaGetLastError(), "tiled pair-count launch");
+}
+
+}  // namespace smcx

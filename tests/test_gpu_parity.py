@@ -43,16 +43,20 @@ def test_initial_configuration(stream, kind, dims, M, comp, storage):
     assert (got == ref).all()
 
 
+@pytest.mark.parametrize("kernel", [smcx.KERNEL_AUTO, smcx.KERNEL_GENERIC], ids=["auto", "generic"])
 @pytest.mark.parametrize("kind,K,dims,M,storage", [
     (smcx.BCC, 4, (8, 6, 10), 4, smcx.INT8),
     (smcx.BCC, 2, (6, 6, 6), 3, smcx.PACKED4),
+    (smcx.BCC, 4, (45, 38, 41), 4, smcx.PACKED4),
+    (smcx.BCC, 3, (21, 7, 26), 2, smcx.INT8),
     (smcx.FCC, 3, (6, 8, 6), 5, smcx.PACKED4),
 ])
-def test_energy_pair_counts_sro(stream, kind, K, dims, M, storage):
+def test_energy_pair_counts_sro(stream, kind, K, dims, M, storage, kernel):
     N = O.n_sites(kind, dims)
     cfg = np.random.default_rng(5).integers(0, M, N).astype(np.int8)
     V = epi_gaussian(K, M, 20.0, 3)
     lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, storage=storage, stream=stream)
+    lat.set_kernel(kernel)
     lat.set_epi(V)
     lat.set_config(cfg)
     assert (lat.get_config() == cfg).all()
