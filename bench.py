@@ -485,7 +485,7 @@ def run_smcx(args, rank, world, local_rank):
                                 "parallelism": f"replicas x{world}" if world > 1 else "single lattice"}),
         "roofline": {"bound": "alu", "achieved": achieved_g, "peak": lds_peak, "unit": "Gload/s",
                      "frac": achieved_g / lds_peak, "traffic": traffic,
-                     "kernel": "k_tile_sweep",
+                     "kernel": "k_bcc_tile_sweep",
                      "note": "shared-memory gather roof: 70 lane-loads per trial (s, s' and 68 distinct "
                              "neighbours) against 152 SMs x 32 lanes x 2070 MHz"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
