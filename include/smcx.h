@@ -181,6 +181,14 @@ int smcx_get_schedule(const smcx_lattice* h, smcx_sched* out);
  */
 int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed);
 
+/* Verification hook: run tile colours 0..n_colours-1 (0..8) of sweep number
+ * `cumulative sweep index` without advancing the index, i.e. the first part
+ * of the next smcx_sweep.  Tiles of one colour never interact, so after one
+ * colour every tile of colour 0 can be compared with an independent
+ * single-tile computation even on a lattice too large to sweep elsewhere.
+ * Needs a tiled schedule (SMCX_E_UNSUPPORTED for the link-cell schedule). */
+int smcx_sweep_partial(smcx_lattice* h, double T, uint64_t seed, int n_colours);
+
 /* Exact total energy (0.01 meV units) of the current configuration. */
 int smcx_energy(smcx_lattice* h, int64_t* E);
 

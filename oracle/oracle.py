@@ -46,6 +46,8 @@ def lib():
         L.orc_threshold.restype = C.c_uint32
         L.orc_schedule_check.argtypes = [i32] * 9
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
+        L.orc_tile_pass.argtypes = [i32] * 6 + [vp, vp, dbl, u64, u64, i32] + [i32] * 7 + [vp]
+        L.orc_init_sample.argtypes = [i32] * 5 + [vp, u64, vp, i32, vp]
         L.orc_phase_of.argtypes = [i32] * 8 + [i64, vp]
         L.orc_phase_of.restype = i64
         _lib = L
@@ -179,3 +181,24 @@ def phase_of(kind, dims, L, nt, s):
     t = np.zeros(3, np.int32)
     ph = lib().orc_phase_of(kind, *dims, L, *nt, int(s), _p(t))
     return int(ph), tuple(int(x) for x in t)
+
+
+def tile_pass(kind, dims, M, K, V, sigma, T, seed, sweep, replica, L, nt, tile):
+    """Run every phase of one tile in place (see orc_tile_pass)."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    Vv = np.ascontiguousarray(V, np.int32)
+    st = np.zeros(4, np.int64)
+    rc = lib().orc_tile_pass(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(seed), int(sweep),
+                             int(replica), int(L), *[int(t) for t in nt], *[int(t) for t in tile], _p(st))
+    if rc:
+        raise ValueError(f"oracle tile pass rejected the request ({rc})")
+    return st
+
+
+def init_sample(kind, dims, M, comp, seed, ids):
+    ids = np.ascontiguousarray(ids, np.int64)
+    out = np.zeros(ids.size, np.int8)
+    c = np.ascontiguousarray(comp, np.float64)
+    if lib().orc_init_sample(kind, *dims, M, _p(c), int(seed), _p(ids), ids.size, _p(out)):
+        raise ValueError("init sample failed")
+    return out

@@ -558,6 +558,100 @@ static void attempt(attempt_ctx* c, int64_t s) {
   }
 }
 
+/* All intra-colour phases of ONE tile (tile indices tx, ty, tz) of sweep
+ * `sweep`: the part of the sweep loop below that belongs to this tile.  Tiles
+ * of one colour never interact, so on that tile (and its partner ring) the
+ * result equals the whole colour pass. */
+int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                  int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica,
+                  int L, int ntx, int nty, int ntz, int tx, int ty, int tz, int64_t* stats) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  if (orc_schedule_check(kind, nx, ny, nz, K, L, ntx, nty, ntz) || L == 0) return -2;
+  if (tx < 0 || tx >= ntx || ty < 0 || ty >= nty || tz < 0 || tz >= ntz) return -1;
+  uint32_t* A = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NA_MAX);
+  uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NB);
+  int nA;
+  if (!A || !B || orc_threshold_tables(T, A, &nA, B)) {
+    free(A);
+    free(B);
+    return -1;
+  }
+  attempt_ctx c;
+  c.kind = kind;
+  c.nx = nx;
+  c.ny = ny;
+  c.nz = nz;
+  c.m = m;
+  c.M = M;
+  c.S = &S;
+  c.V = V;
+  c.sigma = sigma;
+  c.A = A;
+  c.B = B;
+  c.nA = nA;
+  c.seed = seed;
+  c.replica = replica;
+  c.stats = stats;
+  c.sweep = sweep;
+  stats[0] = stats[1] = stats[2] = stats[3] = 0;
+  int x0, sx, y0, sy, z0, sz;
+  tile_bounds(nx, ntx, tx, &x0, &sx);
+  tile_bounds(ny, nty, ty, &y0, &sy);
+  tile_bounds(nz, ntz, tz, &z0, &sz);
+  for (int ic = 0; ic < L * L * L * m; ic++) {
+    int b = ic % m;
+    int cx = (ic / m) % L, cy = (ic / m / L) % L, cz = ic / m / L / L;
+    for (int z = z0 + cz; z < z0 + sz; z += L)
+      for (int y = y0 + cy; y < y0 + sy; y += L)
+        for (int x = x0 + cx; x < x0 + sx; x += L) attempt(&c, (((int64_t)z * ny + y) * nx + x) * m + b);
+  }
+  free(A);
+  free(B);
+  return 0;
+}
+
+/* Species of sampled sites in the initial configuration of a lattice too
+ * large to sort here: each sample's rank among all N keys (ties by id) is
+ * counted in one pass and mapped through the species counts. */
+int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp, uint64_t seed,
+                    const int64_t* ids, int n_ids, int8_t* out) {
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || n_ids < 1 || n_ids > 64) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t counts[ORC_MMAX];
+  if (orc_species_counts(M, comp, N, counts)) return -1;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint64_t skey[64];
+  int64_t rank[64];
+  for (int j = 0; j < n_ids; j++) {
+    uint32_t ctr[4] = {(uint32_t)ids[j], (uint32_t)((uint64_t)ids[j] >> 32), 0u, 0x80000000u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    skey[j] = ((uint64_t)o[0] << 32) | o[1];
+    rank[j] = 0;
+  }
+  for (int64_t i = 0; i < N; i++) {
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, 0x80000000u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    uint64_t k = ((uint64_t)o[0] << 32) | o[1];
+    for (int j = 0; j < n_ids; j++)
+      if (k < skey[j] || (k == skey[j] && i < ids[j])) rank[j]++;
+  }
+  for (int j = 0; j < n_ids; j++) {
+    int64_t r = rank[j], acc = 0;
+    int p = 0;
+    for (p = 0; p < M; p++) {
+      acc += counts[p];
+      if (r < acc) break;
+    }
+    out[j] = (int8_t)p;
+  }
+  return 0;
+}
+
 int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,

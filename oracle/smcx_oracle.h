@@ -98,6 +98,14 @@ int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
               int64_t* stats /*[4]: attempts, accepts, same-species,
                                  sum of accepted dE*/);
+/* All phases of one tile (tx, ty, tz) of sweep `sweep` (stats as orc_sweep). */
+int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                  int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica,
+                  int L, int ntx, int nty, int ntz, int tx, int ty, int tz, int64_t* stats);
+/* Initial species of up to 64 sampled sites of a lattice too large to sort
+ * (one pass over all N keys). */
+int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp, uint64_t seed,
+                    const int64_t* ids, int n_ids, int8_t* out);
 /* Phase id of a site under schedule (L, nt*): tile colour * nA + intra colour,
  * or -1 for the serial schedule.  Used by the independence test. */
 int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,

@@ -276,6 +276,19 @@ int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed) {
   });
 }
 
+int smcx_sweep_partial(smcx_lattice* h, double T, uint64_t seed, int n_colours) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi before smcx_sweep_partial");
+    need(h->sched.L != 0, SMCX_E_SCHEDULE, "no checkerboard schedule fits this lattice");
+    need(T > 0.0 && isfinite(T), SMCX_E_INVALID_ARG, "temperature must be finite and > 0");
+    need(n_colours >= 0 && n_colours <= 8, SMCX_E_INVALID_ARG, "n_colours must be in 0..8");
+    if (n_colours == 0) return;
+    upload_thresholds(h, T);
+    sweep_device(h, h->thr_nA, seed, 1, n_colours);
+  });
+}
+
 int smcx_pair_counts(smcx_lattice* h, int64_t* C) {
   return guarded([&] {
     need(h && C, SMCX_E_INVALID_ARG, "NULL argument");

@@ -136,13 +136,13 @@ void pack_from_int8(smcx_lattice* h, const int8_t* d_ids, int64_t first, int64_t
 void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count);
 void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
 void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
-void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
+void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours = 8);
 bool bcc_fast_usable(const smcx_lattice* h);
 bool bcc_counts_usable(const smcx_lattice* h, int nt[3]);
 void pair_counts_bcc_tiled(smcx_lattice* h, const int nt[3]);
 int bcc_slots_per_axis(const int n[3], const smcx_sched& sc);
 void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots);
-void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps);
+void sweep_bcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
 void species_counts(int M, const double* comp, int64_t N, int64_t* counts);
 
 struct SweepParams;

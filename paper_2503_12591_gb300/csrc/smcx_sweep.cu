@@ -306,10 +306,11 @@ static void fill_offsets(const smcx_lattice* hd, SweepParams& P, int BX, int BY)
 }
 
 template <int KIND, int K>
-static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps) {
+static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, int n_colours) {
   const smcx_sched& sc = hd->sched;
   cudaStream_t st = hd->stream;
   if (sc.nt[0] == 1 && sc.nt[1] == 1 && sc.nt[2] == 1) {
+    if (n_colours != 8) fail(SMCX_E_UNSUPPORTED, "partial sweeps need a tiled schedule");
     const long long nlc = (long long)(P.n[0] / sc.L) * (P.n[1] / sc.L) * (P.n[2] / sc.L);
     const int grid = (int)((nlc + 255) / 256);
     const int nic = sc.L * sc.L * sc.L * hd->m;
@@ -335,7 +336,7 @@ static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps) {
              "tile sweep smem attribute");
   for (int64_t s = 0; s < n_sweeps; s++) {
     P.sweep = hd->sweep_cum + (uint64_t)s;
-    for (int tc = 0; tc < 8; tc++) {
+    for (int tc = 0; tc < n_colours; tc++) {
       P.tc = tc;
       const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
       k_tile_sweep<KIND, K><<<grid, 256, smem, st>>>(P);
@@ -344,9 +345,9 @@ static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps) {
   check_cuda(cudaGetLastError(), "tile sweep launch");
 }
 
-void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
+void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
   if (hd->kernel_choice != 1 && bcc_fast_usable(hd)) {
-    sweep_bcc_fast(hd, nA, seed, n_sweeps);
+    sweep_bcc_fast(hd, nA, seed, n_sweeps, n_colours);
     return;
   }
   SweepParams P;
@@ -379,17 +380,17 @@ void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
   const int K = hd->shells.K;
   if (hd->kind == kBCC) {
     switch (K) {
-      case 1: launch_sweeps<kBCC, 1>(hd, P, n_sweeps); break;
-      case 2: launch_sweeps<kBCC, 2>(hd, P, n_sweeps); break;
-      case 3: launch_sweeps<kBCC, 3>(hd, P, n_sweeps); break;
-      case 4: launch_sweeps<kBCC, 4>(hd, P, n_sweeps); break;
+      case 1: launch_sweeps<kBCC, 1>(hd, P, n_sweeps, n_colours); break;
+      case 2: launch_sweeps<kBCC, 2>(hd, P, n_sweeps, n_colours); break;
+      case 3: launch_sweeps<kBCC, 3>(hd, P, n_sweeps, n_colours); break;
+      case 4: launch_sweeps<kBCC, 4>(hd, P, n_sweeps, n_colours); break;
       default: fail(SMCX_E_UNSUPPORTED, "shell count");
     }
   } else {
     switch (K) {
-      case 1: launch_sweeps<kFCC, 1>(hd, P, n_sweeps); break;
-      case 2: launch_sweeps<kFCC, 2>(hd, P, n_sweeps); break;
-      case 3: launch_sweeps<kFCC, 3>(hd, P, n_sweeps); break;
+      case 1: launch_sweeps<kFCC, 1>(hd, P, n_sweeps, n_colours); break;
+      case 2: launch_sweeps<kFCC, 2>(hd, P, n_sweeps, n_colours); break;
+      case 3: launch_sweeps<kFCC, 3>(hd, P, n_sweeps, n_colours); break;
       default: fail(SMCX_E_UNSUPPORTED, "shell count");
     }
   }

@@ -78,7 +78,7 @@ void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots) {
 
 template <int K, int NW, int PL, int SLOTS>
 static void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads,
-                       int64_t n_sweeps) {
+                       int64_t n_sweeps, int n_colours) {
   const size_t smem = bccfast::smem_bytes(D.nA);
   check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -87,33 +87,33 @@ static void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Pla
   const unsigned long long first = D.sweep;
   for (int64_t s = 0; s < n_sweeps; s++) {
     D.sweep = first + (unsigned long long)s;
-    for (int tc = 0; tc < 8; tc++)
+    for (int tc = 0; tc < n_colours; tc++)
       bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS><<<grid, threads, smem, hd->stream>>>(D, Q, tc);
   }
   check_cuda(cudaGetLastError(), "bcc sweep launch");
 }
 
 static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int nw, int pl,
-                     int threads, int slots, int64_t n) {
+                     int threads, int slots, int64_t n, int nc) {
   const int K = hd->shells.K;
   if (K == 4) {
-    if (nw == 1 && pl == 2 && slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n);
-    if (nw == 1 && pl == 2) return launch_bcc<4, 1, 2, 2>(hd, D, Q, threads, n);
-    if (nw == 1 && slots == 1) return launch_bcc<4, 1, 3, 1>(hd, D, Q, threads, n);
-    if (nw == 1) return launch_bcc<4, 1, 3, 2>(hd, D, Q, threads, n);
-    if (pl == 2 && slots == 1) return launch_bcc<4, 2, 2, 1>(hd, D, Q, threads, n);
-    if (pl == 2) return launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n);
-    if (slots == 1) return launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n);
-    return launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n);
+    if (nw == 1 && pl == 2 && slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n, nc);
+    if (nw == 1 && pl == 2) return launch_bcc<4, 1, 2, 2>(hd, D, Q, threads, n, nc);
+    if (nw == 1 && slots == 1) return launch_bcc<4, 1, 3, 1>(hd, D, Q, threads, n, nc);
+    if (nw == 1) return launch_bcc<4, 1, 3, 2>(hd, D, Q, threads, n, nc);
+    if (pl == 2 && slots == 1) return launch_bcc<4, 2, 2, 1>(hd, D, Q, threads, n, nc);
+    if (pl == 2) return launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n, nc);
+    if (slots == 1) return launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n, nc);
+    return launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n, nc);
   }
   // fewer shells: one general variant each (any M <= 8, three planes)
   if (slots != 1) fail(SMCX_E_UNSUPPORTED, "block shape");
-  if (K == 3) return launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n);
-  if (K == 2) return launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n);
-  return launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n);
+  if (K == 3) return launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n, nc);
+  if (K == 2) return launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n, nc);
+  return launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n, nc);
 }
 
-void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
+void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
   bccfast::LatDesc D;
   memset(&D, 0, sizeof(D));
   const smcx_sched& sc = hd->sched;
@@ -142,7 +142,7 @@ void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps) {
     bcc_block_shape(D.NQ, 0, &threads, &slots);
     if (slots != 1) fail(SMCX_E_UNSUPPORTED, "tile too large for the fewer-shell kernel");
   }
-  dispatch(hd, D, Q, hd->shells.K == 4 ? nw : 2, PL, threads, slots, n_sweeps);
+  dispatch(hd, D, Q, hd->shells.K == 4 ? nw : 2, PL, threads, slots, n_sweeps, n_colours);
 }
 
 }  // namespace smcx

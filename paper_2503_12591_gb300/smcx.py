@@ -55,6 +55,7 @@ _SIGS = {
     "smcx_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64]),
+    "smcx_sweep_partial": (C.c_int, [C.c_void_p, C.c_double, C.c_uint64, C.c_int]),
     "smcx_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_pair_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_sro": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -203,6 +204,9 @@ class Lattice:
     def sweep(self, T, n_sweeps, seed):
         _check(lib().smcx_sweep(self._h, float(T), int(n_sweeps), int(seed)))
 
+    def sweep_partial(self, T, seed, n_colours):
+        _check(lib().smcx_sweep_partial(self._h, float(T), int(seed), int(n_colours)))
+
     def energy(self):
         e = np.zeros(1, np.int64)
         _check(lib().smcx_energy(self._h, _p(e)))
@@ -291,6 +295,9 @@ class Batch:
         th = np.zeros(1, np.int32)
         _check(lib().smcx_batch_autotune(self._h, _p(T), int(trial_sweeps), _p(th)))
         return int(th[0])
+
+    def sweep_partial(self, T, seed, n_colours):
+        _check(lib().smcx_sweep_partial(self._h, float(T), int(seed), int(n_colours)))
 
     def energy(self):
         e = np.zeros(len(self.lattices), np.int64)

@@ -117,3 +117,38 @@ def test_schedule_independence_brute_force(kind, K, dims, L, nt):
 def test_schedule_checker_finds_violations(kind, K, dims, L, nt):
     assert O.schedule_check(kind, dims, K, L, nt) != 0
     assert _violations(kind, dims, K, L, nt) > 0
+
+
+@pytest.mark.parametrize("kind,K,dims,L,nt", [
+    (O.BCC, 4, (12, 14, 13), 3, (4, 2, 4)),
+    (O.FCC, 3, (9, 8, 10), 3, (2, 2, 2)),
+])
+def test_tile_passes_compose_to_sweep(kind, K, dims, L, nt):
+    """Running every tile of colour 0, then colour 1, ... (tiles in a random
+    order inside a colour) with the single-tile pass equals the oracle sweep:
+    the single-tile pass is the sweep loop restricted to one tile."""
+    from paper_2503_12591_gb300.inputs import epi_gaussian
+    M = 4
+    V = epi_gaussian(K, M, 20.0, 6)
+    sig = O.init_config(kind, dims, M, [0.25] * 4, 8)
+    a = sig.copy()
+    st = O.sweep(kind, dims, M, K, V, a, 1100.0, 1, 3, sweep0=5, replica=2, L=L, nt=nt)
+    b = sig.copy()
+    rng = np.random.default_rng(1)
+    tot = np.zeros(4, np.int64)
+    for tc in range(8):
+        tiles = [(x, y, z) for z in range(nt[2]) for y in range(nt[1]) for x in range(nt[0])
+                 if (x & 1) | ((y & 1) << 1) | ((z & 1) << 2) == tc]
+        rng.shuffle(tiles)
+        for t in tiles:
+            tot += O.tile_pass(kind, dims, M, K, V, b, 1100.0, 3, 5, 2, L, nt, t)
+    assert (a == b).all()
+    assert tot.tolist() == st.tolist()
+
+
+def test_init_sample_matches_full_placement():
+    dims = (5, 6, 7)
+    comp = [0.4, 0.35, 0.25]
+    full = O.init_config(O.FCC, dims, 3, comp, 21)
+    ids = np.array([0, 1, 17, 333, 500, full.size - 1], np.int64)
+    assert (O.init_sample(O.FCC, dims, 3, comp, 21, ids) == full[ids]).all()
