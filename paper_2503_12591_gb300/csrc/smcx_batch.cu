@@ -81,7 +81,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
 }
 
 template <int K, int NW, int PL, int SLOTS>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(128, 6)
     k_bcc_batch(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
                 int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -160,14 +160,13 @@ using KernelFn = void (*)(const bccfast::Planes, const bccfast::LatDesc*, const 
 
 KernelFn pick_kernel(int nw, int pl, int slots) {
   using namespace bccfast;
-  if (nw == 1 && pl == 2 && slots == 1) return k_bcc_batch<4, 1, 2, 1>;
-  if (nw == 1 && pl == 2) return k_bcc_batch<4, 1, 2, 2>;
-  if (nw == 1 && slots == 1) return k_bcc_batch<4, 1, 3, 1>;
-  if (nw == 1) return k_bcc_batch<4, 1, 3, 2>;
-  if (pl == 2 && slots == 1) return k_bcc_batch<4, 2, 2, 1>;
-  if (pl == 2) return k_bcc_batch<4, 2, 2, 2>;
-  if (slots == 1) return k_bcc_batch<4, 2, 3, 1>;
-  return k_bcc_batch<4, 2, 3, 2>;
+#define SMCX_PICK(NW_, PL_) \
+  return slots == 1 ? k_bcc_batch<4, NW_, PL_, 1> : (slots == 2 ? k_bcc_batch<4, NW_, PL_, 2> : k_bcc_batch<4, NW_, PL_, 4>)
+  if (nw == 1 && pl == 2) SMCX_PICK(1, 2);
+  if (nw == 1) SMCX_PICK(1, 3);
+  if (pl == 2) SMCX_PICK(2, 2);
+  SMCX_PICK(2, 3);
+#undef SMCX_PICK
 }
 
 }  // namespace

@@ -7,7 +7,7 @@ namespace smcx {
 namespace bccfast {
 
 template <int K, int NW, int PL, int SLOTS>
-__global__ void __launch_bounds__(512, 2) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
+__global__ void __launch_bounds__(128, 6) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   uint8_t* box = smem;
@@ -52,7 +52,7 @@ bool bcc_fast_usable(const smcx_lattice* hd) {
     if (tmax + 4 > bccfast::BOX) return false;
     nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
   }
-  return nq * nq * nq <= 1024;
+  return nq * nq * nq <= 512;
 }
 
 int bcc_slots_per_axis(const int n[3], const smcx_sched& sc) {
@@ -61,17 +61,16 @@ int bcc_slots_per_axis(const int n[3], const smcx_sched& sc) {
   return nq;
 }
 
-// Threads per CTA and slots per thread for NQ^3 link-cell slots: the
-// handle's tuned block size if set, else one slot per thread.
+// Threads per CTA (at most 128, the kernels' launch bound) and link-cell
+// slots per thread (1, 2 or 4) for NQ^3 slots: the handle's tuned block
+// size if set, else the fewest threads that need no more slots.
 void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots) {
   const int ns = nq * nq * nq;
-  int t = tuned_threads > 0 ? tuned_threads : std::min(512, ((ns + 31) / 32) * 32);
+  int t = tuned_threads > 0 ? std::min(128, tuned_threads) : std::min(128, ((ns + 31) / 32) * 32);
   int s = (ns + t - 1) / t;
-  if (s > 2) {
-    s = 2;
-    t = std::min(512, ((ns + 2 * 32 - 1) / (2 * 32)) * 32);
-    s = (ns + t - 1) / t;
-  }
+  s = s <= 1 ? 1 : (s <= 2 ? 2 : 4);
+  if (tuned_threads <= 0) t = std::min(128, ((ns + s - 1) / s + 31) / 32 * 32);
+  if ((long long)t * s < ns) fail(SMCX_E_UNSUPPORTED, "tile needs more than 512 link-cell slots");
   *threads = t;
   *slots = s;
 }
@@ -96,21 +95,23 @@ static void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Pla
 static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int nw, int pl,
                      int threads, int slots, int64_t n, int nc) {
   const int K = hd->shells.K;
+#define SMCX_BCC_SLOTS(K_, NW_, PL_)                                             \
+  do {                                                                           \
+    if (slots == 1) return launch_bcc<K_, NW_, PL_, 1>(hd, D, Q, threads, n, nc); \
+    if (slots == 2) return launch_bcc<K_, NW_, PL_, 2>(hd, D, Q, threads, n, nc); \
+    return launch_bcc<K_, NW_, PL_, 4>(hd, D, Q, threads, n, nc);                \
+  } while (0)
   if (K == 4) {
-    if (nw == 1 && pl == 2 && slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n, nc);
-    if (nw == 1 && pl == 2) return launch_bcc<4, 1, 2, 2>(hd, D, Q, threads, n, nc);
-    if (nw == 1 && slots == 1) return launch_bcc<4, 1, 3, 1>(hd, D, Q, threads, n, nc);
-    if (nw == 1) return launch_bcc<4, 1, 3, 2>(hd, D, Q, threads, n, nc);
-    if (pl == 2 && slots == 1) return launch_bcc<4, 2, 2, 1>(hd, D, Q, threads, n, nc);
-    if (pl == 2) return launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n, nc);
-    if (slots == 1) return launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n, nc);
-    return launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n, nc);
+    if (nw == 1 && pl == 2) SMCX_BCC_SLOTS(4, 1, 2);
+    if (nw == 1) SMCX_BCC_SLOTS(4, 1, 3);
+    if (pl == 2) SMCX_BCC_SLOTS(4, 2, 2);
+    SMCX_BCC_SLOTS(4, 2, 3);
   }
   // fewer shells: one general variant each (any M <= 8, three planes)
-  if (slots != 1) fail(SMCX_E_UNSUPPORTED, "block shape");
-  if (K == 3) return launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n, nc);
-  if (K == 2) return launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n, nc);
-  return launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n, nc);
+  if (K == 3) SMCX_BCC_SLOTS(3, 2, 3);
+  if (K == 2) SMCX_BCC_SLOTS(2, 2, 3);
+  SMCX_BCC_SLOTS(1, 2, 3);
+#undef SMCX_BCC_SLOTS
 }
 
 void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
@@ -138,10 +139,7 @@ void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
   const int nw = hd->M <= 4 ? 1 : 2;
   int threads, slots;
   bcc_block_shape(D.NQ, hd->bcc_threads, &threads, &slots);
-  if (hd->shells.K != 4) {
-    bcc_block_shape(D.NQ, 0, &threads, &slots);
-    if (slots != 1) fail(SMCX_E_UNSUPPORTED, "tile too large for the fewer-shell kernel");
-  }
+
   dispatch(hd, D, Q, hd->shells.K == 4 ? nw : 2, PL, threads, slots, n_sweeps, n_colours);
 }
 
