@@ -376,6 +376,18 @@ def run_gradient(stream):
     return out
 
 
+def aggregate_ranks(ms, sites, steps, dist_mod=None, device="cuda"):
+    """Replicas-only scaling: every rank sweeps its own lattice; the job time
+    is the slowest rank's, the job's trials are the sum over ranks."""
+    import torch
+    world = dist_mod.get_world_size() if dist_mod is not None else 1
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist_mod is not None:
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, sites * steps * world / (ms_max / 1e3)
+
+
 def run_smcx(args, rank, world, local_rank):
     import torch
 
@@ -416,13 +428,9 @@ def run_smcx(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = aggregate_ranks(ms, WORK.sites, args.steps, dist)
     launches_per_sweep = 8 if sched[1] != (1, 1, 1) else sched[0] ** 3 * 2
     n_launch = launches_per_sweep * args.steps
-    value = WORK.sites * args.steps * world / (ms_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
