@@ -165,6 +165,21 @@ int smcx_set_kernel(smcx_lattice* h, int which);
  * trajectory it follows as replica r of a batch. */
 int smcx_set_replica(smcx_lattice* h, int replica);
 
+/* Proposal mode.  SMCX_PROPOSAL_SITE (default): every trial draws its own
+ * shell-1 direction (the reading of the paper: a random nearest neighbour per
+ * trial).  SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra
+ * colour ic), drawn from Philox with counter (tile index, (ic >> 1) |
+ * replica << 16, sweep lo, sweep hi | 2^30) and key = seed, output word 0 for
+ * even ic and word 2 for odd ic, where tile index = (tz * nt[1] + ty) * nt[0]
+ * + tx (0 for the link-cell schedule); acceptance uniforms stay per trial.  Each trial is still a symmetric proposal, so every
+ * phase keeps detailed balance and the canonical distribution is unchanged;
+ * trials of a phase move along the same vector, which lets the BCC kernel
+ * fetch the two environments as one compile-time union.  Batched sweeps use
+ * SMCX_PROPOSAL_SITE. */
+#define SMCX_PROPOSAL_SITE 0
+#define SMCX_PROPOSAL_TILE 1
+int smcx_set_proposal(smcx_lattice* h, int mode);
+
 /* Threads per CTA of the BCC shared-memory kernel (0 = one thread per
  * link-cell slot; else a multiple of 32 up to 512).  Performance only. */
 int smcx_set_block(smcx_lattice* h, int threads);

@@ -46,6 +46,8 @@ def lib():
         L.orc_threshold.restype = C.c_uint32
         L.orc_schedule_check.argtypes = [i32] * 9
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
+        L.orc_sweep_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp, i32])
+        L.orc_phase_direction.argtypes = [u64, u64, i32, i64, i32, i32]
         L.orc_tile_pass.argtypes = [i32] * 6 + [vp, vp, dbl, u64, u64, i32] + [i32] * 7 + [vp]
         L.orc_init_sample.argtypes = [i32] * 5 + [vp, u64, vp, i32, vp]
         L.orc_phase_of.argtypes = [i32] * 8 + [i64, vp]
@@ -163,15 +165,16 @@ def schedule_check(kind, dims, K, L, nt):
 
 
 def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
-          L=0, nt=(1, 1, 1)):
+          L=0, nt=(1, 1, 1), proposal=0):
     """Run n_sweeps in place on sigma (int8, contiguous); returns stats
-    (attempts, accepts, same-species proposals, sum of accepted dE)."""
+    (attempts, accepts, same-species proposals, sum of accepted dE).
+    proposal: 0 = direction per trial, 1 = shared per (sweep, tile, phase)."""
     assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
     Vv = np.ascontiguousarray(V, np.int32)
     st = np.zeros(4, np.int64)
-    rc = lib().orc_sweep(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
-                         int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
-                         _p(st))
+    rc = lib().orc_sweep_proposal(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
+                                  int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
+                                  _p(st), int(proposal))
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
     return st
@@ -202,3 +205,7 @@ def init_sample(kind, dims, M, comp, seed, ids):
     if lib().orc_init_sample(kind, *dims, M, _p(c), int(seed), _p(ids), ids.size, _p(out)):
         raise ValueError("init sample failed")
     return out
+
+
+def phase_direction(seed, sweep, replica, tile, ic, z1):
+    return int(lib().orc_phase_direction(int(seed), int(sweep), int(replica), int(tile), int(ic), int(z1)))

@@ -532,11 +532,11 @@ typedef struct {
 /* One canonical swap trial at site s (Supplementary "Monte Carlo
  * Simulation Algorithms"): partner = a uniformly chosen shell-1 neighbour,
  * energy change from the two sites' environments, Metropolis acceptance. */
-static void attempt(attempt_ctx* c, int64_t s) {
+static void attempt_dir(attempt_ctx* c, int64_t s, int forced_dir) {
   uint32_t rd, ru;
   orc_attempt_words(c->seed, c->sweep, c->replica, s, &rd, &ru);
   int z1 = c->S->z[0];
-  int dir = (int)(((uint64_t)rd * (uint64_t)z1) >> 32);
+  int dir = forced_dir >= 0 ? forced_dir : (int)(((uint64_t)rd * (uint64_t)z1) >> 32);
   int64_t sp = orc_neighbour(c->kind, c->nx, c->ny, c->nz, s, c->S->v[dir]);
   c->stats[0]++;
   int a = c->sigma[s], b = c->sigma[sp];
@@ -556,6 +556,23 @@ static void attempt(attempt_ctx* c, int64_t s) {
     c->stats[1]++;
     c->stats[3] += dE;
   }
+}
+
+static void attempt(attempt_ctx* c, int64_t s) { attempt_dir(c, s, -1); }
+
+/* Shared-direction proposals: one shell-1 direction per (sweep, tile, intra
+ * colour ic), drawn from Philox with counter (tile index, (ic >> 1) |
+ * replica << 16, sweep lo, sweep hi | 2^30) and key = seed, output word 0 for
+ * even ic and word 2 for odd ic; the acceptance uniforms stay per site.
+ * Every trial of a phase is still a symmetric proposal (the swap along a
+ * fixed vector is its own inverse), so each phase keeps detailed balance. */
+int orc_phase_direction(uint64_t seed, uint64_t sweep, int replica, int64_t tile, int ic, int z1) {
+  uint32_t ctr[4] = {(uint32_t)tile, ((uint32_t)ic >> 1) | ((uint32_t)replica << 16), (uint32_t)sweep,
+                     (uint32_t)(sweep >> 32) | 0x40000000u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  return (int)(((uint64_t)((ic & 1) ? o[2] : o[0]) * (uint64_t)z1) >> 32);
 }
 
 /* All intra-colour phases of ONE tile (tile indices tx, ty, tz) of sweep
@@ -652,10 +669,32 @@ int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp,
   return 0;
 }
 
+static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                      int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                      uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                      int64_t* stats, int proposal);
+
 int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
               int64_t* stats) {
+  return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
+                    stats, 0);
+}
+
+int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                       int64_t* stats, int proposal) {
+  if (proposal != 0 && (proposal != 1 || L == 0)) return -2;
+  return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
+                    stats, proposal);
+}
+
+static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                      int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                      uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                      int64_t* stats, int proposal) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
@@ -705,10 +744,13 @@ int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               tile_bounds(nx, ntx, ix, &x0, &sx);
               tile_bounds(ny, nty, iy, &y0, &sy);
               tile_bounds(nz, ntz, iz, &z0, &sz);
+              int fd = -1;
+              if (proposal == 1)
+                fd = orc_phase_direction(seed, c.sweep, replica, ((int64_t)iz * nty + iy) * ntx + ix, ic, S.z[0]);
               for (int z = z0 + cz; z < z0 + sz; z += L)
                 for (int y = y0 + cy; y < y0 + sy; y += L)
                   for (int x = x0 + cx; x < x0 + sx; x += L)
-                    attempt(&c, (((int64_t)z * ny + y) * nx + x) * m + b);
+                    attempt_dir(&c, (((int64_t)z * ny + y) * nx + x) * m + b, fd);
             }
       }
   }

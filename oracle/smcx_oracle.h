@@ -98,6 +98,14 @@ int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
               int64_t* stats /*[4]: attempts, accepts, same-species,
                                  sum of accepted dE*/);
+/* Sweep with a proposal mode: 0 = a uniform shell-1 direction per trial
+ * (orc_sweep), 1 = one shared direction per (sweep, tile, intra colour),
+ * see orc_phase_direction.  Mode 1 needs a checkerboard schedule (L > 0). */
+int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                       int64_t* stats, int proposal);
+int orc_phase_direction(uint64_t seed, uint64_t sweep, int replica, int64_t tile, int ic, int z1);
 /* All phases of one tile (tx, ty, tz) of sweep `sweep` (stats as orc_sweep). */
 int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                   int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica,

@@ -238,6 +238,14 @@ int smcx_set_replica(smcx_lattice* h, int replica) {
   });
 }
 
+int smcx_set_proposal(smcx_lattice* h, int mode) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(mode == SMCX_PROPOSAL_SITE || mode == SMCX_PROPOSAL_TILE, SMCX_E_INVALID_ARG, "unknown proposal mode");
+    h->proposal = mode;
+  });
+}
+
 int smcx_set_block(smcx_lattice* h, int threads) {
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");

@@ -116,6 +116,7 @@ void check_batch(const smcx_batch* b) {
     if (h->M != h0->M || h->shells.K != h0->shells.K || h->V != h0->V)
       fail(SMCX_E_INVALID_ARG, "replicas must share M and the EPI table");
     if (h->stream != b->stream) fail(SMCX_E_INVALID_ARG, "replicas must share the batch stream");
+    if (h->proposal != SMCX_PROPOSAL_SITE) fail(SMCX_E_UNSUPPORTED, "batched sweeps use per-trial directions");
     if (!bcc_fast_usable(h))
       fail(SMCX_E_UNSUPPORTED, "replica schedule needs tiles of at most 20 cells (BCC, M <= 8)");
   }
@@ -148,6 +149,7 @@ void rebuild_items(smcx_batch* b) {
   b->n_items = (int)items.size();
   int threads, slots;
   bcc_block_shape(nq, b->threads, &threads, &slots);
+  if (slots > 2) fail(SMCX_E_UNSUPPORTED, "batched tiles need at most 256 link-cell slots");
   b->threads = threads;
   b->slots = slots;
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
@@ -160,8 +162,7 @@ using KernelFn = void (*)(const bccfast::Planes, const bccfast::LatDesc*, const 
 
 KernelFn pick_kernel(int nw, int pl, int slots) {
   using namespace bccfast;
-#define SMCX_PICK(NW_, PL_) \
-  return slots == 1 ? k_bcc_batch<4, NW_, PL_, 1> : (slots == 2 ? k_bcc_batch<4, NW_, PL_, 2> : k_bcc_batch<4, NW_, PL_, 4>)
+#define SMCX_PICK(NW_, PL_) return slots == 1 ? k_bcc_batch<4, NW_, PL_, 1> : k_bcc_batch<4, NW_, PL_, 2>
   if (nw == 1 && pl == 2) SMCX_PICK(1, 2);
   if (nw == 1) SMCX_PICK(1, 3);
   if (pl == 2) SMCX_PICK(2, 2);

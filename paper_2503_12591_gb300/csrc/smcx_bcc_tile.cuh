@@ -53,6 +53,7 @@ struct LatDesc {
   uint32_t seed_lo, seed_hi;
   unsigned long long sweep;     // cumulative index of the first sweep of the call
   int M;                        // species count (pair counting)
+  int proposal;                 // 0: direction per trial; 1: per (sweep, tile, intra colour)
 };
 
 // 50 BCC neighbour vectors (half units) of shells 1..4 with their shell.
@@ -203,15 +204,119 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   }
 }
 
+// ---- shared-direction proposals ------------------------------------------
+// With one direction per (sweep, tile, intra colour) every lane of a phase
+// has its partner at the same offset, so the union of the two environments
+// (68 distinct sites for 4 BCC shells, instead of 2 x 50 loads) is the same
+// for the whole warp: each site adds to the counter of its shell around s and
+// subtracts from the counter of its shell around s'.  The 8 directions are
+// reflections of direction 7 = (+,+,+), which preserve both shells, so one
+// entry list per sublattice (shells fixed at compile time) serves all of
+// them; only the box offsets depend on the direction, and are read from a
+// constant-memory table at a warp-uniform index.
+struct UEntry {
+  int x, y, z, k1, k2;  // half-unit vector from s; shell around s / s' (-1: none)
+};
+struct UTable {
+  UEntry e[96];
+  int n;
+};
+__host__ __device__ constexpr int bcc_shell_k(int x, int y, int z, int K) {
+  const bool odd = (x & 1) && (y & 1) && (z & 1);
+  const bool even = !(x & 1) && !(y & 1) && !(z & 1);
+  if (!(odd || even)) return -1;
+  const int k = bcc_shell_of(x, y, z);
+  return k < K ? k : -1;
+}
+// union of the environments of s and s' = s + (1,1,1) (direction 7)
+template <int K>
+__host__ __device__ constexpr UTable make_union7() {
+  UTable t{};
+  t.n = 0;
+  for (int x = -4; x <= 4; x++)
+    for (int y = -4; y <= 4; y++)
+      for (int z = -4; z <= 4; z++) {
+        if ((x == 0 && y == 0 && z == 0) || (x == 1 && y == 1 && z == 1)) continue;
+        const int k1 = bcc_shell_k(x, y, z, K);
+        const int k2 = bcc_shell_k(x - 1, y - 1, z - 1, K);
+        if (k1 < 0 && k2 < 0) continue;
+        t.e[t.n] = UEntry{x, y, z, k1, k2};
+        t.n++;
+      }
+  return t;
+}
+constexpr int kUnionMax = 72;
+struct UnionOffsets {
+  int off[2][8][kUnionMax];  // box offset of entry j reflected into direction d
+  int poff[2][8];            // partner offset
+};
+__host__ __device__ constexpr UnionOffsets make_union_offsets() {
+  UnionOffsets u{};
+  constexpr UTable T = make_union7<4>();
+  for (int B = 0; B < 2; B++)
+    for (int d = 0; d < 8; d++) {
+      const int sx = (d >> 2) & 1 ? 1 : -1, sy = (d >> 1) & 1 ? 1 : -1, sz = d & 1 ? 1 : -1;
+      u.poff[B][d] = nb_offset(B, sx, sy, sz);
+      for (int j = 0; j < T.n; j++) u.off[B][d][j] = nb_offset(B, sx * T.e[j].x, sy * T.e[j].y, sz * T.e[j].z);
+    }
+  return u;
+}
+
+// dE = G_b - G_a from the per-shell counter differences, and the decision.
+template <int K, int NW, int PL>
+__device__ __forceinline__ void finish_trial(uint8_t* box, int s, int sp, uint32_t a8, uint32_t b8,
+                                             const uint32_t (&h)[kMaxShells][2], uint32_t ru, const Planes& P,
+                                             int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc,
+                                             long long& dsum) {
+  const int a = (int)(a8 >> 3), b = (int)(b8 >> 3);
+  int Ga = 0, Gb = 0;
+#pragma unroll
+  for (int p = 0; p < 4 * NW; p++) {
+    int acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+#pragma unroll
+      for (int w = 0; w < NW; w++) {
+        const int d = (int)(h[k][w] ^ 0x80808080u);
+        acc0 = dp4a_su(d, P.P[0][k][p][w], acc0);
+        if (PL == 2) {
+          acc1 = dp4a_ss(d, P.P[1][k][p][w], acc1);
+        } else {
+          acc1 = dp4a_su(d, P.P[1][k][p][w], acc1);
+          acc2 = dp4a_ss(d, P.P[2][k][p][w], acc2);
+        }
+      }
+    }
+    const int G = acc0 + (acc1 << 8) + (acc2 << 16);
+    Ga = (p == a) ? G : Ga;
+    Gb = (p == b) ? G : Gb;
+  }
+  const int dE = Gb - Ga;
+  if (metropolis_accept(dE, ru, sA, nA, sB)) {
+    box[s] = (uint8_t)b8;
+    box[sp] = (uint8_t)a8;
+    acc++;
+    dsum += dE;
+  }
+}
+
 // One tile pass: stage the tile of colour `tc` with index `jt` among the
 // tiles of that colour (plus its 2-cell halo) into shared memory, run every
 // intra-colour phase of the tile, write the tile and its 1-cell partner ring
 // back, add the statistics.  Every thread of the CTA must call it.
 // Shared memory: box (2 * SUB bytes), sA (nA words), sB (kNB words), s_stat[3].
-template <int K, int NW, int PL, int SLOTS>
+// Shared-direction trial; defined where the offset table lives
+// (smcx_sweep_bcc_dir.cu).
+template <int B, int K, int NW, int PL>
+__device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, const Planes& P, int nA,
+                                 const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
+                                 long long& dsum);
+
+template <int K, int NW, int PL, int SLOTS, int PROP = 0>
 __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q, int tc, int jt,
                                               unsigned long long sweep, uint8_t* box, uint32_t* sA, uint32_t* sB,
                                               unsigned long long* s_stat) {
+  __shared__ uint8_t s_dir[512];  // phase directions (shared-direction proposals)
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int ntc0 = D.nt[0] / 2, ntc1 = D.nt[1] / 2;
@@ -228,6 +333,14 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   if (tid < 3) s_stat[tid] = 0;
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+  if (PROP == 1) {
+    const unsigned tile = (unsigned)((ti[2] * D.nt[1] + ti[1]) * D.nt[0] + ti[0]);
+    for (int pr = tid; pr < D.L * D.L * D.L; pr += nth) {
+      const uint4 r = phase_direction_block(D.seed_lo, D.seed_hi, sweep, D.replica, tile, pr);
+      s_dir[2 * pr] = (uint8_t)(r.x >> 29);
+      s_dir[2 * pr + 1] = (uint8_t)(r.z >> 29);
+    }
+  }
 
   // stage tile + 2-cell halo: one box row (fixed y, z) per warp iteration
   constexpr int h = 2;
@@ -286,7 +399,11 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
             keep_d[j] = rw.z;
             keep_u[j] = rw.w;
             const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
-            trial<0, K, NW, PL>(box, s, rw.x, rw.y, Q, D.nA, sA, sB, acc, same, dsum);
+            if (PROP == 1)
+              trial_shared_dir<0, K, NW, PL>(box, s, s_dir[((cz * L + cy) * L + cx) * 2], rw.y, Q, D.nA, sA, sB, acc,
+                                             same, dsum);
+            else
+              trial<0, K, NW, PL>(box, s, rw.x, rw.y, Q, D.nA, sA, sB, acc, same, dsum);
           }
         }
         __syncthreads();
@@ -295,7 +412,11 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
           const int xr = cx + L * qx[j], yr = cy + L * qy[j], zr = cz + L * qz[j];
           if (slot[j] && xr < ts[0] && yr < ts[1] && zr < ts[2]) {
             const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
-            trial<1, K, NW, PL>(box, SUB + s, keep_d[j], keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
+            if (PROP == 1)
+              trial_shared_dir<1, K, NW, PL>(box, SUB + s, s_dir[((cz * L + cy) * L + cx) * 2 + 1], keep_u[j], Q,
+                                             D.nA, sA, sB, acc, same, dsum);
+            else
+              trial<1, K, NW, PL>(box, SUB + s, keep_d[j], keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
           }
         }
         __syncthreads();
@@ -337,6 +458,35 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
 // high-part entries.
 __host__ __device__ constexpr size_t smem_bytes(int nA) { return 2 * SUB + (size_t)(nA + kNB) * 4; }
 
+
+// Single-lattice sweep kernel: one CTA per tile of colour `tc`.
+template <int K, int NW, int PL, int SLOTS, int PROP>
+__global__ void __launch_bounds__(128, 6) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_stat[3];
+  uint8_t* box = smem;
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
+  uint32_t* sB = sA + D.nA;
+  bcc_tile_pass<K, NW, PL, SLOTS, PROP>(D, Q, tc, blockIdx.x, D.sweep, box, sA, sB, s_stat);
+}
+
 }  // namespace bccfast
+
+template <int K, int NW, int PL, int SLOTS, int PROP = 0>
+inline void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads,
+                       int64_t n_sweeps, int n_colours) {
+  const size_t smem = bccfast::smem_bytes(D.nA);
+  check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS, PROP>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+             "bcc sweep smem attribute");
+  const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
+  const unsigned long long first = D.sweep;
+  for (int64_t s = 0; s < n_sweeps; s++) {
+    D.sweep = first + (unsigned long long)s;
+    for (int tc = 0; tc < n_colours; tc++)
+      bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS, PROP><<<grid, threads, smem, hd->stream>>>(D, Q, tc);
+  }
+  check_cuda(cudaGetLastError(), "bcc sweep launch");
+}
 
 }  // namespace smcx

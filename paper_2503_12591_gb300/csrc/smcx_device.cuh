@@ -33,6 +33,22 @@ __device__ __forceinline__ uint4 attempt_block(unsigned long long gid, unsigned 
                        make_uint2(seed_lo, seed_hi));
 }
 
+// Shell-1 direction shared by every trial of one (sweep, tile, intra colour)
+// under shared-direction proposals: Philox counter (tile, (ic >> 1) |
+// replica << 16, sweep lo, sweep hi | 2^30), key = seed; word 0 (even ic) or
+// word 2 (odd ic); floor(word * z1 / 2^32).
+__device__ __forceinline__ uint4 phase_direction_block(uint32_t seed_lo, uint32_t seed_hi, unsigned long long sweep,
+                                                       int rep, unsigned tile, int ic_pair) {
+  return philox4x32_10(make_uint4(tile, (uint32_t)ic_pair | ((uint32_t)rep << 16), (uint32_t)sweep,
+                                  (uint32_t)(sweep >> 32) | 0x40000000u),
+                       make_uint2(seed_lo, seed_hi));
+}
+__device__ __forceinline__ int phase_direction(uint32_t seed_lo, uint32_t seed_hi, unsigned long long sweep, int rep,
+                                               unsigned tile, int ic, int z1) {
+  const uint4 r = phase_direction_block(seed_lo, seed_hi, sweep, rep, tile, ic >> 1);
+  return (int)__umulhi((ic & 1) ? r.z : r.x, (uint32_t)z1);
+}
+
 // Shell sizes of the cubic lattices (BCC 8, 6, 12, 24; FCC 12, 6, 24).
 __host__ __device__ constexpr int shell_size(int kind, int k) {
   return kind == kBCC ? (k == 0 ? 8 : k == 1 ? 6 : k == 2 ? 12 : 24)
@@ -85,6 +101,7 @@ struct SweepParams {
   uint32_t seed_lo, seed_hi;
   unsigned long long sweep;
   int ic;                      // link-cell kernel: intra colour of the launch
+  int proposal;                // 0: direction per trial; 1: per (sweep, tile, intra colour)
   int off[4][kMaxVec];         // box offsets of neighbours, per centre sublattice
   int poff[4][kMaxZ1];         // box offset of the partner, per sublattice/direction
   int psub[4][kMaxZ1];         // partner sublattice

@@ -121,6 +121,7 @@ struct smcx_lattice {
 
   int kernel_choice = 0;  // 0 = fastest usable, 1 = generic tile/link-cell kernels
   int replica = 0;        // Philox replica id (counter word 1, bits 16..31)
+  int proposal = 0;       // SMCX_PROPOSAL_SITE or SMCX_PROPOSAL_TILE
   int bcc_threads = 0;    // tuned block size of the BCC tile kernel (0 = default)
   double thr_T = -1.0;
   int thr_nA = 0;

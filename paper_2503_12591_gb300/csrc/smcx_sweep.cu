@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(256) k_tile_sweep(const SweepParams P) {
       const uint4 rw = attempt_block(gid, P.sweep, P.replica, P.seed_lo, P.seed_hi);
       const uint32_t rd = (gid & 1) ? rw.z : rw.x;
       const uint32_t ru = (gid & 1) ? rw.w : rw.y;
-      const int dir = (int)__umulhi(rd, (uint32_t)Z1);
+      const int dir = P.proposal == 1
+                          ? phase_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica,
+                                            (unsigned)((ti[2] * P.nt[1] + ti[1]) * P.nt[0] + ti[0]), ic, Z1)
+                          : (int)__umulhi(rd, (uint32_t)Z1);
       const int sp = s + s_poff[b * Z1 + dir];
       const int bp = s_psub[b * Z1 + dir];
       const int sa = box[s], sb = box[sp];
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(256) k_linkcell_sweep(const SweepParams P) {
     const uint4 rw = attempt_block(gid, P.sweep, P.replica, P.seed_lo, P.seed_hi);
     const uint32_t rd = (gid & 1) ? rw.z : rw.x;
     const uint32_t ru = (gid & 1) ? rw.w : rw.y;
-    const int dir = (int)__umulhi(rd, (uint32_t)Z1);
+    const int dir = P.proposal == 1 ? phase_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica, 0u, P.ic, Z1)
+                                    : (int)__umulhi(rd, (uint32_t)Z1);
     const signed char* pd = P.gp[b][dir];
     const int px = wrap_add(x, pd[0], nx), py = wrap_add(y, pd[1], ny), pz = wrap_add(z, pd[2], nz);
     const int pb = pd[3];
@@ -374,6 +378,7 @@ void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int
   P.nA = nA;
   P.storage = hd->storage;
   P.replica = hd->replica;
+  P.proposal = hd->proposal;
   P.seed_lo = (uint32_t)seed;
   P.seed_hi = (uint32_t)(seed >> 32);
   fill_offsets(hd, P, P.BX, P.BY);

@@ -4,19 +4,6 @@
 
 namespace smcx {
 
-namespace bccfast {
-
-template <int K, int NW, int PL, int SLOTS>
-__global__ void __launch_bounds__(128, 6) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_stat[3];
-  uint8_t* box = smem;
-  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
-  uint32_t* sB = sA + D.nA;
-  bcc_tile_pass<K, NW, PL, SLOTS>(D, Q, tc, blockIdx.x, D.sweep, box, sA, sB, s_stat);
-}
-
-}  // namespace bccfast
 
 // Byte planes of V: the fewest that hold every entry (2 at least, which
 // covers |V| < 2^15), or more if the caller asks (min_planes).  Planes below
@@ -42,6 +29,12 @@ int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes) {
 bool bcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;
   if (hd->kind != kBCC || hd->M > kMaxSweepM || !hd->have_epi) return false;
+  if (hd->proposal == 1) {
+    // one compiled variant: 4 shells, M <= 4, |V| < 2^15, one slot per thread
+    if (hd->shells.K != 4 || hd->M > 4) return false;
+    for (int32_t v : hd->V)
+      if (v >= 32768 || v <= -32768) return false;
+  }
   if (sc.L == 0 || (sc.nt[0] == 1 && sc.nt[1] == 1 && sc.nt[2] == 1)) return false;
   if (halo_cells(hd->shells) != 2 || ring_cells(hd->shells) != 1) return false;
   for (int32_t v : hd->V)
@@ -51,6 +44,13 @@ bool bcc_fast_usable(const smcx_lattice* hd) {
     const int tmax = (hd->n[a] + sc.nt[a] - 1) / sc.nt[a];
     if (tmax + 4 > bccfast::BOX) return false;
     nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
+  }
+  if (hd->proposal == 1 && nq * nq * nq > 128) return false;  // one slot per thread
+  // four slots per thread are compiled for 4 shells, M <= 4, two planes only
+  if (nq * nq * nq > 256) {
+    if (hd->shells.K != 4 || hd->M > 4) return false;
+    for (int32_t v : hd->V)
+      if (v >= 32768 || v <= -32768) return false;
   }
   return nq * nq * nq <= 512;
 }
@@ -75,43 +75,32 @@ void bcc_block_shape(int nq, int tuned_threads, int* threads, int* slots) {
   *slots = s;
 }
 
-template <int K, int NW, int PL, int SLOTS>
-static void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads,
-                       int64_t n_sweeps, int n_colours) {
-  const size_t smem = bccfast::smem_bytes(D.nA);
-  check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-             "bcc sweep smem attribute");
-  const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
-  const unsigned long long first = D.sweep;
-  for (int64_t s = 0; s < n_sweeps; s++) {
-    D.sweep = first + (unsigned long long)s;
-    for (int tc = 0; tc < n_colours; tc++)
-      bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS><<<grid, threads, smem, hd->stream>>>(D, Q, tc);
-  }
-  check_cuda(cudaGetLastError(), "bcc sweep launch");
-}
+
+void sweep_bcc_dir(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads, int64_t n,
+                   int nc);  // smcx_sweep_bcc_dir.cu
 
 static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int nw, int pl,
                      int threads, int slots, int64_t n, int nc) {
   const int K = hd->shells.K;
-#define SMCX_BCC_SLOTS(K_, NW_, PL_)                                             \
-  do {                                                                           \
-    if (slots == 1) return launch_bcc<K_, NW_, PL_, 1>(hd, D, Q, threads, n, nc); \
-    if (slots == 2) return launch_bcc<K_, NW_, PL_, 2>(hd, D, Q, threads, n, nc); \
-    return launch_bcc<K_, NW_, PL_, 4>(hd, D, Q, threads, n, nc);                \
-  } while (0)
+  if (D.proposal == 1) return sweep_bcc_dir(hd, D, Q, threads, n, nc);
   if (K == 4) {
-    if (nw == 1 && pl == 2) SMCX_BCC_SLOTS(4, 1, 2);
-    if (nw == 1) SMCX_BCC_SLOTS(4, 1, 3);
-    if (pl == 2) SMCX_BCC_SLOTS(4, 2, 2);
-    SMCX_BCC_SLOTS(4, 2, 3);
+    if (nw == 1 && pl == 2) {
+      if (slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n, nc);
+      if (slots == 2) return launch_bcc<4, 1, 2, 2>(hd, D, Q, threads, n, nc);
+      return launch_bcc<4, 1, 2, 4>(hd, D, Q, threads, n, nc);
+    }
+    if (slots == 4) fail(SMCX_E_UNSUPPORTED, "block shape");
+    if (nw == 1) return slots == 1 ? launch_bcc<4, 1, 3, 1>(hd, D, Q, threads, n, nc)
+                                   : launch_bcc<4, 1, 3, 2>(hd, D, Q, threads, n, nc);
+    if (pl == 2) return slots == 1 ? launch_bcc<4, 2, 2, 1>(hd, D, Q, threads, n, nc)
+                                   : launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n, nc);
+    return slots == 1 ? launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n, nc);
   }
   // fewer shells: one general variant each (any M <= 8, three planes)
-  if (K == 3) SMCX_BCC_SLOTS(3, 2, 3);
-  if (K == 2) SMCX_BCC_SLOTS(2, 2, 3);
-  SMCX_BCC_SLOTS(1, 2, 3);
-#undef SMCX_BCC_SLOTS
+  if (slots == 4) fail(SMCX_E_UNSUPPORTED, "block shape");
+  if (K == 3) return slots == 1 ? launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<3, 2, 3, 2>(hd, D, Q, threads, n, nc);
+  if (K == 2) return slots == 1 ? launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<2, 2, 3, 2>(hd, D, Q, threads, n, nc);
+  return slots == 1 ? launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<1, 2, 3, 2>(hd, D, Q, threads, n, nc);
 }
 
 void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
@@ -133,6 +122,7 @@ void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
   D.seed_lo = (uint32_t)seed;
   D.seed_hi = (uint32_t)(seed >> 32);
   D.sweep = hd->sweep_cum;
+  D.proposal = hd->proposal;
   bccfast::Planes Q;
   // fewer than 4 shells: one general variant (three planes, two words)
   const int PL = build_planes(hd, &Q, hd->shells.K == 4 ? 2 : 3);

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsmcx.so")
 BCC, FCC = 0, 1
 INT8, PACKED4 = 0, 1
 KERNEL_AUTO, KERNEL_GENERIC = 0, 1
+PROPOSAL_SITE, PROPOSAL_TILE = 0, 1
 NA_MAX, NB = 4096, 1024
 
 OK = 0
@@ -45,6 +46,7 @@ _SIGS = {
     "smcx_set_kernel": (C.c_int, [C.c_void_p, C.c_int]),
     "smcx_set_replica": (C.c_int, [C.c_void_p, C.c_int]),
     "smcx_set_block": (C.c_int, [C.c_void_p, C.c_int]),
+    "smcx_set_proposal": (C.c_int, [C.c_void_p, C.c_int]),
     "smcx_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_batch_destroy": (C.c_int, [C.c_void_p]),
     "smcx_batch_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64]),
@@ -184,6 +186,9 @@ class Lattice:
 
     def set_replica(self, r):
         _check(lib().smcx_set_replica(self._h, int(r)))
+
+    def set_proposal(self, mode):
+        _check(lib().smcx_set_proposal(self._h, int(mode)))
 
     def set_block(self, threads):
         _check(lib().smcx_set_block(self._h, int(threads)))

@@ -193,3 +193,27 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     ref, rst = _oracle_run(smcx.BCC, dims, M, K, V, [0.25] * 4, 4, T, 3, 2, sched)
     assert (lat.get_config() == ref).all()
     assert lat.state()[1].tolist() == rst.tolist()
+
+
+@pytest.mark.parametrize("kernel", [smcx.KERNEL_AUTO, smcx.KERNEL_GENERIC], ids=["auto", "generic"])
+@pytest.mark.parametrize("case", [
+    (smcx.BCC, 4, (20, 20, 20), 4, [0.25] * 4, smcx.PACKED4, (4, (2, 2, 2)), 1200.0, 4),
+    (smcx.BCC, 4, (37, 22, 40), 4, [0.25] * 4, smcx.INT8, (4, (2, 2, 2)), 900.0, 3),     # ragged
+    (smcx.BCC, 4, (18, 16, 20), 3, [0.5, 0.3, 0.2], smcx.PACKED4, (3, (2, 2, 2)), 2000.0, 3),  # L=3: generic
+    (smcx.BCC, 2, (12, 12, 12), 4, [0.25] * 4, smcx.INT8, (3, (1, 1, 1)), 1000.0, 3),     # link-cell
+    (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 3),
+], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc"])
+def test_shared_direction_proposals(stream, case, kernel):
+    """SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra colour)."""
+    kind, K, dims, M, comp, storage, sched, T, n = case
+    V = epi_gaussian(K, M, 20.0, 12)
+    lat = smcx.Lattice(kind, dims, M, comp, init_seed=5, storage=storage, sched=sched, stream=stream)
+    lat.set_kernel(kernel)
+    lat.set_proposal(smcx.PROPOSAL_TILE)
+    lat.set_replica(3)
+    lat.set_epi(V)
+    lat.sweep(T, n, 4)
+    ref = O.init_config(kind, dims, M, comp, 5)
+    rst = O.sweep(kind, dims, M, K, V, ref, T, n, 4, replica=3, L=sched[0], nt=sched[1], proposal=1)
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[1].tolist() == rst.tolist()

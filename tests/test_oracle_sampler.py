@@ -172,3 +172,55 @@ def test_phase_order_independence(kind, K, dims, L, nt):
     for sw in range(2):
         _python_sweep(kind, dims, M, K, V, b, 1500.0, 5, sw, L, nt, rng)
     assert (a == b).all()
+
+
+def test_shared_direction_enumeration_chi2():
+    """Shared-direction proposals sample the same canonical distribution:
+    nearest-neighbour EPI (K = 1) on the 16-site box with the link-cell
+    schedule L = 2 (every phase holds one site), exact enumeration chi^2."""
+    dims, K = (2, 2, 2), 1
+    V = epi_gaussian(K, 2, 20.0, 31)
+    T = 1500.0
+    E = []
+    for ones in itertools.combinations(range(16), 8):
+        s = np.zeros(16, np.int8)
+        s[list(ones)] = 1
+        E.append(O.energy(O.BCC, dims, 2, K, V, s))
+    E = np.array(E)
+    lev, inv = np.unique(E, return_inverse=True)
+    p = np.bincount(inv) * np.exp(-(lev - lev.min()) * 0.01 / (KB * T))
+    p /= p.sum()
+    sig = O.init_config(O.BCC, dims, 2, [0.5, 0.5], 3)
+    idx = {int(e): i for i, e in enumerate(lev)}
+    hist = np.zeros(len(lev))
+    n, thin = 5000, 4
+    for i in range(n):
+        O.sweep(O.BCC, dims, 2, K, V, sig, T, thin, 9, sweep0=thin * i, L=2, proposal=1)
+        hist[idx[O.energy(O.BCC, dims, 2, K, V, sig)]] += 1
+    exp = p * n
+    keep = exp >= 5
+    obs = np.concatenate([hist[keep], [hist[~keep].sum()]])
+    ex = np.concatenate([exp[keep], [exp[~keep].sum()]])
+    if ex[-1] < 5:
+        obs, ex = obs[:-1], ex[:-1]
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    assert stats.chi2.sf(chi2, len(ex) - 1) > 1e-3
+
+
+def test_shared_direction_differs_and_is_uniform():
+    z1 = 8
+    counts = np.zeros(z1, np.int64)
+    for t in range(50):
+        for ic in range(128):
+            counts[O.phase_direction(5, 3, 0, t, ic, z1)] += 1
+    exp = counts.sum() / z1
+    assert ((counts - exp) ** 2 / exp).sum() < 30.0
+    dims, K, M = (12, 12, 12), 4, 4
+    V = epi_gaussian(K, M, 20.0, 3)
+    a = O.init_config(O.BCC, dims, M, [0.25] * 4, 2)
+    b = a.copy()
+    O.sweep(O.BCC, dims, M, K, V, a, 1000.0, 2, 1, L=4, nt=(2, 2, 2), proposal=0)
+    st = O.sweep(O.BCC, dims, M, K, V, b, 1000.0, 2, 1, L=4, nt=(2, 2, 2), proposal=1)
+    assert (a != b).any()
+    assert (np.bincount(b, minlength=M) == np.bincount(a, minlength=M)).all()
+    assert st[0] == 2 * b.size
