@@ -1,13 +1,18 @@
 // Ordered pair counts of a BCC lattice (M <= 4) from shared-memory tiles.
 //
 // Same result as k_pair_counts (smcx_aux.cu): C[k][p][q] = number of (site
-// i, shell-k vector v) with s_i = p and s_{i+v} = q.  Each CTA stages one
-// tile plus its 2-cell halo exactly as the sweep does, and for every site of
-// the tile adds 1 << (8 s_{i+v}) over the shell-k vectors into a byte-packed
-// register, which is split into two 16-bit-field accumulators per (shell,
-// centre species).  At the end the warp sums each accumulator with a
-// reduce-add, lane 0 adds the unpacked counts to a shared histogram, and the
-// CTA adds that to the global int64 histogram.
+// i, shell-k vector v) with s_i = p and s_{i+v} = q.  Every unordered pair is
+// visited once: with H_k the half of shell k whose first nonzero component is
+// positive, U[k][p][q] = #(i, v in H_k) with s_i = p, s_{i+v} = q, and on a
+// periodic lattice the vector -v contributes U[k][q][p] (substitute i -> i+v
+// in the sum), so C[k][p][q] = U[k][p][q] + U[k][q][p].
+// Each CTA stages one tile plus its 2-cell halo exactly as the sweep does,
+// and for every site of the tile adds 1 << (8 s_{i+v}) over the half-shell
+// vectors into a byte-packed register, which is split into two 16-bit-field
+// accumulators per (shell, centre species).  At the end the warp sums each
+// accumulator with a reduce-add, lane 0 adds the unpacked counts to a shared
+// histogram U, and the CTA adds U and its transpose to the global int64
+// histogram.
 #include "smcx_bcc_tile.cuh"
 
 namespace smcx {
@@ -80,6 +85,8 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
       for (int j = 0; j < T.n; j++) {
         const int k = T.v[j].k;
         if (k >= K) continue;
+        const bool half = T.v[j].x > 0 || (T.v[j].x == 0 && (T.v[j].y > 0 || (T.v[j].y == 0 && T.v[j].z > 0)));
+        if (!half) continue;
         const int off = B == 0 ? nb_offset(0, T.v[j].x, T.v[j].y, T.v[j].z) : nb_offset(1, T.v[j].x, T.v[j].y, T.v[j].z);
         hk[k] += 1u << box[s + off];
       }
@@ -95,7 +102,7 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
       }
     }
   }
-  // warp sums (16-bit fields: at most 32 lanes x 32 cells x 2 sites x 24 = 49152 per field)
+  // warp sums (16-bit fields: at most 32 lanes x 32 cells x 2 sites x 12 = 24576 per field)
 #pragma unroll
   for (int k = 0; k < K; k++)
 #pragma unroll
@@ -112,7 +119,10 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
   __syncthreads();
   for (int i = tid; i < K * 16; i += nth) {
     const int k = i / 16, p = (i / 4) % 4, q = i % 4;
-    if (p < D.M && q < D.M && hist[i]) atomicAdd(&counts[(k * D.M + p) * D.M + q], (unsigned long long)hist[i]);
+    if (p < D.M && q < D.M && hist[i]) {
+      atomicAdd(&counts[(k * D.M + p) * D.M + q], (unsigned long long)hist[i]);
+      atomicAdd(&counts[(k * D.M + q) * D.M + p], (unsigned long long)hist[i]);
+    }
   }
 }
 
