@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-shared", action="store_true")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -129,21 +130,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(n_sweeps=12):
-    """The oracle as it stands, single-threaded, on a BCC 64^3 sample."""
+def cpu_baseline(n_sweeps=24, n_serial=4):
+    """The oracle as it stands on a BCC 64^3 sample: its OpenMP mode (each
+    phase's sites split across all host cores, identical result) and, for
+    reference, its serial mode."""
     import oracle as O
 
     V = epi_gaussian(WORK.K, WORK.M, WORK.sigma_mev, WORK.epi_seed)
     sig = O.init_config(O.BCC, CPU_SAMPLE_DIMS, WORK.M, equiatomic(WORK.M), WORK.init_seed)
     t0 = time.perf_counter()
-    O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_sweeps, SEED,
-            L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+    _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_sweeps, SEED,
+                               L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=os.cpu_count() or 1)
     dt = time.perf_counter() - t0
     n = sig.size * n_sweeps
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"serial C oracle, BCC {CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites), 4 species, "
-                      f"4 shells, {T_KELVIN:.0f} K, schedule L={CPU_SAMPLE_SCHED[0]} "
-                      f"tiles {CPU_SAMPLE_SCHED[1]}, {n_sweeps} sweeps = {n} trials in {dt:.1f} s"}
+    t1 = time.perf_counter()
+    O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_serial, SEED, sweep0=n_sweeps,
+            L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+    dts = time.perf_counter() - t1
+    return {"value": n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "serial_value": sig.size * n_serial / dts,
+            "sample": f"C oracle, OpenMP over the sites of each phase ({used} threads), BCC "
+                      f"{CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites), 4 species, 4 shells, {T_KELVIN:.0f} K, "
+                      f"schedule L={CPU_SAMPLE_SCHED[0]} tiles {CPU_SAMPLE_SCHED[1]}, {n_sweeps} sweeps = {n} "
+                      f"trials in {dt:.1f} s; serial_value: the same oracle on 1 core, {n_serial} sweeps"}
 
 
 def config_block(extra=None):
@@ -158,8 +167,8 @@ def config_block(extra=None):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the serial CPU oracle, each step one sweep of a BCC
-    64^3 sample of the workload."""
+    """Reference arm: the CPU oracle (OpenMP over the sites of each phase, all
+    host cores), each step one sweep of a BCC 64^3 sample of the workload."""
     if rank != 0:
         return
     import oracle as O
@@ -167,24 +176,27 @@ def run_reference(args, rank, world):
     V = epi_gaussian(WORK.K, WORK.M, WORK.sigma_mev, WORK.epi_seed)
     sig = O.init_config(O.BCC, CPU_SAMPLE_DIMS, WORK.M, equiatomic(WORK.M), WORK.init_seed)
     sw = 0
+    threads = os.cpu_count() or 1
+    used = 1
     for _ in range(args.warmup):
-        O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
-                L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+        _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
+                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads)
         sw += 1
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
-                L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+        _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
+                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads)
         sw += 1
     dt = time.perf_counter() - t0
     val = sig.size * args.steps / dt
-    sample = (f"serial C oracle, one sweep of BCC {CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites) per step, "
-              f"same species/shells/temperature/schedule shape")
+    sample = (f"C oracle, OpenMP over the sites of each phase ({used} threads), one sweep of BCC "
+              f"{CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites) per step, same species/shells/temperature/"
+              f"schedule shape")
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
            "config": config_block({"sample": sample}), "impl": "reference",
-           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -432,6 +444,27 @@ def run_smcx(args, rank, world, local_rank):
     launches_per_sweep = 8 if sched[1] != (1, 1, 1) else sched[0] ** 3 * 2
     n_launch = launches_per_sweep * args.steps
 
+    # ---- shared-direction proposals (one shell-1 direction per tile phase) --
+    shared = None
+    if not args.no_shared:
+        lat.set_proposal(smcx.PROPOSAL_TILE)
+        for _ in range(args.warmup):
+            lat.sweep(T_KELVIN, 1, SEED)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            lat.sweep(T_KELVIN, 1, SEED)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms_s, value_s = aggregate_ranks(e0.elapsed_time(e1), WORK.sites, args.steps, dist)
+        lat.set_proposal(smcx.PROPOSAL_SITE)
+        shared = {"value": value_s, "unit": UNIT, "ms_per_step": ms_s / args.steps,
+                  "kernel": "k_bcc_tile_sweep<4,1,2,1,1>",
+                  "note": "optional proposal: one shell-1 direction per (sweep, tile, intra colour); "
+                          "same Boltzmann stationary distribution, different trajectories; not the "
+                          "headline, which uses the per-trial random direction"}
+
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
@@ -504,6 +537,8 @@ def run_smcx(args, rank, world, local_rank):
     }
     if e2e is not None:
         out["e2e"] = e2e
+    if shared is not None:
+        out["shared_direction"] = shared
     if not args.no_batched and world == 1:
         out["batched"] = run_batched(stream)
     if not args.no_grad and world == 1:

@@ -47,6 +47,9 @@ def lib():
         L.orc_schedule_check.argtypes = [i32] * 9
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_sweep_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp, i32])
+        L.orc_exchange_round.argtypes = [i32, vp, vp, vp, u64, u64, vp]
+        L.orc_sweep_parallel.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp,
+                                                      i32, vp])
         L.orc_phase_direction.argtypes = [u64, u64, i32, i64, i32, i32]
         L.orc_tile_pass.argtypes = [i32] * 6 + [vp, vp, dbl, u64, u64, i32] + [i32] * 7 + [vp]
         L.orc_init_sample.argtypes = [i32] * 5 + [vp, u64, vp, i32, vp]
@@ -178,6 +181,37 @@ def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
     return st
+
+
+def sweep_parallel(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
+                   L=0, nt=(1, 1, 1), threads=0):
+    """oracle sweep with every phase split across OpenMP threads (identical
+    result to sweep()); returns (stats, threads used)."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    Vv = np.ascontiguousarray(V, np.int32)
+    st = np.zeros(4, np.int64)
+    used = np.zeros(1, np.int32)
+    rc = lib().orc_sweep_parallel(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
+                                  int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
+                                  _p(st), int(threads), _p(used))
+    if rc:
+        raise ValueError(f"oracle sweep rejected the request ({rc})")
+    return st, int(used[0])
+
+
+def exchange_round(T_slot, E, slot_rep, rnd, seed, accepts=None):
+    """One replica-exchange round (orc_exchange_round); slot_rep (int32) and
+    accepts (int64, [R-1]) are updated in place."""
+    T = np.ascontiguousarray(T_slot, np.float64)
+    Ev = np.ascontiguousarray(E, np.int64)
+    assert slot_rep.dtype == np.int32 and slot_rep.flags.c_contiguous
+    R = T.size
+    acc = accepts if accepts is not None else np.zeros(max(R - 1, 1), np.int64)
+    assert acc.dtype == np.int64
+    rc = lib().orc_exchange_round(R, _p(T), _p(Ev), _p(slot_rep), int(rnd), int(seed), _p(acc))
+    if rc:
+        raise ValueError(f"oracle exchange rejected the request ({rc})")
+    return slot_rep
 
 
 def phase_of(kind, dims, L, nt, s):

@@ -9,6 +9,9 @@
 
 #include <math.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <string.h>
 
 /* ------------------------------------------------------------------ */
@@ -672,14 +675,14 @@ int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp,
 static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
-                      int64_t* stats, int proposal);
+                      int64_t* stats, int proposal, int n_threads);
 
 int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
               int64_t* stats) {
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
-                    stats, 0);
+                    stats, 0, 1);
 }
 
 int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
@@ -688,13 +691,91 @@ int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int
                        int64_t* stats, int proposal) {
   if (proposal != 0 && (proposal != 1 || L == 0)) return -2;
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
-                    stats, proposal);
+                    stats, proposal, 1);
+}
+
+/* The same sweep with the sites of each phase split across n_threads OpenMP
+ * threads (n_threads <= 0: the OpenMP default).  Sites of one phase are
+ * independent, so the result equals the serial sweep's bit for bit.  The
+ * serial schedule (L = 0) stays serial.  Returns the thread count used in
+ * *used (1 when built without OpenMP). */
+int orc_sweep_parallel(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                       int64_t* stats, int n_threads, int* used) {
+#ifdef _OPENMP
+  int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+  int nt = 1;
+  (void)n_threads;
+#endif
+  if (L == 0) nt = 1;
+  if (used) *used = nt;
+  return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
+                    stats, 0, nt);
+}
+
+/* One sweep of the link-cell / tile schedule with each phase's sites listed
+ * in the serial loop's order and split across threads; every thread keeps its
+ * own statistics, summed at the end (integer sums: order-free). */
+static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty, int ntz, uint64_t sweep0,
+                                  int64_t n_sweeps, int n_threads) {
+  const int m = c0->m, nx = c0->nx, ny = c0->ny, nz = c0->nz;
+  const int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  int64_t tot[4] = {0, 0, 0, 0};
+  int nA_ic = L * L * L * m;
+  for (int64_t n = 0; n < n_sweeps; n++) {
+    uint64_t sw = sweep0 + (uint64_t)n;
+    for (int tc = 0; tc < 8; tc++)
+      for (int ic = 0; ic < nA_ic; ic++) {
+        int b = ic % m;
+        int cx = (ic / m) % L, cy = (ic / m / L) % L, cz = ic / m / L / L;
+        int64_t cnt = 0;
+        for (int iz = 0; iz < ntz; iz++)
+          for (int iy = 0; iy < nty; iy++)
+            for (int ix = 0; ix < ntx; ix++) {
+              if (((ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2)) != tc) continue;
+              int x0, sx, y0, sy, z0, sz;
+              tile_bounds(nx, ntx, ix, &x0, &sx);
+              tile_bounds(ny, nty, iy, &y0, &sy);
+              tile_bounds(nz, ntz, iz, &z0, &sz);
+              for (int z = z0 + cz; z < z0 + sz; z += L)
+                for (int y = y0 + cy; y < y0 + sy; y += L)
+                  for (int x = x0 + cx; x < x0 + sx; x += L) list[cnt++] = (((int64_t)z * ny + y) * nx + x) * m + b;
+            }
+        int64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads) reduction(+ : t0, t1, t2, t3)
+#endif
+        {
+          attempt_ctx c = *c0;
+          int64_t st[4] = {0, 0, 0, 0};
+          c.stats = st;
+          c.sweep = sw;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+          for (int64_t i = 0; i < cnt; i++) attempt_dir(&c, list[i], -1);
+          t0 += st[0];
+          t1 += st[1];
+          t2 += st[2];
+          t3 += st[3];
+        }
+        tot[0] += t0;
+        tot[1] += t1;
+        tot[2] += t2;
+        tot[3] += t3;
+      }
+  }
+  for (int i = 0; i < 4; i++) c0->stats[i] += tot[i];
+  free(list);
 }
 
 static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
-                      int64_t* stats, int proposal) {
+                      int64_t* stats, int proposal, int n_threads) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
@@ -725,6 +806,12 @@ static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int3
   c.stats = stats;
   stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int64_t N = (int64_t)nx * ny * nz * m;
+  if (n_threads > 1) {
+    sweep_phases_parallel(&c, L, ntx, nty, ntz, sweep0, n_sweeps, n_threads);
+    free(A);
+    free(B);
+    return 0;
+  }
   for (int64_t n = 0; n < n_sweeps; n++) {
     c.sweep = sweep0 + (uint64_t)n;
     if (L == 0) {
@@ -756,5 +843,48 @@ static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int3
   }
   free(A);
   free(B);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Replica exchange between temperature slots (Supplementary           */
+/* "Parallelization opportunities": configurations at different        */
+/* temperatures are exchanged with a rule that keeps detailed balance). */
+/*   Slot t holds temperature T_slot[t] and replica slot_rep[t].  Round */
+/*   r pairs the slots (t, t+1) with t = r mod 2, r mod 2 + 2, ...  The */
+/*   swap of the replicas a (slot t) and c (slot t+1) multiplies the    */
+/*   joint Boltzmann weight by exp(x), x = (beta_t - beta_{t+1})        */
+/*   (E_a - E_c), beta = 1/(k_B T); it is accepted when x >= 0, else    */
+/*   when u < floor(2^32 exp(x)) (capped at 2^32 - 1), with u word 0 of */
+/*   Philox(counter (t, r lo, r hi, 0xC0000000), key = seed).  Energies */
+/*   are in 0.01 meV.                                                   */
+/* ------------------------------------------------------------------ */
+int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* slot_rep, uint64_t round,
+                       uint64_t seed, int64_t* accepts) {
+  for (int t = 0; t < R; t++)
+    if (!(T_slot[t] > 0.0)) return -1;
+  for (int t = (int)(round & 1); t + 1 < R; t += 2) {
+    int a = slot_rep[t], c = slot_rep[t + 1];
+    double bt = 1.0 / (ORC_KB_MEV * T_slot[t]);
+    double bu = 1.0 / (ORC_KB_MEV * T_slot[t + 1]);
+    double x = (bt - bu) * ((double)(E[a] - E[c]) * 0.01);
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)round, (uint32_t)(round >> 32), 0xC0000000u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    int accept = 0;
+    if (x >= 0.0) {
+      accept = 1;
+    } else {
+      double v = exp(x) * 4294967296.0;
+      uint32_t thr = v >= 4294967295.0 ? 4294967295u : (uint32_t)v;
+      accept = o[0] < thr;
+    }
+    if (accept) {
+      slot_rep[t] = c;
+      slot_rep[t + 1] = a;
+      if (accepts) accepts[t]++;
+    }
+  }
   return 0;
 }

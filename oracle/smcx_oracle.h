@@ -105,6 +105,14 @@ int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int
                        int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                        uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
                        int64_t* stats, int proposal);
+
+/* orc_sweep with each phase split across OpenMP threads (identical result;
+ * n_threads <= 0 = OpenMP default; *used = threads used, 1 without OpenMP
+ * or for the serial schedule L = 0). */
+int orc_sweep_parallel(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
+                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
+                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
+                       int64_t* stats, int n_threads, int* used);
 int orc_phase_direction(uint64_t seed, uint64_t sweep, int replica, int64_t tile, int ic, int z1);
 /* All phases of one tile (tx, ty, tz) of sweep `sweep` (stats as orc_sweep). */
 int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
@@ -118,6 +126,12 @@ int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp,
  * or -1 for the serial schedule.  Used by the independence test. */
 int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,
                      int ntz, int64_t s, int* tile /*[3] out, may be NULL*/);
+
+/* One replica-exchange round: slot pairs (t, t+1), t = round mod 2, +2, ...;
+ * slot_rep [R] in/out (replica at each slot), E [R] energies by replica
+ * (0.01 meV), accepts [R-1] incremented per accepted slot pair. */
+int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* slot_rep, uint64_t round,
+                       uint64_t seed, int64_t* accepts);
 
 #ifdef __cplusplus
 }
