@@ -138,6 +138,26 @@ int smcx_lattice_create(smcx_lattice** out, int kind, int nx, int ny, int nz, in
                         const double* comp, uint64_t init_seed, int storage,
                         const smcx_sched* sched, void* stream);
 
+/*
+ * Make a handle over a lattice store the caller already holds on the device
+ * (e.g. the storage of a framework tensor), without copying it.
+ *   d_sites   device (or managed) pointer to the species of the N sites in
+ *             canonical site order, in the layout of `storage`: one byte per
+ *             site (SMCX_INT8) or two sites per byte, the even site in the
+ *             low nibble (SMCX_PACKED4).  The caller keeps ownership; the
+ *             buffer must outlive the handle, and nothing else may write it
+ *             while the handle's stream has work queued on it.
+ *   bytes     size of the buffer; at least N (INT8) or N/2 (PACKED4) bytes.
+ *   other arguments as for smcx_lattice_create (no composition or seed: the
+ *   configuration is the buffer's).
+ * Every stored id is checked on the device: SMCX_E_INVALID_ARG if one is
+ * >= M, if the buffer is too small or is not device memory.  The handle
+ * sweeps, measures and reads/writes the configuration in place;
+ * smcx_lattice_destroy frees the handle's own buffers, not d_sites.
+ */
+int smcx_lattice_wrap(smcx_lattice** out, int kind, int nx, int ny, int nz, int M, void* d_sites,
+                      size_t bytes, int storage, const smcx_sched* sched, void* stream);
+
 /* Release the handle and its device memory (synchronises its stream). */
 int smcx_lattice_destroy(smcx_lattice* h);
 

@@ -39,7 +39,7 @@ void need(bool ok, int code, const char* msg) {
 int kind_max_shells(int kind) { return kind == kBCC ? 4 : 3; }
 
 void release(smcx_lattice* h) {
-  cudaFree(h->d_sites);
+  if (h->owns_sites) cudaFree(h->d_sites);
   cudaFree(h->d_stats);
   cudaFree(h->d_counts);
   cudaFree(h->d_energy);
@@ -114,44 +114,84 @@ int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B) {
   });
 }
 
+// Geometry, schedule and every buffer except the lattice store.
+static void setup_handle(smcx_lattice* h, int kind, int nx, int ny, int nz, int M, int storage,
+                         const smcx_sched* sched, void* stream) {
+  h->kind = kind;
+  h->m = sites_per_cell(kind);
+  h->M = M;
+  h->storage = storage;
+  h->n[0] = nx;
+  h->n[1] = ny;
+  h->n[2] = nz;
+  h->N = (int64_t)nx * ny * nz * h->m;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  apply_schedule(h, sched);
+  int dev_count = 0;
+  check_cuda(cudaGetDeviceCount(&dev_count), "no CUDA device");
+  check_cuda(cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long)), "stats");  // trials, accepts, same, sum dE
+  check_cuda(cudaMalloc(&h->d_counts, (size_t)kMaxShells * M * M * sizeof(unsigned long long)), "counts");
+  check_cuda(cudaMalloc(&h->d_energy, sizeof(long long)), "energy");
+  check_cuda(cudaMalloc(&h->d_thr, (kNA + kNB) * sizeof(uint32_t)), "threshold table");
+  const size_t nw = (size_t)M * M * kMaxShells * M + (size_t)M * M + (size_t)kMaxShells * M * M;
+  check_cuda(cudaMalloc(&h->d_wtab, nw * sizeof(int32_t)), "EPI table");
+  check_cuda(cudaMalloc(&h->d_flag, sizeof(int)), "flag");
+  check_cuda(cudaMemsetAsync(h->d_stats, 0, 4 * sizeof(unsigned long long), h->stream), "clear stats");
+  check_cuda(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream), "clear flag");
+}
+
+static void check_create_args(smcx_lattice** out, int kind, int nx, int ny, int nz, int M, int storage) {
+  need(out != nullptr, SMCX_E_INVALID_ARG, "NULL handle pointer");
+  *out = nullptr;
+  need(kind == kBCC || kind == kFCC, SMCX_E_INVALID_ARG, "kind must be SMCX_BCC or SMCX_FCC");
+  need(nx >= 1 && ny >= 1 && nz >= 1, SMCX_E_INVALID_ARG, "dimensions must be >= 1");
+  need(storage == SMCX_INT8 || storage == SMCX_PACKED4, SMCX_E_INVALID_ARG, "unknown storage");
+  need(M >= 1 && M <= (storage == SMCX_PACKED4 ? 15 : 127), SMCX_E_INVALID_ARG,
+       "species count out of range for the storage");
+}
+
 int smcx_lattice_create(smcx_lattice** out, int kind, int nx, int ny, int nz, int M, const double* comp,
                         uint64_t init_seed, int storage, const smcx_sched* sched, void* stream) {
   return guarded([&] {
-    need(out != nullptr, SMCX_E_INVALID_ARG, "NULL handle pointer");
-    *out = nullptr;
-    need(kind == kBCC || kind == kFCC, SMCX_E_INVALID_ARG, "kind must be SMCX_BCC or SMCX_FCC");
-    need(nx >= 1 && ny >= 1 && nz >= 1, SMCX_E_INVALID_ARG, "dimensions must be >= 1");
-    need(storage == SMCX_INT8 || storage == SMCX_PACKED4, SMCX_E_INVALID_ARG, "unknown storage");
-    need(M >= 1 && M <= (storage == SMCX_PACKED4 ? 15 : 127), SMCX_E_INVALID_ARG,
-         "species count out of range for the storage");
+    check_create_args(out, kind, nx, ny, nz, M, storage);
     need(comp != nullptr, SMCX_E_INVALID_ARG, "NULL composition");
     smcx_lattice* h = new smcx_lattice();
     try {
-      h->kind = kind;
-      h->m = sites_per_cell(kind);
-      h->M = M;
-      h->storage = storage;
-      h->n[0] = nx;
-      h->n[1] = ny;
-      h->n[2] = nz;
-      h->N = (int64_t)nx * ny * nz * h->m;
-      h->stream = reinterpret_cast<cudaStream_t>(stream);
-      apply_schedule(h, sched);
-      int dev_count = 0;
-      check_cuda(cudaGetDeviceCount(&dev_count), "no CUDA device");
+      setup_handle(h, kind, nx, ny, nz, M, storage, sched, stream);
       h->site_bytes = (size_t)(storage == SMCX_INT8 ? h->N : (h->N + 1) / 2);
       h->site_bytes = (h->site_bytes + 15) & ~(size_t)15;
       check_cuda(cudaMalloc(&h->d_sites, h->site_bytes), "lattice store");
-      check_cuda(cudaMalloc(&h->d_stats, 4 * sizeof(unsigned long long)), "stats");  // trials, accepts, same, sum dE
-      check_cuda(cudaMalloc(&h->d_counts, (size_t)kMaxShells * M * M * sizeof(unsigned long long)), "counts");
-      check_cuda(cudaMalloc(&h->d_energy, sizeof(long long)), "energy");
-      check_cuda(cudaMalloc(&h->d_thr, (kNA + kNB) * sizeof(uint32_t)), "threshold table");
-      const size_t nw = (size_t)M * M * kMaxShells * M + (size_t)M * M + (size_t)kMaxShells * M * M;
-      check_cuda(cudaMalloc(&h->d_wtab, nw * sizeof(int32_t)), "EPI table");
-      check_cuda(cudaMalloc(&h->d_flag, sizeof(int)), "flag");
-      check_cuda(cudaMemsetAsync(h->d_stats, 0, 4 * sizeof(unsigned long long), h->stream), "clear stats");
-      check_cuda(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream), "clear flag");
       init_config_device(h, comp, init_seed);
+    } catch (...) {
+      release(h);
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+int smcx_lattice_wrap(smcx_lattice** out, int kind, int nx, int ny, int nz, int M, void* d_sites, size_t bytes,
+                      int storage, const smcx_sched* sched, void* stream) {
+  return guarded([&] {
+    check_create_args(out, kind, nx, ny, nz, M, storage);
+    need(d_sites != nullptr, SMCX_E_INVALID_ARG, "NULL lattice store");
+    cudaPointerAttributes attr;
+    check_cuda(cudaPointerGetAttributes(&attr, d_sites), "pointer attributes");
+    need(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged, SMCX_E_INVALID_ARG,
+         "lattice store is not device memory");
+    smcx_lattice* h = new smcx_lattice();
+    try {
+      h->owns_sites = false;
+      h->d_sites = static_cast<uint8_t*>(d_sites);
+      setup_handle(h, kind, nx, ny, nz, M, storage, sched, stream);
+      h->site_bytes = (size_t)(storage == SMCX_INT8 ? h->N : (h->N + 1) / 2);
+      need(bytes >= h->site_bytes, SMCX_E_INVALID_ARG, "lattice store smaller than the lattice");
+      validate_store(h);
+      int flag = 0;
+      check_cuda(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag download");
+      check_cuda(cudaStreamSynchronize(h->stream), "validate sync");
+      need(flag == 0, SMCX_E_INVALID_ARG, "lattice store holds species ids outside 0..M-1");
     } catch (...) {
       release(h);
       delete h;

@@ -262,6 +262,19 @@ __global__ void k_unpack(const uint8_t* sites, long long first, long long count,
     ids[i] = (int8_t)load_site(sites, first + i, storage);
 }
 
+__global__ void k_validate_store(const uint8_t* sites, long long count, int storage, int M, int* flag) {
+  int bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= (load_site(sites, i, storage) >= M);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+void validate_store(smcx_lattice* hd) {
+  k_validate_store<<<1024, 256, 0, hd->stream>>>(hd->d_sites, hd->N, hd->storage, hd->M, hd->d_flag);
+  check_cuda(cudaGetLastError(), "validate launch");
+}
+
 void validate_int8(smcx_lattice* hd, const int8_t* d_ids, int64_t count) {
   k_validate<<<1024, 256, 0, hd->stream>>>(d_ids, count, hd->M, hd->d_flag);
   check_cuda(cudaGetLastError(), "validate launch");

@@ -110,6 +110,7 @@ struct smcx_lattice {
 
   uint8_t* d_sites = nullptr;
   size_t site_bytes = 0;
+  bool owns_sites = true;                 // false for a handle made by smcx_lattice_wrap
   unsigned long long* d_stats = nullptr;  // [4] trials, accepts, same, sum dE
   unsigned long long* d_counts = nullptr; // [K*M*M] reduction output
   long long* d_energy = nullptr;          // [1]
@@ -133,6 +134,7 @@ namespace smcx {
 // Kernels' host launchers (implemented in the .cu files).
 void init_config_device(smcx_lattice* h, const double* comp, uint64_t seed);
 void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // sets d_flag
+void validate_store(smcx_lattice* h);  // every stored id < M, else sets d_flag
 void pack_from_int8(smcx_lattice* h, const int8_t* d_ids, int64_t first, int64_t count);
 void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count);
 void pair_counts_device(smcx_lattice* h);          // fills h->d_counts

@@ -39,6 +39,8 @@ _lib = None
 _SIGS = {
     "smcx_last_error": (C.c_char_p, []),
     "smcx_version": (C.c_int, []),
+    "smcx_lattice_wrap": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -154,6 +156,26 @@ class Lattice:
         _check(lib().smcx_lattice_create(C.byref(h), kind, *self.dims, self.M, _p(c), int(init_seed), storage,
                                          sp, _stream_ptr(stream)))
         self._h = h
+
+    @classmethod
+    def wrap(cls, kind, dims, M, ptr, nbytes, storage=INT8, sched=None, stream=None, owner=None):
+        """Handle over a caller-held device lattice store (smcx_lattice_wrap);
+        `owner` (e.g. the torch tensor behind ptr) is kept alive with it."""
+        self = cls.__new__(cls)
+        self.kind, self.dims, self.M, self.storage = kind, tuple(int(d) for d in dims), int(M), storage
+        self.m = 2 if kind == BCC else 4
+        self.N = self.dims[0] * self.dims[1] * self.dims[2] * self.m
+        self.K = 0
+        self._owner = owner
+        h = C.c_void_p()
+        sp = None
+        if sched is not None:
+            s = Sched(int(sched[0]), (C.c_int32 * 3)(*[int(t) for t in sched[1]]))
+            sp = C.byref(s)
+        _check(lib().smcx_lattice_wrap(C.byref(h), kind, *self.dims, self.M, C.c_void_p(int(ptr)), int(nbytes),
+                                       storage, sp, _stream_ptr(stream)))
+        self._h = h
+        return self
 
     # -- lifetime --------------------------------------------------------
     def close(self):

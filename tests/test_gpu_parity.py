@@ -217,3 +217,56 @@ def test_shared_direction_proposals(stream, case, kernel):
     rst = O.sweep(kind, dims, M, K, V, ref, T, n, 4, replica=3, L=sched[0], nt=sched[1], proposal=1)
     assert (lat.get_config() == ref).all()
     assert lat.state()[1].tolist() == rst.tolist()
+
+
+@pytest.mark.parametrize("storage", [smcx.INT8, smcx.PACKED4], ids=["int8", "packed4"])
+def test_wrap_caller_store_in_place(stream, storage):
+    """smcx_lattice_wrap sweeps a caller-held device buffer in place; the
+    buffer then holds the oracle's configuration."""
+    kind, K, dims, M = smcx.BCC, 4, (12, 12, 12), 4
+    V = epi_gaussian(K, M, 20.0, 3)
+    cfg = O.init_config(kind, dims, M, [0.25] * 4, 9)
+    if storage == smcx.INT8:
+        buf = torch.from_numpy(cfg.copy()).to("cuda")
+    else:
+        u = cfg.astype(np.uint8)
+        buf = torch.from_numpy((u[0::2] | (u[1::2] << 4)).astype(np.uint8)).to("cuda")
+    torch.cuda.synchronize()
+    lat = smcx.Lattice.wrap(kind, dims, M, buf.data_ptr(), buf.numel(), storage=storage,
+                            sched=(3, (4, 4, 4)), stream=stream, owner=buf)
+    lat.set_epi(V)
+    lat.sweep(1000.0, 2, 5)
+    lat.synchronize()
+    ref = cfg.copy()
+    st = O.sweep(kind, dims, M, K, V, ref, 1000.0, 2, 5, L=3, nt=(4, 4, 4))
+    host = buf.cpu().numpy()
+    if storage == smcx.INT8:
+        got = host.view(np.int8)
+    else:
+        got = np.empty(cfg.size, np.int8)
+        got[0::2] = host & 15
+        got[1::2] = host >> 4
+    assert (got == ref).all()
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[1].tolist() == st.tolist()
+    assert lat.energy() == O.energy(kind, dims, M, K, V, ref)
+    lat.close()
+    assert buf.numel() > 0  # the caller's buffer survives the handle
+
+
+def test_wrap_rejects_bad_store(stream):
+    dims, M = (8, 8, 8), 4
+    N = 2 * 8 * 8 * 8
+    bad = torch.zeros(N, dtype=torch.int8, device="cuda")
+    bad[N - 1] = 4  # species id >= M
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice.wrap(smcx.BCC, dims, M, bad.data_ptr(), bad.numel(), stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG
+    ok = torch.zeros(N, dtype=torch.int8, device="cuda")
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice.wrap(smcx.BCC, dims, M, ok.data_ptr(), N - 1, stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG
+    host = np.zeros(N, np.int8)
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.Lattice.wrap(smcx.BCC, dims, M, host.ctypes.data, N, stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG
