@@ -47,6 +47,8 @@ def lib():
         L.orc_schedule_check.argtypes = [i32] * 9
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_sweep_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp, i32])
+        L.orc_local_energy2.argtypes = [i32] * 6 + [vp, vp, vp]
+        L.orc_clusters.argtypes = [i32] * 6 + [vp, vp, i64, vp, vp]
         L.orc_exchange_round.argtypes = [i32, vp, vp, vp, u64, u64, vp]
         L.orc_sweep_parallel.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp,
                                                       i32, vp])
@@ -197,6 +199,43 @@ def sweep_parallel(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, repl
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
     return st, int(used[0])
+
+
+def local_energy2(kind, dims, M, K, V, sigma):
+    """Twice the local energy of every site (int64 [N], 0.01 meV)."""
+    N = n_sites(kind, dims)
+    Vv = np.ascontiguousarray(V, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    out = np.zeros(N, np.int64)
+    if lib().orc_local_energy2(kind, *dims, M, K, _p(Vv), _p(s), _p(out)):
+        raise ValueError("oracle local energy rejected the request")
+    return out
+
+
+def clusters(kind, dims, M, K, V, sigma, thr2):
+    """Cluster labels (smallest site id of each cluster) and their count."""
+    N = n_sites(kind, dims)
+    Vv = np.ascontiguousarray(V, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    lab = np.zeros(N, np.int64)
+    nc = np.zeros(1, np.int64)
+    if lib().orc_clusters(kind, *dims, M, K, _p(Vv), _p(s), int(thr2), _p(lab), _p(nc)):
+        raise ValueError("oracle clusters rejected the request")
+    return lab, int(nc[0])
+
+
+def cluster_summary(labels, sigma, M, min_size):
+    """Clusters of at least min_size sites, largest first (ties: smaller
+    label first): (labels, sizes, species counts [n][M])."""
+    roots, size = np.unique(labels, return_counts=True)
+    keep = size >= min_size
+    roots, size = roots[keep], size[keep]
+    order = np.lexsort((roots, -size))
+    roots, size = roots[order], size[order]
+    counts = np.zeros((roots.size, M), np.int64)
+    for j, r in enumerate(roots):
+        counts[j] = np.bincount(np.asarray(sigma)[labels == r], minlength=M)[:M]
+    return roots, size, counts
 
 
 def exchange_round(T_slot, E, slot_rep, rnd, seed, accepts=None):

@@ -888,3 +888,72 @@ int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* s
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Local-energy field and clusters (Results, FeCoNiAlTi one-billion-    */
+/* atom section; Method "MC simulation": the local energy of every site */
+/* is computed, an energy threshold decides which sites go together,    */
+/* and union-find collects the clusters).                               */
+/*   e2[i] = 2 E_i = sum_k sum_{v in shell k} V_k[s_i][s_{i+v}], so the  */
+/*   local energies (Eq. Linear_EPI without bias terms) add up to E.    */
+/*   Site class = (e2[i] < thr2).  Two shell-1 neighbours of one class  */
+/*   are in one cluster; a cluster is labelled by its smallest site id. */
+/* ------------------------------------------------------------------ */
+int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                      int64_t* e2) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  for (int64_t s = 0; s < N; s++) {
+    int64_t acc = 0;
+    for (int k = 0; k < K; k++)
+      for (int i = S.start[k]; i < S.start[k + 1]; i++) {
+        int64_t t = orc_neighbour(kind, nx, ny, nz, s, S.v[i]);
+        acc += V[((int64_t)k * M + sigma[s]) * M + sigma[t]];
+      }
+    e2[s] = acc;
+  }
+  return 0;
+}
+
+/* Breadth-first search from every unvisited site in increasing id order:
+ * the start of each search is the smallest id of its cluster. */
+int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                 int64_t thr2, int64_t* labels, int64_t* n_clusters) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t* e2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  if (!e2 || !queue) {
+    free(e2);
+    free(queue);
+    return -1;
+  }
+  orc_local_energy2(kind, nx, ny, nz, M, K, V, sigma, e2);
+  for (int64_t s = 0; s < N; s++) labels[s] = -1;
+  int64_t nc = 0;
+  for (int64_t s0 = 0; s0 < N; s0++) {
+    if (labels[s0] >= 0) continue;
+    nc++;
+    int cls = e2[s0] < thr2;
+    int64_t head = 0, tail = 0;
+    queue[tail++] = s0;
+    labels[s0] = s0;
+    while (head < tail) {
+      int64_t s = queue[head++];
+      for (int i = S.start[0]; i < S.start[1]; i++) {
+        int64_t t = orc_neighbour(kind, nx, ny, nz, s, S.v[i]);
+        if (labels[t] >= 0 || (e2[t] < thr2) != cls) continue;
+        labels[t] = s0;
+        queue[tail++] = t;
+      }
+    }
+  }
+  *n_clusters = nc;
+  free(e2);
+  free(queue);
+  return 0;
+}

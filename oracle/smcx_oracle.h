@@ -133,6 +133,16 @@ int64_t orc_phase_of(int kind, int nx, int ny, int nz, int L, int ntx, int nty,
 int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* slot_rep, uint64_t round,
                        uint64_t seed, int64_t* accepts);
 
+/* Twice the local energy of every site, e2 [N] (0.01 meV):
+ * e2[i] = sum_k sum_{v in shell k} V_k[s_i][s_{i+v}]; sum_i e2[i] = 2 E. */
+int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                      int64_t* e2);
+
+/* Clusters: class(i) = e2[i] < thr2; shell-1 neighbours of one class are
+ * connected; labels [N] = smallest site id of the cluster; *n_clusters. */
+int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                 int64_t thr2, int64_t* labels, int64_t* n_clusters);
+
 #ifdef __cplusplus
 }
 #endif
