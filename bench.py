@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-shared", action="store_true")
+    ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -264,6 +265,96 @@ def run_batched(stream):
             "plain": "64 handles, one smcx_sweep call each (8 tile-colour launches per sweep)",
             "workload": "64 BCC cubic lattices, edges U{24..96} (seed 1), 4 species, shared 4-shell EPI, "
                         "T log-spaced 300-3000 K, int8 storage"}
+
+
+EX_R, EX_EDGE, EX_ROUNDS, EX_SPR = 32, 48, 40, 10
+
+
+def run_exchange(stream):
+    """Replica exchange: 32 BCC 48^3 replicas (221,184 sites each) on
+    temperature slots 600-1400 K (linear), 40 rounds of 10 batched sweeps +
+    one exchange step, against the same 400 batched sweeps with no exchange."""
+    import time as _t
+
+    import torch
+    from paper_2503_12591_gb300 import smcx
+
+    V = epi_gaussian(4, 4, 20.0, 1)
+    T_slot = np.linspace(600.0, 1400.0, EX_R)
+
+    def make(r):
+        lat = smcx.Lattice(smcx.BCC, (EX_EDGE,) * 3, 4, equiatomic(4), init_seed=2000 + r, storage=smcx.INT8,
+                           stream=stream)
+        lat.set_replica(r)
+        lat.set_epi(V)
+        return lat
+
+    lats = [make(r) for r in range(EX_R)]
+    sites = sum(l.N for l in lats)
+    b = smcx.Batch(lats, stream)
+    rep, ctr, acc = b.exchange(T_slot, np.arange(EX_R), 2, EX_SPR, SEED)  # warm-up, graph capture
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    rep, ctr, acc = b.exchange(T_slot, rep, EX_ROUNDS, EX_SPR, SEED, round_ctr=ctr, accepts=acc)
+    torch.cuda.synchronize()
+    s_ex = _t.perf_counter() - t0
+    T_rep = np.empty(EX_R)
+    T_rep[rep] = T_slot
+    b.sweep(T_rep, EX_SPR, SEED)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    for _ in range(EX_ROUNDS):
+        b.sweep(T_rep, EX_SPR, SEED)
+    torch.cuda.synchronize()
+    s_plain = _t.perf_counter() - t0
+    b.close()
+    for l in lats:
+        l.close()
+    att = sites * EX_ROUNDS * EX_SPR
+    n_prop = sum(len(range(i & 1, EX_R - 1, 2)) for i in range(ctr))  # proposals since round 0
+    return {"value": att / s_ex, "unit": UNIT, "no_exchange_value": att / s_plain, "overhead": s_ex / s_plain,
+            "exchange_acceptance": float(acc.sum()) / max(1, n_prop),
+            "replicas": EX_R, "sites": sites, "rounds": EX_ROUNDS, "sweeps_per_round": EX_SPR,
+            "workload": f"{EX_R} x BCC {EX_EDGE}^3 int8, shared 4-shell EPI, T slots 600-1400 K linear; "
+                        "host wall time per round: batched sweeps + exact energies + exchange step"}
+
+
+def run_clusters(stream):
+    """Local-energy field and union-find clusters on the FCC 400^3 scale
+    workload (256M sites, 5 species, packed 4-bit) after one sweep at 1200 K,
+    threshold = median of a 1/97 sample of 2 E_i; CUDA events on the stream."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W
+
+    lat = smcx.Lattice(W.kind, W.dims, W.M, W.comp, init_seed=W.init_seed, storage=W.storage, stream=stream)
+    lat.set_epi(W.epi())
+    lat.sweep(W.temperatures[0], 1, W.seed)
+    N = lat.N
+    e2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    lat.local_energy(e2.data_ptr())  # warm-up
+    lat.synchronize()
+    thr = int(torch.kthvalue(e2[::97].cpu(), e2[::97].numel() // 2).values.item())
+    lat.clusters(thr, lab.data_ptr())
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    lat.local_energy(e2.data_ptr())
+    ev[1].record(stream)
+    nc = lat.clusters(thr, lab.data_ptr())
+    ev[2].record(stream)
+    roots, sizes, _ = lat.cluster_summary(lab.data_ptr(), 100, 16)
+    ev[3].record(stream)
+    ev[3].synchronize()
+    ms_e, ms_c, ms_s = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]))
+    lat.close()
+    return {"sites": N, "ms_local_energy": ms_e, "ms_clusters": ms_c, "ms_summary": ms_s,
+            "local_energy_sites_per_s": N / (ms_e / 1e3), "clusters_sites_per_s": N / (ms_c / 1e3),
+            "n_clusters": nc, "largest": [int(x) for x in sizes[:5]],
+            "workload": "FCC 400^3 = 256M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI N(0,30 meV), "
+                        "packed 4-bit, one sweep at 1200 K; class = 2E_i < median; shell-1 connectivity; "
+                        "clusters = local energies + union-find + compression; summary >= 100 sites"}
 
 
 def run_gradient(stream):
@@ -541,8 +632,11 @@ def run_smcx(args, rank, world, local_rank):
         out["shared_direction"] = shared
     if not args.no_batched and world == 1:
         out["batched"] = run_batched(stream)
+        out["replica_exchange"] = run_exchange(stream)
     if not args.no_grad and world == 1:
         out["gradient"] = run_gradient(stream)
+    if not args.no_clusters and world == 1:
+        out["clusters"] = run_clusters(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

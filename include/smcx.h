@@ -236,6 +236,36 @@ int smcx_pair_counts(smcx_lattice* h, int64_t* C);
  * fraction of Method Eq. quadratic_local_SRO summed over the lattice. */
 int smcx_sro(smcx_lattice* h, double* alpha);
 
+/*
+ * Local-energy field and clusters (Results, FeCoNiAlTi one-billion-atom
+ * section; Method "MC simulation": the local energy of every site, an energy
+ * threshold, union-find over neighbouring sites).  Need smcx_set_epi; the
+ * local energies must fit int32 (sum_k z_k max|V_k| < 2^31, else
+ * SMCX_E_RANGE).  All three are enqueued on the handle's stream and return
+ * after it has finished.
+ *
+ * smcx_local_energy: d_e2 (device, [N] int32, caller-owned) receives twice
+ *   the local energy of every site, 2 E_i = sum_k sum_{v in shell k}
+ *   V_k[s_i][s_{i+v}] (0.01 meV; Eq. Linear_EPI without bias terms, each bond
+ *   at both ends, so sum_i 2 E_i = 2 E), canonical site order.
+ * smcx_clusters: a site's class is (2 E_i < thr2); two shell-1 neighbours of
+ *   one class are in one cluster.  d_labels (device, [N] int32, caller-owned)
+ *   receives for every site the smallest site id of its cluster (a unique
+ *   labelling); *n_clusters (may be NULL) the number of clusters.  Needs N <
+ *   2^31 (SMCX_E_RANGE); temporary device memory N bytes.  SMCX_E_TIMEOUT if
+ *   the union-find exceeded its iteration limit (labels then undefined).
+ * smcx_cluster_summary: from labels made by smcx_clusters on this handle's
+ *   current configuration, the clusters of at least min_size sites, largest
+ *   first (ties: smaller label first), at most max_out of them: roots [max_out]
+ *   (labels), sizes [max_out], counts [max_out][M] (species counts, may be
+ *   NULL); *n_out = number written.  Temporary device memory 4 N bytes.
+ *   SMCX_E_RANGE if more than 2^26 clusters reach min_size.
+ */
+int smcx_local_energy(smcx_lattice* h, int32_t* d_e2);
+int smcx_clusters(smcx_lattice* h, int64_t thr2, int32_t* d_labels, int64_t* n_clusters);
+int smcx_cluster_summary(smcx_lattice* h, const int32_t* d_labels, int64_t min_size, int max_out, int64_t* roots,
+                         int64_t* sizes, int64_t* counts, int* n_out);
+
 /* Copy the configuration out / in as int8 species ids in canonical site
  * order (N = nx*ny*nz*m entries).  set_config checks ids < M and keeps the
  * sweep counter; it does not require the old composition. */
@@ -303,6 +333,29 @@ int smcx_batch_destroy(smcx_batch* b);
 int smcx_batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed);
 int smcx_batch_autotune(smcx_batch* b, const double* T, int trial_sweeps, int* threads);
 int smcx_batch_energy(smcx_batch* b, int64_t* E);
+
+/*
+ * Replica exchange between temperature slots (Supplementary "Parallelization
+ * opportunities": configurations at different temperatures are exchanged by
+ * a rule that keeps detailed balance).  Needs replicas of one lattice shape.
+ *   T_slot      [R] temperature of each slot (K, > 0).
+ *   slot_rep    [R] in/out: the replica at each slot, a permutation of 0..R-1.
+ *   n_rounds    rounds to run; each sweeps every replica sweeps_per_round
+ *               times at its slot's temperature (one batched launch), then
+ *               proposes swaps of the slot pairs (t, t+1), t = round mod 2,
+ *               round mod 2 + 2, ...
+ *   round_ctr   in/out cumulative round counter (selects the pairing and the
+ *               random numbers; split calls equal one call).
+ *   accepts     [R-1] in/out, may be NULL: accepted swaps per slot pair.
+ * The swap of replicas a (slot t) and c (slot t+1) is accepted when x =
+ * (beta_t - beta_{t+1}) (E_a - E_c) >= 0, beta = 1/(k_B T), E in 0.01 meV,
+ * else when u < floor(2^32 exp(x)) (capped at 2^32 - 1), u = word 0 of
+ * Philox4x32-10(counter (t, round lo, round hi, 0xC0000000), key = seed).
+ * The energies are exact (start energy + accepted dE).  Configurations stay
+ * in their replica; only the temperature assignment moves.
+ */
+int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int64_t n_rounds,
+                        int64_t sweeps_per_round, uint64_t seed, uint64_t* round_ctr, int64_t* accepts);
 int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_graph);
 int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
 

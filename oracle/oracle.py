@@ -48,6 +48,7 @@ def lib():
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_sweep_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp, i32])
         L.orc_local_energy2.argtypes = [i32] * 6 + [vp, vp, vp]
+        L.orc_local_energy2_sample.argtypes = [i32] * 6 + [vp, vp, vp, i64, vp]
         L.orc_clusters.argtypes = [i32] * 6 + [vp, vp, i64, vp, vp]
         L.orc_exchange_round.argtypes = [i32, vp, vp, vp, u64, u64, vp]
         L.orc_sweep_parallel.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp,
@@ -208,6 +209,17 @@ def local_energy2(kind, dims, M, K, V, sigma):
     s = np.ascontiguousarray(sigma, np.int8)
     out = np.zeros(N, np.int64)
     if lib().orc_local_energy2(kind, *dims, M, K, _p(Vv), _p(s), _p(out)):
+        raise ValueError("oracle local energy rejected the request")
+    return out
+
+
+def local_energy2_sample(kind, dims, M, K, V, sigma, ids):
+    """2 E_i of the listed sites only."""
+    Vv = np.ascontiguousarray(V, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    idv = np.ascontiguousarray(ids, np.int64)
+    out = np.zeros(idv.size, np.int64)
+    if lib().orc_local_energy2_sample(kind, *dims, M, K, _p(Vv), _p(s), _p(idv), idv.size, _p(out)):
         raise ValueError("oracle local energy rejected the request")
     return out
 

@@ -917,6 +917,26 @@ int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int3
   return 0;
 }
 
+/* e2 of the sites ids[0..n-1] only (same definition, for lattices too large
+ * to evaluate whole). */
+int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                             const int64_t* ids, int64_t n, int64_t* e2) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  for (int64_t j = 0; j < n; j++) {
+    int64_t s = ids[j];
+    int64_t acc = 0;
+    for (int k = 0; k < K; k++)
+      for (int i = S.start[k]; i < S.start[k + 1]; i++) {
+        int64_t t = orc_neighbour(kind, nx, ny, nz, s, S.v[i]);
+        acc += V[((int64_t)k * M + sigma[s]) * M + sigma[t]];
+      }
+    e2[j] = acc;
+  }
+  return 0;
+}
+
 /* Breadth-first search from every unvisited site in increasing id order:
  * the start of each search is the smallest id of its cluster. */
 int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,

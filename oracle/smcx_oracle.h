@@ -138,6 +138,10 @@ int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* s
 int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
                       int64_t* e2);
 
+/* e2 of the listed sites only: e2 [n] for ids [n]. */
+int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                             const int64_t* ids, int64_t n, int64_t* e2);
+
 /* Clusters: class(i) = e2[i] < thr2; shell-1 neighbours of one class are
  * connected; labels [N] = smallest site id of the cluster; *n_clusters. */
 int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,

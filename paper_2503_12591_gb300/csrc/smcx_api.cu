@@ -221,6 +221,7 @@ int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V) {
         for (int q = 0; q < M; q++)
           need(V[(k * M + p) * M + q] == V[(k * M + q) * M + p], SMCX_E_INVALID_ARG, "EPI table is not symmetric");
     Shells S = make_shells(h->kind, K);
+    check_reach(S, h->n);
     // largest |dE|: every neighbour of both sites changes by at most the
     // largest species difference of its shell, plus the s-s' bond term
     long long bound = 0;

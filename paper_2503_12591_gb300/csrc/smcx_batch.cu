@@ -405,6 +405,77 @@ void batch_autotune(smcx_batch* b, const double* T, int trial, int* best_threads
   if (best_threads) *best_threads = bestc.threads;
 }
 
+// Replica exchange (Supplementary "Parallelization opportunities": the
+// configurations at different temperatures are exchanged by a rule that
+// keeps detailed balance).  A round sweeps every replica at the temperature
+// of its slot, then proposes swaps of the slot pairs (t, t+1), t = round mod
+// 2, +2, ...; the swap of replicas a (slot t) and c (slot t+1) is accepted
+// when x = (beta_t - beta_{t+1})(E_a - E_c) >= 0, else when u <
+// floor(2^32 exp(x)) (capped at 2^32 - 1), u = word 0 of Philox(counter (t,
+// round lo, round hi, 0xC0000000), key = seed).  Energies are exact: the
+// start energy of each replica plus its accumulated accepted dE.  The O(R)
+// decision runs on the host in double, like the acceptance tables.
+void batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int64_t n_rounds,
+                    int64_t sweeps_per_round, uint64_t seed, uint64_t* round_ctr, int64_t* accepts) {
+  check_batch(b);
+  const int R = (int)b->lat.size();
+  const smcx_lattice* h0 = b->lat[0];
+  for (const smcx_lattice* h : b->lat)
+    if (h->n[0] != h0->n[0] || h->n[1] != h0->n[1] || h->n[2] != h0->n[2])
+      fail(SMCX_E_INVALID_ARG, "replica exchange needs replicas of one lattice shape");
+  std::vector<int> seen(R, 0);
+  for (int t = 0; t < R; t++) {
+    if (!(T_slot[t] > 0.0) || !std::isfinite(T_slot[t])) fail(SMCX_E_INVALID_ARG, "temperatures must be finite and > 0");
+    if (slot_rep[t] < 0 || slot_rep[t] >= R || seen[slot_rep[t]]++)
+      fail(SMCX_E_INVALID_ARG, "slot_rep must be a permutation of the replicas");
+  }
+  std::vector<long long> E(R), d0(R), dcur(R);
+  for (int r = 0; r < R; r++) {
+    int64_t e = 0;
+    int rc = smcx_energy(b->lat[r], &e);
+    if (rc != SMCX_OK) fail(rc, last_error());
+    E[r] = e;
+  }
+  auto read_dsum = [&](std::vector<long long>& out) {
+    for (int r = 0; r < R; r++)
+      check_cuda(cudaMemcpyAsync(&out[r], b->lat[r]->d_stats + 3, sizeof(long long), cudaMemcpyDeviceToHost, b->stream),
+                 "stats download");
+    check_cuda(cudaStreamSynchronize(b->stream), "stats sync");
+  };
+  read_dsum(d0);
+  std::vector<double> T(R);
+  const double kB = 8.617333262e-2;  // meV / K
+  for (int64_t i = 0; i < n_rounds; i++) {
+    for (int t = 0; t < R; t++) T[slot_rep[t]] = T_slot[t];
+    batch_sweep(b, T.data(), sweeps_per_round, seed);
+    read_dsum(dcur);
+    const uint64_t rnd = *round_ctr;
+    for (int t = (int)(rnd & 1); t + 1 < R; t += 2) {
+      const int a = slot_rep[t], c = slot_rep[t + 1];
+      const long long Ea = E[a] + dcur[a] - d0[a], Ec = E[c] + dcur[c] - d0[c];
+      const double bt = 1.0 / (kB * T_slot[t]);
+      const double bu = 1.0 / (kB * T_slot[t + 1]);
+      const double x = (bt - bu) * ((double)(Ea - Ec) * 0.01);
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)rnd, (uint32_t)(rnd >> 32), 0xC0000000u),
+                                    make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+      bool accept;
+      if (x >= 0.0) {
+        accept = true;
+      } else {
+        const double v = std::exp(x) * 4294967296.0;
+        const uint32_t thr = v >= 4294967295.0 ? 4294967295u : (uint32_t)v;
+        accept = w.x < thr;
+      }
+      if (accept) {
+        slot_rep[t] = c;
+        slot_rep[t + 1] = a;
+        if (accepts) accepts[t]++;
+      }
+    }
+    *round_ctr = rnd + 1;
+  }
+}
+
 }  // namespace smcx
 
 namespace {
@@ -466,6 +537,15 @@ int smcx_batch_energy(smcx_batch* b, int64_t* E) {
       int rc = smcx_energy(b->lat[r], E + r);
       if (rc != SMCX_OK) fail(rc, last_error());
     }
+  });
+}
+
+int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int64_t n_rounds,
+                        int64_t sweeps_per_round, uint64_t seed, uint64_t* round_ctr, int64_t* accepts) {
+  return guarded_call([&] {
+    need_(b && T_slot && slot_rep && round_ctr, SMCX_E_INVALID_ARG, "NULL argument");
+    need_(n_rounds >= 0 && sweeps_per_round >= 0, SMCX_E_INVALID_ARG, "negative round or sweep count");
+    batch_exchange(b, T_slot, slot_rep, n_rounds, sweeps_per_round, seed, round_ctr, accepts);
   });
 }
 

@@ -187,6 +187,10 @@ int smcx_pair_counts_batch(int kind, int nx, int ny, int nz, int M, int K, const
     if (!d_configs || !d_counts || B < 0) fail(SMCX_E_INVALID_ARG, "bad arguments");
     if (nx < 1 || ny < 1 || nz < 1 || M < 1 || M > 127) fail(SMCX_E_INVALID_ARG, "bad geometry");
     const Shells S = make_shells(kind, K);
+    {
+      const int n3[3] = {nx, ny, nz};
+      check_reach(S, n3);
+    }
     const long long N = (long long)nx * ny * nz * S.m;
     const int KMM = K * M * M;
     const size_t smem = (size_t)KMM * 4 + (size_t)N;

@@ -47,6 +47,21 @@ int basis_index(int kind, int rx, int ry, int rz) {
   return -1;
 }
 
+// The global-memory kernels wrap a neighbour's cell coordinate once; that is
+// exact while every shell vector moves at most n[a] cells along axis a.
+void check_reach(const Shells& S, const int n[3]) {
+  for (int b = 0; b < S.m; b++) {
+    int B[3];
+    basis_of(S.kind, b, B);
+    for (int j = 0; j < S.nv; j++)
+      for (int a = 0; a < 3; a++) {
+        const int p = B[a] + S.v[j][a];
+        const int d = (p >= 0) ? p / 2 : -((-p + 1) / 2);
+        if (d > n[a] || -d > n[a]) fail(SMCX_E_INVALID_ARG, "lattice edge shorter than the reach of the shells");
+      }
+  }
+}
+
 Shells make_shells(int kind, int K) {
   Shells s;
   s.kind = kind;

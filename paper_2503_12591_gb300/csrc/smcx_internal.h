@@ -74,6 +74,7 @@ int sites_per_cell(int kind);
 void basis_of(int kind, int b, int out[3]);
 int basis_index(int kind, int rx, int ry, int rz);
 Shells make_shells(int kind, int K);
+void check_reach(const Shells& S, const int n[3]);  // SMCX_E_INVALID_ARG if an edge < reach
 // smallest link-cell edge and tile thickness for which the checkerboard
 // phases are independent (see smcx_sched)
 int min_link_cell(const Shells& s);
@@ -135,6 +136,10 @@ namespace smcx {
 void init_config_device(smcx_lattice* h, const double* comp, uint64_t seed);
 void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // sets d_flag
 void validate_store(smcx_lattice* h);  // every stored id < M, else sets d_flag
+void local_energy_device(smcx_lattice* h, int32_t* d_e2);
+void clusters_device(smcx_lattice* h, long long thr2, int32_t* d_labels, int64_t* n_clusters);
+void cluster_summary_device(smcx_lattice* h, const int32_t* d_labels, long long min_size, int max_out,
+                            int64_t* roots, int64_t* sizes, int64_t* counts, int* n_out);
 void pack_from_int8(smcx_lattice* h, const int8_t* d_ids, int64_t first, int64_t count);
 void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count);
 void pair_counts_device(smcx_lattice* h);          // fills h->d_counts

@@ -61,6 +61,10 @@ extern "C" int smcx_energy_noalloc(int kind, int nx, int ny, int nz, int M, int 
     if (storage != SMCX_INT8 && storage != SMCX_PACKED4) fail(SMCX_E_INVALID_ARG, "unknown storage");
     if (M < 1 || M > (storage == SMCX_PACKED4 ? 15 : 127)) fail(SMCX_E_INVALID_ARG, "species count out of range");
     const Shells S = make_shells(kind, K);  // validates K
+    {
+      const int n3[3] = {nx, ny, nz};
+      check_reach(S, n3);
+    }
     const int KMM = K * M * M;
     if (KMM > kNoAllocMaxKMM)
       fail(SMCX_E_INVALID_ARG, "K*M*M = " + std::to_string(KMM) + " exceeds the fixed scratch of this entry point (" +

@@ -41,6 +41,10 @@ _SIGS = {
     "smcx_version": (C.c_int, []),
     "smcx_lattice_wrap": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_void_p, C.c_size_t, C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_local_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_clusters": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "smcx_cluster_summary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -53,6 +57,8 @@ _SIGS = {
     "smcx_batch_destroy": (C.c_int, [C.c_void_p]),
     "smcx_batch_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64]),
     "smcx_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "smcx_batch_exchange": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_uint64,
+                                      C.c_void_p, C.c_void_p]),
     "smcx_batch_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smcx_batch_set_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -156,6 +162,29 @@ class Lattice:
         _check(lib().smcx_lattice_create(C.byref(h), kind, *self.dims, self.M, _p(c), int(init_seed), storage,
                                          sp, _stream_ptr(stream)))
         self._h = h
+
+    # -- local energies and clusters (device outputs) -----------------------
+    def local_energy(self, d_e2):
+        """2 E_i of every site into the device int32 buffer at d_e2 ([N])."""
+        _check(lib().smcx_local_energy(self._h, C.c_void_p(int(d_e2))))
+
+    def clusters(self, thr2, d_labels):
+        """Cluster labels into the device int32 buffer at d_labels ([N]);
+        returns the number of clusters."""
+        n = np.zeros(1, np.int64)
+        _check(lib().smcx_clusters(self._h, int(thr2), C.c_void_p(int(d_labels)), _p(n)))
+        return int(n[0])
+
+    def cluster_summary(self, d_labels, min_size, max_out):
+        """(roots, sizes, species counts [n][M]) of the largest clusters."""
+        roots = np.zeros(max(1, max_out), np.int64)
+        sizes = np.zeros(max(1, max_out), np.int64)
+        counts = np.zeros((max(1, max_out), self.M), np.int64)
+        n = np.zeros(1, np.int32)
+        _check(lib().smcx_cluster_summary(self._h, C.c_void_p(int(d_labels)), int(min_size), int(max_out),
+                                          _p(roots), _p(sizes), _p(counts), _p(n)))
+        k = int(n[0])
+        return roots[:k], sizes[:k], counts[:k]
 
     @classmethod
     def wrap(cls, kind, dims, M, ptr, nbytes, storage=INT8, sched=None, stream=None, owner=None):
@@ -323,8 +352,19 @@ class Batch:
         _check(lib().smcx_batch_autotune(self._h, _p(T), int(trial_sweeps), _p(th)))
         return int(th[0])
 
-    def sweep_partial(self, T, seed, n_colours):
-        _check(lib().smcx_sweep_partial(self._h, float(T), int(seed), int(n_colours)))
+    def exchange(self, T_slot, slot_rep, n_rounds, sweeps_per_round, seed, round_ctr=0, accepts=None):
+        """Replica exchange (smcx_batch_exchange).  Returns (slot_rep, round
+        counter, accepts), the arrays updated copies of the inputs."""
+        T = np.ascontiguousarray(T_slot, np.float64)
+        R = len(self.lattices)
+        assert T.size == R
+        rep = np.ascontiguousarray(slot_rep, np.int32).copy()
+        ctr = np.array([round_ctr], np.uint64)
+        acc = (np.zeros(max(R - 1, 1), np.int64) if accepts is None
+               else np.ascontiguousarray(accepts, np.int64).copy())
+        _check(lib().smcx_batch_exchange(self._h, _p(T), _p(rep), int(n_rounds), int(sweeps_per_round), int(seed),
+                                         _p(ctr), _p(acc)))
+        return rep, int(ctr[0]), acc
 
     def energy(self):
         e = np.zeros(len(self.lattices), np.int64)

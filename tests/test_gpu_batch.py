@@ -103,3 +103,52 @@ def test_batch_barrier_timeout_reports_and_recovers(stream):
     torch.cuda.synchronize()
     assert lats[0].energy() == lats[0].energy()
     b.close()
+
+
+def test_replica_exchange_matches_oracle(stream):
+    """Batched sweeps with replica exchange against the oracle: per round,
+    every replica sweeps at its slot's temperature, then the slot pairs of
+    the round's parity exchange by the oracle's rule."""
+    V = epi_gaussian(4, 4, 20.0, 1)
+    dims, R, spr, n_rounds, seed = (12, 12, 12), 4, 2, 6, 21
+    sched = _sched(dims, L=3)
+    T_slot = np.array([1000.0, 1040.0, 1080.0, 1120.0])
+    lats = [_make(dims, r, V, stream, sched) for r in range(R)]
+    b = smcx.Batch(lats, stream)
+    rep, ctr, acc = b.exchange(T_slot, np.arange(R), 3, spr, seed)
+    rep, ctr, acc = b.exchange(T_slot, rep, n_rounds - 3, spr, seed, round_ctr=ctr, accepts=acc)
+    assert ctr == n_rounds
+
+    cfg = [O.init_config(O.BCC, dims, 4, [0.25] * 4, 100 + r) for r in range(R)]
+    E = np.array([O.energy(O.BCC, dims, 4, 4, V, c) for c in cfg], np.int64)
+    orep = np.arange(R, dtype=np.int32)
+    oacc = np.zeros(R - 1, np.int64)
+    for i in range(n_rounds):
+        T_rep = np.empty(R)
+        T_rep[orep] = T_slot
+        for r in range(R):
+            st = O.sweep(O.BCC, dims, 4, 4, V, cfg[r], T_rep[r], spr, seed, sweep0=i * spr, replica=r,
+                         L=sched[0], nt=sched[1])
+            E[r] += st[3]
+        O.exchange_round(T_slot, E, orep, i, seed, oacc)
+    assert rep.tolist() == orep.tolist()
+    assert acc.tolist() == oacc.tolist()
+    for r in range(R):
+        assert (lats[r].get_config() == cfg[r]).all(), f"replica {r}"
+        assert lats[r].energy() == E[r]
+    assert acc.sum() > 0  # the chosen temperatures exchange now and then
+
+
+def test_replica_exchange_rejects_bad_input(stream):
+    V = epi_gaussian(4, 4, 20.0, 1)
+    lats = [_make((12, 12, 12), 0, V, stream, _sched((12, 12, 12))),
+            _make((14, 12, 12), 1, V, stream, _sched((14, 12, 12)))]
+    b = smcx.Batch(lats, stream)
+    with pytest.raises(smcx.SmcxError):
+        b.exchange([1000.0, 1100.0], [0, 1], 1, 1, 3)  # shapes differ
+    lats2 = [_make((12, 12, 12), r, V, stream, _sched((12, 12, 12))) for r in range(2)]
+    b2 = smcx.Batch(lats2, stream)
+    with pytest.raises(smcx.SmcxError):
+        b2.exchange([1000.0, 1100.0], [0, 0], 1, 1, 3)  # not a permutation
+    with pytest.raises(smcx.SmcxError):
+        b2.exchange([1000.0, -1.0], [0, 1], 1, 1, 3)

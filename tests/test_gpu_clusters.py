@@ -1,0 +1,132 @@
+"""Local-energy field and clusters on the GPU against the oracle (Results,
+FeCoNiAlTi one-billion-atom section; Method "MC simulation").
+
+Small lattices: 2 E_i, labels, cluster count and the size/composition
+summary bit-exact.  FCC 400^3 (256M sites, the scale workload): sampled
+local energies against the oracle, the sum rule sum_i 2 E_i = 2 E, and the
+label invariants that define the clustering (labels are cluster minima,
+every same-class shell-1 pair shares a label, sampled sites).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_12591_gb300 import smcx
+from paper_2503_12591_gb300.inputs import SCALE_FCC400, epi_gaussian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.current_stream()
+
+
+CASES = [
+    (smcx.BCC, 4, (10, 9, 11), 4, smcx.INT8),
+    (smcx.BCC, 4, (12, 12, 12), 3, smcx.PACKED4),
+    (smcx.BCC, 2, (7, 8, 6), 2, smcx.INT8),
+    (smcx.FCC, 3, (6, 7, 5), 5, smcx.PACKED4),
+    (smcx.FCC, 3, (8, 8, 8), 2, smcx.INT8),
+]
+
+
+def _lattice(stream, kind, K, dims, M, storage, sweeps=0):
+    lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, init_seed=4, storage=storage, stream=stream)
+    V = epi_gaussian(K, M, 20.0, 6)
+    lat.set_epi(V)
+    if sweeps:
+        lat.set_kernel(smcx.KERNEL_GENERIC)
+        lat.sweep(600.0, sweeps, 9)
+    return lat, V
+
+
+@pytest.mark.parametrize("kind,K,dims,M,storage", CASES)
+@pytest.mark.parametrize("sweeps", [0, 6])
+def test_local_energy_clusters_summary(stream, kind, K, dims, M, storage, sweeps):
+    try:
+        lat, V = _lattice(stream, kind, K, dims, M, storage, sweeps)
+    except smcx.SmcxError as e:
+        pytest.skip(f"schedule: {e}")
+    cfg = lat.get_config()
+    N = cfg.size
+    e2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.local_energy(e2.data_ptr())
+    lat.synchronize()
+    want = O.local_energy2(kind, dims, M, K, V, cfg)
+    got = e2.cpu().numpy().astype(np.int64)
+    assert (got == want).all()
+    assert got.sum() == 2 * lat.energy()
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    for q in (0.2, 0.5, 0.8):
+        thr = int(np.quantile(want, q))
+        nc = lat.clusters(thr, lab.data_ptr())
+        olab, onc = O.clusters(kind, dims, M, K, V, cfg, thr)
+        assert nc == onc
+        glab = lab.cpu().numpy().astype(np.int64)
+        assert (glab == olab).all()
+        roots, sizes, counts = lat.cluster_summary(lab.data_ptr(), 2, 50)
+        oroots, osizes, ocounts = O.cluster_summary(olab, cfg, M, 2)
+        k = min(50, oroots.size)
+        assert roots.tolist() == oroots[:k].tolist()
+        assert sizes.tolist() == osizes[:k].tolist()
+        assert counts.tolist() == ocounts[:k].tolist()
+    lat.close()
+
+
+def test_cluster_errors(stream):
+    lat = smcx.Lattice(smcx.BCC, (8, 8, 8), 4, [0.25] * 4, stream=stream)
+    buf = torch.empty(lat.N, dtype=torch.int32, device="cuda")
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.local_energy(buf.data_ptr())
+    assert e.value.code == smcx.E_NO_EPI
+    V = np.zeros((4, 4, 4), np.int32)
+    V[:] = 200_000_000  # 50 * 2e8 > 2^31
+    lat.set_epi(V)
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.local_energy(buf.data_ptr())
+    assert e.value.code == smcx.E_RANGE
+
+
+def test_full_size_fcc400(stream):
+    w = SCALE_FCC400
+    lat = smcx.Lattice(w.kind, w.dims, w.M, w.comp, init_seed=w.init_seed, storage=w.storage, stream=stream)
+    V = w.epi()
+    lat.set_epi(V)
+    lat.sweep(w.temperatures[0], 1, w.seed)
+    N = lat.N
+    cfg = lat.get_config()
+    e2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.local_energy(e2.data_ptr())
+    lat.synchronize()
+    assert int(e2.sum(dtype=torch.int64).item()) == 2 * lat.energy()
+    ids = np.random.default_rng(1).choice(N, 64, replace=False).astype(np.int64)
+    want = O.local_energy2_sample(w.kind, w.dims, w.M, w.K, V, cfg, ids)
+    assert (e2[torch.from_numpy(ids).cuda()].cpu().numpy() == want).all()
+    thr = int(torch.kthvalue(e2[::97].cpu(), e2[::97].numel() // 2).values.item())
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    nc = lat.clusters(thr, lab.data_ptr())
+    idx = torch.arange(N, device="cuda", dtype=torch.int64)
+    l64 = lab.long()
+    assert bool((l64 <= idx).all())                 # a label is a site of the cluster below or at i
+    assert bool((l64[l64] == l64).all())            # labels are fixed points (roots)
+    assert int((l64 == idx).sum().item()) == nc     # one root per cluster
+    cls = (e2 < thr)
+    # every same-class shell-1 neighbour of sampled sites shares the label
+    z, vecs = O.shells(w.kind, 1)
+    labh = lab[torch.from_numpy(ids).cuda()].cpu().numpy()
+    clsh = cls.cpu().numpy()
+    allh = lab.cpu().numpy()
+    for j, s in enumerate(ids):
+        for v in vecs[:z[0]]:
+            t = O.neighbour(w.kind, w.dims, int(s), v)
+            if clsh[t] == clsh[s]:
+                assert allh[t] == labh[j]
+    roots, sizes, counts = lat.cluster_summary(lab.data_ptr(), 100, 10)
+    assert (np.diff(sizes) <= 0).all()
+    assert (counts.sum(1) == sizes).all()
+    for r, sz in zip(roots[:3], sizes[:3]):
+        assert int((l64 == int(r)).sum().item()) == sz
+    lat.close()

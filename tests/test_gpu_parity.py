@@ -270,3 +270,21 @@ def test_wrap_rejects_bad_store(stream):
     with pytest.raises(smcx.SmcxError) as e:
         smcx.Lattice.wrap(smcx.BCC, dims, M, host.ctypes.data, N, stream=stream)
     assert e.value.code == smcx.E_INVALID_ARG
+
+
+def test_edge_shorter_than_reach_rejected(stream):
+    """A 4-shell BCC table reaches two cells along an axis: an edge of one
+    cell is refused before any kernel runs (the gathers wrap once)."""
+    lat = smcx.Lattice(smcx.BCC, (1, 8, 8), 4, [0.25] * 4, stream=stream)
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_epi(epi_gaussian(4, 4, 20.0, 1))
+    assert e.value.code == smcx.E_INVALID_ARG
+    lat.set_epi(epi_gaussian(3, 4, 20.0, 1))  # 3 shells reach one cell: accepted
+    cfg = lat.get_config()
+    assert lat.energy() == O.energy(smcx.BCC, (1, 8, 8), 4, 3, epi_gaussian(3, 4, 20.0, 1), cfg)
+    lat.close()
+    d = torch.zeros(2 * 1 * 8 * 8, dtype=torch.int8, device="cuda")
+    with pytest.raises(smcx.SmcxError) as e:
+        smcx.energy_noalloc(smcx.BCC, (1, 8, 8), 4, smcx.INT8, epi_gaussian(4, 4, 20.0, 1), d.data_ptr(),
+                            stream=stream)
+    assert e.value.code == smcx.E_INVALID_ARG

@@ -105,3 +105,13 @@ def test_cluster_summary_by_hand():
     assert roots.tolist() == [5, 0, 2]
     assert size.tolist() == [4, 3, 2]
     assert counts.tolist() == [[2, 1, 1], [1, 2, 0], [0, 0, 2]]
+
+
+def test_sampled_local_energy_equals_full():
+    dims = (5, 4, 3)
+    N = O.n_sites(O.FCC, dims)
+    sig = np.random.default_rng(2).integers(0, 3, N).astype(np.int8)
+    V = epi_gaussian(3, 3, 20.0, 1)
+    full = O.local_energy2(O.FCC, dims, 3, 3, V, sig)
+    ids = np.array([0, 7, 100, N - 1], np.int64)
+    assert (O.local_energy2_sample(O.FCC, dims, 3, 3, V, sig, ids) == full[ids]).all()
