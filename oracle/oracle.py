@@ -50,6 +50,12 @@ def lib():
         L.orc_local_energy2.argtypes = [i32] * 6 + [vp, vp, vp]
         L.orc_local_energy2_sample.argtypes = [i32] * 6 + [vp, vp, vp, i64, vp]
         L.orc_clusters.argtypes = [i32] * 6 + [vp, vp, i64, vp, vp]
+        L.orc_energy_qsro.argtypes = [i32] * 6 + [vp, vp, vp]
+        L.orc_energy_qsro.restype = i64
+        L.orc_delta_e_qsro.argtypes = [i32] * 6 + [vp, vp, vp, i64, i32]
+        L.orc_delta_e_qsro.restype = i64
+        L.orc_schedule_check_model.argtypes = [i32] * 10
+        L.orc_sweep_qsro.argtypes = ([i32] * 6 + [vp, vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_exchange_round.argtypes = [i32, vp, vp, vp, u64, u64, vp]
         L.orc_sweep_parallel.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp,
                                                       i32, vp])
@@ -200,6 +206,41 @@ def sweep_parallel(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, repl
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
     return st, int(used[0])
+
+
+def energy_qsro(kind, dims, M, K, V, W, sigma):
+    """Energy of the qSRO model (pair part + sum_i sum_k W[k][s_i] n_k(i)^2)."""
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    e = lib().orc_energy_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(s))
+    if e == np.iinfo(np.int64).min:
+        raise ValueError("oracle rejected the request")
+    return int(e)
+
+
+def delta_e_qsro(kind, dims, M, K, V, W, sigma, s, d):
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    e = lib().orc_delta_e_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(sigma), int(s), int(d))
+    if e == np.iinfo(np.int64).min:
+        raise ValueError("oracle rejected the request")
+    return int(e)
+
+
+def schedule_check_model(kind, dims, K, L, nt, model):
+    return int(lib().orc_schedule_check_model(kind, *dims, K, L, *nt, model))
+
+
+def sweep_qsro(kind, dims, M, K, V, W, sigma, T, n_sweeps, seed, sweep0=0, replica=0, L=0, nt=(1, 1, 1)):
+    """qSRO-model sweeps in place on sigma; returns the statistics."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    st = np.zeros(4, np.int64)
+    rc = lib().orc_sweep_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(sigma), float(T), int(n_sweeps), int(seed),
+                              int(sweep0), int(replica), int(L), *[int(t) for t in nt], _p(st))
+    if rc:
+        raise ValueError(f"oracle sweep rejected the request ({rc})")
+    return st
 
 
 def local_energy2(kind, dims, M, K, V, sigma):

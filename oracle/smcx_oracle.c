@@ -365,6 +365,83 @@ int64_t orc_delta_e(int kind, int nx, int ny, int nz, int M, int K,
   return delta_e_local(kind, nx, ny, nz, M, &S, V, sigma, s, sp);
 }
 
+/* ------------------------------------------------------------------ */
+/* qSRO model (Method "The EPI and qSRO model", Eq. quadratic_local_SRO): */
+/* the pair terms plus, per site, W_k[s_i] (n_k(i))^2 over the shells,    */
+/* where n_k(i) is the number of shell-k neighbours of i with i's own     */
+/* species (the same-element pair fraction pi_m^{pp} times z_k).  W is in */
+/* 0.01 meV with the 1/z_k^2 of the pair fraction folded in, so every     */
+/* energy stays an integer; the regularisation term of the equation is   */
+/* a constant for the sampler.                                          */
+/* ------------------------------------------------------------------ */
+static int64_t qsro_site(int kind, int nx, int ny, int nz, int M, const shells_t* S, const int32_t* W,
+                         const int8_t* sigma, int64_t i) {
+  int c = sigma[i];
+  int64_t q = 0;
+  for (int k = 0; k < S->K; k++) {
+    int64_t n = 0;
+    for (int j = S->start[k]; j < S->start[k + 1]; j++)
+      if (sigma[orc_neighbour(kind, nx, ny, nz, i, S->v[j])] == c) n++;
+    q += (int64_t)W[k * M + c] * n * n;
+  }
+  return q;
+}
+
+/* The quadratic part of the energy change of swapping s and sp: the sites
+ * whose term can change are s, sp and their neighbours over all K shells
+ * (each listed once); their terms are summed before and after the swap. */
+static int64_t delta_q_local(int kind, int nx, int ny, int nz, int M, const shells_t* S, const int32_t* W,
+                             int8_t* sigma, int64_t s, int64_t sp) {
+  int64_t U[2 + 2 * 512];
+  int nu = 0;
+  int64_t cand[2] = {s, sp};
+  for (int e = 0; e < 2; e++) {
+    int64_t list[1 + 512];
+    int nl = 0;
+    list[nl++] = cand[e];
+    for (int j = 0; j < S->start[S->K]; j++) list[nl++] = orc_neighbour(kind, nx, ny, nz, cand[e], S->v[j]);
+    for (int a = 0; a < nl; a++) {
+      int dup = 0;
+      for (int b = 0; b < nu; b++)
+        if (U[b] == list[a]) {
+          dup = 1;
+          break;
+        }
+      if (!dup) U[nu++] = list[a];
+    }
+  }
+  int64_t before = 0, after = 0;
+  for (int a = 0; a < nu; a++) before += qsro_site(kind, nx, ny, nz, M, S, W, sigma, U[a]);
+  int8_t t = sigma[s];
+  sigma[s] = sigma[sp];
+  sigma[sp] = t;
+  for (int a = 0; a < nu; a++) after += qsro_site(kind, nx, ny, nz, M, S, W, sigma, U[a]);
+  sigma[sp] = sigma[s];
+  sigma[s] = t;
+  return after - before;
+}
+
+int64_t orc_energy_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                        const int8_t* sigma) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return INT64_MIN;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  int64_t e = orc_energy(kind, nx, ny, nz, M, K, V, sigma);
+  for (int64_t i = 0; i < N; i++) e += qsro_site(kind, nx, ny, nz, M, &S, W, sigma, i);
+  return e;
+}
+
+int64_t orc_delta_e_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                         int8_t* sigma, int64_t s, int dir) {
+  shells_t S;
+  if (load_shells(kind, K, &S)) return INT64_MIN;
+  if (dir < 0 || dir >= S.z[0]) return INT64_MIN;
+  int64_t sp = orc_neighbour(kind, nx, ny, nz, s, S.v[dir]);
+  return delta_e_local(kind, nx, ny, nz, M, &S, V, sigma, s, sp) +
+         delta_q_local(kind, nx, ny, nz, M, &S, W, sigma, s, sp);
+}
+
 /* Warren-Cowley SRO over ordered pairs: alpha = 1 - C_k[p][q]/(z_k N_p c_q),
  * c_q = N_q/N; 0 where a species is absent. */
 int orc_sro(int kind, int nx, int ny, int nz, int M, int K, const int8_t* sigma,
@@ -451,20 +528,26 @@ static void reaches(const shells_t* S, int* R1, int* RK) {
     }
 }
 
-int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
-                       int ntx, int nty, int ntz) {
+/* model 0 (pair model): a trial reads the sites within R1 + RK of its
+ * centre; model 1 (qSRO): within R1 + 2 RK (the environments of every site
+ * whose local energy the swap changes).  A concurrent trial writes within R1
+ * of its own centre, so two trials of one phase must be more than
+ * reach = 2 R1 + RK (model 0) or 2 R1 + 2 RK (model 1) half units apart
+ * along some axis. */
+int orc_schedule_check_model(int kind, int nx, int ny, int nz, int K, int L, int ntx, int nty, int ntz, int model) {
   shells_t S;
   if (orc_sites_per_cell(kind) == 0 || load_shells(kind, K, &S)) return -1;
   if (orc_check_geometry(kind, nx, ny, nz, K)) return -1;
+  if (model != 0 && model != 1) return -1;
   if (L == 0) return 0; /* serial */
   int R1, RK;
   reaches(&S, &R1, &RK);
-  /* same intra colour: half-unit separation >= 2L on some axis; partners
-   * move each end by <= R1, the read reach is RK. */
-  int Lmin = (2 * R1 + RK) / 2 + 1;
+  int reach = model == 1 ? 2 * R1 + 2 * RK : 2 * R1 + RK;
+  /* same intra colour: half-unit separation >= 2L on some axis */
+  int Lmin = reach / 2 + 1;
   /* same tile colour, different tiles: a whole tile of g cells between
    * them, half-unit separation >= 2g + 1. */
-  int gmin = (2 * R1 + RK - 1) / 2 + 1;
+  int gmin = (reach - 1) / 2 + 1;
   if (L < Lmin) return -2;
   int n[3] = {nx, ny, nz}, nt[3] = {ntx, nty, ntz};
   for (int a = 0; a < 3; a++) {
@@ -477,6 +560,11 @@ int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
     }
   }
   return 0;
+}
+
+int orc_schedule_check(int kind, int nx, int ny, int nz, int K, int L,
+                       int ntx, int nty, int ntz) {
+  return orc_schedule_check_model(kind, nx, ny, nz, K, L, ntx, nty, ntz, 0);
 }
 
 static void tile_bounds(int n, int nt, int i, int* start, int* size) {
@@ -530,6 +618,7 @@ typedef struct {
   uint64_t seed, sweep;
   int replica;
   int64_t* stats;
+  const int32_t* W; /* qSRO weights [K][M], NULL for the pair model */
 } attempt_ctx;
 
 /* One canonical swap trial at site s (Supplementary "Monte Carlo
@@ -548,6 +637,7 @@ static void attempt_dir(attempt_ctx* c, int64_t s, int forced_dir) {
     return;
   }
   int64_t dE = delta_e_local(c->kind, c->nx, c->ny, c->nz, c->M, c->S, c->V, c->sigma, s, sp);
+  if (c->W) dE += delta_q_local(c->kind, c->nx, c->ny, c->nz, c->M, c->S, c->W, c->sigma, s, sp);
   int accept = 0;
   if (dE <= 0)
     accept = 1;
@@ -614,6 +704,7 @@ int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t*
   c.seed = seed;
   c.replica = replica;
   c.stats = stats;
+  c.W = NULL;
   c.sweep = sweep;
   stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int x0, sx, y0, sy, z0, sz;
@@ -675,14 +766,14 @@ int orc_init_sample(int kind, int nx, int ny, int nz, int M, const double* comp,
 static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
-                      int64_t* stats, int proposal, int n_threads);
+                      int64_t* stats, int proposal, int n_threads, const int32_t* W);
 
 int orc_sweep(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
               int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
               uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
               int64_t* stats) {
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
-                    stats, 0, 1);
+                    stats, 0, 1, NULL);
 }
 
 int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
@@ -691,7 +782,7 @@ int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int
                        int64_t* stats, int proposal) {
   if (proposal != 0 && (proposal != 1 || L == 0)) return -2;
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
-                    stats, proposal, 1);
+                    stats, proposal, 1, NULL);
 }
 
 /* The same sweep with the sites of each phase split across n_threads OpenMP
@@ -712,7 +803,16 @@ int orc_sweep_parallel(int kind, int nx, int ny, int nz, int M, int K, const int
   if (L == 0) nt = 1;
   if (used) *used = nt;
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
-                    stats, 0, nt);
+                    stats, 0, nt, NULL);
+}
+
+/* Sweep of the qSRO model (W [K][M], see qsro_site); the schedule is checked
+ * against the qSRO read reach. */
+int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                   int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
+                   int ntx, int nty, int ntz, int64_t* stats) {
+  return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
+                    stats, 0, 1, W);
 }
 
 /* One sweep of the link-cell / tile schedule with each phase's sites listed
@@ -775,11 +875,11 @@ static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty
 static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                       int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                       uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
-                      int64_t* stats, int proposal, int n_threads) {
+                      int64_t* stats, int proposal, int n_threads, const int32_t* W) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
-  if (orc_schedule_check(kind, nx, ny, nz, K, L, ntx, nty, ntz)) return -2;
+  if (orc_schedule_check_model(kind, nx, ny, nz, K, L, ntx, nty, ntz, W ? 1 : 0)) return -2;
   uint32_t* A = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NA_MAX);
   uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NB);
   int nA;
@@ -804,6 +904,7 @@ static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int3
   c.seed = seed;
   c.replica = replica;
   c.stats = stats;
+  c.W = W;
   stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int64_t N = (int64_t)nx * ny * nz * m;
   if (n_threads > 1) {

@@ -147,6 +147,22 @@ int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, con
 int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
                  int64_t thr2, int64_t* labels, int64_t* n_clusters);
 
+/* qSRO model (Eq. quadratic_local_SRO, integer form): E = pair energy +
+ * sum_i sum_k W[k][s_i] n_k(i)^2, n_k(i) = shell-k neighbours of i with i's
+ * species; W [K][M] in 0.01 meV. */
+int64_t orc_energy_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                        const int8_t* sigma);
+/* Energy change of swapping s with its shell-1 neighbour dir (sigma is
+ * restored before returning). */
+int64_t orc_delta_e_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                         int8_t* sigma, int64_t s, int dir);
+/* Schedule check for model 0 (pair) or 1 (qSRO: larger read reach). */
+int orc_schedule_check_model(int kind, int nx, int ny, int nz, int K, int L, int ntx, int nty, int ntz, int model);
+/* orc_sweep for the qSRO model. */
+int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                   int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
+                   int ntx, int nty, int ntz, int64_t* stats);
+
 #ifdef __cplusplus
 }
 #endif
