@@ -170,6 +170,25 @@ int smcx_lattice_destroy(smcx_lattice* h);
  */
 int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V);
 
+/*
+ * qSRO model (Method "The EPI and qSRO model", Eq. quadratic_local_SRO), in
+ * integer form: E = the pair energy of smcx_set_epi + sum_i sum_k
+ * W[k][s_i] n_k(i)^2, where n_k(i) is the number of shell-k neighbours of
+ * site i with i's own species (the same-element pair fraction of the
+ * equation times z_k; W carries the 1/z_k^2) and W [K][M] is in 0.01 meV,
+ * K the shell count of the current EPI table.  The equation's regularisation
+ * term is a constant for the sampler and is not represented.
+ *   W = NULL returns to the pair model; smcx_set_epi also does.
+ * A trial then reads R1 + 2 R_K around its centre (the environments of every
+ * site whose term it changes), so the schedule needs larger link cells and
+ * tiles (FCC, 3 shells: L >= 4); the automatic schedule is re-chosen, an
+ * explicit one re-checked (SMCX_E_SCHEDULE).  qSRO sweeps run tiled
+ * schedules (>= 2 tiles per axis) with per-trial directions; smcx_energy
+ * includes the quadratic term.  SMCX_E_NO_EPI before smcx_set_epi;
+ * SMCX_E_RANGE if |dE| could overflow int32.
+ */
+int smcx_set_qsro(smcx_lattice* h, const int32_t* W);
+
 /* Kernel family used by smcx_sweep.  SMCX_KERNEL_AUTO (default) picks the
  * fastest kernel that supports the lattice (the shared-memory BCC kernel for
  * BCC with M <= 8 and tiles <= 20 cells); SMCX_KERNEL_GENERIC forces the

@@ -257,9 +257,49 @@ int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V) {
                "EPI upload");
     check_cuda(cudaStreamSynchronize(h->stream), "EPI upload sync");
     h->V.assign(V, V + (size_t)K * M * M);
+    h->Wq.clear();  // a new pair table returns the handle to the pair model
     h->shells = S;
     h->sched = sc;
     h->have_epi = true;
+  });
+}
+
+int smcx_set_qsro(smcx_lattice* h, const int32_t* W) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
+    Shells S = h->shells;
+    const int K = S.K, M = h->M;
+    if (W == nullptr) {
+      S.model = 0;
+    } else {
+      S.model = 1;
+      // |dE| bound: the pair part (checked by smcx_set_epi) plus, for s and
+      // s', their whole quadratic terms, and for every other site of the two
+      // environments at most two shells changing by one neighbour
+      long long pair = 0, q = 0, vmax = 0;
+      for (int k = 0; k < K; k++) {
+        long long dmax = 0, wmax = 0;
+        for (int a = 0; a < M; a++)
+          for (int b = 0; b < M; b++)
+            for (int c = 0; c < M; c++)
+              dmax = std::max(dmax, std::llabs((long long)h->V[(k * M + b) * M + c] - h->V[(k * M + a) * M + c]));
+        for (int p = 0; p < M; p++) wmax = std::max(wmax, std::llabs((long long)W[k * M + p]));
+        pair += 2LL * S.z[k] * dmax;
+        q += 4 * wmax * S.z[k] * S.z[k] + 2LL * S.nv * 2 * wmax * (2 * S.z[k] + 1);
+      }
+      for (int i = 0; i < K * M * M; i++) vmax = std::max(vmax, std::llabs((long long)h->V[i]));
+      need(pair + 4 * vmax + q < (1LL << 31) - 1, SMCX_E_RANGE, "qSRO weights too large: |dE| could overflow int32");
+    }
+    smcx_sched sc = h->sched_auto ? choose_schedule(S, h->n) : h->sched;
+    if (sc.L != 0) {
+      std::string why = schedule_problem(S, h->n, sc);
+      if (!why.empty()) fail(SMCX_E_SCHEDULE, "schedule too small for this model: " + why);
+    }
+    if (W == nullptr) h->Wq.clear();
+    else h->Wq.assign(W, W + (size_t)K * M);
+    h->shells = S;
+    h->sched = sc;
   });
 }
 
@@ -355,6 +395,7 @@ int smcx_energy(smcx_lattice* h, int64_t* E) {
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
     pair_counts_device(h);
     energy_device(h);
+    if (!h->Wq.empty()) qsro_energy_add(h);
     long long e = 0;
     check_cuda(cudaMemcpyAsync(&e, h->d_energy, 8, cudaMemcpyDeviceToHost, h->stream), "energy download");
     check_cuda(cudaStreamSynchronize(h->stream), "energy sync");

@@ -107,12 +107,15 @@ Shells make_shells(int kind, int K) {
 }
 
 // Two trials whose centres are 2L half-units apart on one axis cannot touch
-// each other's read sets when 2L - 2 R1 > RK (each partner moves <= R1, a
-// read reaches <= RK).  Across a whole tile of g cells the centres are at
-// least 2g + 1 half-units apart.
-int min_link_cell(const Shells& s) { return (2 * s.R1 + s.RK) / 2 + 1; }
-int min_tile(const Shells& s) { return (2 * s.R1 + s.RK - 1) / 2 + 1; }
-int halo_cells(const Shells& s) { return (s.R1 + s.RK + 1) / 2; }
+// each other's read sets when 2L > 2 R1 + RK (each partner moves <= R1, a
+// pair-model read reaches <= R1 + RK from the centre).  Under the qSRO model
+// a trial also reads the environments of every site whose local energy it
+// changes, R1 + 2 RK from its centre, so 2L > 2 R1 + 2 RK.  Across a whole
+// tile of g cells the centres are at least 2g + 1 half-units apart.
+static int reach_half_units(const Shells& s) { return s.model == 1 ? 2 * s.R1 + 2 * s.RK : 2 * s.R1 + s.RK; }
+int min_link_cell(const Shells& s) { return reach_half_units(s) / 2 + 1; }
+int min_tile(const Shells& s) { return (reach_half_units(s) - 1) / 2 + 1; }
+int halo_cells(const Shells& s) { return (s.R1 + (s.model == 1 ? 2 * s.RK : s.RK) + 1) / 2; }
 int ring_cells(const Shells& s) { return (s.R1 + 1) / 2; }
 
 std::string schedule_problem(const Shells& s, const int n[3], const smcx_sched& sc) {

@@ -68,6 +68,7 @@ struct Shells {
   int v[kMaxVec][3];  // half-lattice-unit vectors, shell-major, lexicographic
   int shell_of[kMaxVec];
   int R1 = 0, RK = 0; // max |component| of shell-1 vectors and of shells 1..K
+  int model = 0;      // 0: pair model; 1: qSRO (a trial reads R1 + 2 RK around its centre)
 };
 
 int sites_per_cell(int kind);
@@ -105,6 +106,7 @@ struct smcx_lattice {
   smcx::Shells shells;  // shells of the EPI in use (K = 0 before set_epi)
   bool have_epi = false;
   std::vector<int32_t> V;
+  std::vector<int32_t> Wq;  // qSRO weights [K][M] (0.01 meV); empty: pair model
   smcx_sched sched{0, {0, 0, 0}};
   bool sched_auto = true;
   cudaStream_t stream = nullptr;
@@ -137,6 +139,8 @@ void init_config_device(smcx_lattice* h, const double* comp, uint64_t seed);
 void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // sets d_flag
 void validate_store(smcx_lattice* h);  // every stored id < M, else sets d_flag
 void local_energy_device(smcx_lattice* h, int32_t* d_e2);
+void sweep_qsro_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
+void qsro_energy_add(smcx_lattice* h);  // adds sum_i sum_k W[k][s_i] n_k(i)^2 to d_energy
 void clusters_device(smcx_lattice* h, long long thr2, int32_t* d_labels, int64_t* n_clusters);
 void cluster_summary_device(smcx_lattice* h, const int32_t* d_labels, long long min_size, int max_out,
                             int64_t* roots, int64_t* sizes, int64_t* counts, int* n_out);

@@ -350,6 +350,10 @@ static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, in
 }
 
 void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
+  if (!hd->Wq.empty()) {
+    sweep_qsro_device(hd, nA, seed, n_sweeps, n_colours);
+    return;
+  }
   if (hd->kernel_choice != 1 && bcc_fast_usable(hd)) {
     sweep_bcc_fast(hd, nA, seed, n_sweeps, n_colours);
     return;

@@ -1,0 +1,491 @@
+// Sweeps of the qSRO model (Method "The EPI and qSRO model", Eq.
+// quadratic_local_SRO), integer form: the pair terms plus, for every site i,
+// sum_k W_k[s_i] n_k(i)^2, n_k(i) = number of shell-k neighbours of i with
+// i's own species (the same-element pair fraction times z_k; W carries the
+// 1/z_k^2 and is in 0.01 meV).
+//
+// The paper computes such energy changes by adding up the local energies of
+// every site in the LIZ.  Here a trial swapping a (at s) and b (at s')
+// computes the change exactly from what actually moves:
+//  * the pair part, as in the pair-model kernels;
+//  * s and s' themselves: their same-species counts before (species a at s,
+//    b at s') and after (b at s, a at s'), from the two environments that
+//    the pair part reads anyway;
+//  * every other site i of the two environments whose species c is a or b
+//    and that sees s in shell k1 and s' in shell k2 with k1 != k2: n_k1(i)
+//    changes by d1 = +1 (c = b) or -1 (c = a) and n_k2(i) by -d1, so its term
+//    changes by W_k[c] (2 d n_k(i) + 1) for those shells; n_k(i) is counted
+//    from i's own shell-k neighbours in shared memory.  Sites of other
+//    species, or seeing both ends in the same shell, do not change.
+// k2 (the shell of s' - i for i = s + v) and whether s' + v lies in the
+// environment of s are per-direction tables built on the host.
+//
+// The trial reads R1 + 2 R_K around its centre, so the schedule uses the
+// larger link cell and halo of this model (FCC with 3 shells: L >= 4, the
+// paper's 4x4x4); tiles run concurrently exactly as in k_tile_sweep.
+#include <algorithm>
+
+#include "smcx_device.cuh"
+
+namespace smcx {
+
+struct QsroTables {
+  int32_t W[kMaxShells * kMaxSweepM];  // W[k][c]
+  signed char k2[kMaxZ1][kMaxVec];      // shell of (p_dir - v_j); -1 outside K shells; -2 when zero
+  signed char in_s[kMaxZ1][kMaxVec];    // 1 when p_dir + v_j is 0 or inside the K shells
+  signed char sub[4][kMaxVec];          // sublattice of the site centre_b + v_j
+  unsigned char start[kMaxShells + 1];  // first vector of each shell
+};
+
+template <int KIND, int K>
+__global__ void __launch_bounds__(256) k_tile_sweep_qsro(const SweepParams P, const QsroTables Q) {
+  constexpr int m = cell_sites(KIND);
+  constexpr int NV = vec_count(KIND, K);
+  constexpr int Z1 = shell_size(KIND, 0);
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_stat[3];
+  __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
+  __shared__ signed char s_k2[kMaxZ1 * NV], s_ins[kMaxZ1 * NV], s_sub[4 * NV];
+  __shared__ int s_start[kMaxShells + 1];
+
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int M = P.M, KM = K * P.M, MM = P.M * P.M;
+  const int nW = MM * KM + MM;
+  int32_t* s_w = reinterpret_cast<int32_t*>(smem);
+  uint32_t* s_A = reinterpret_cast<uint32_t*>(s_w + nW);
+  uint32_t* s_B = s_A + P.nA;
+  int* s_off = reinterpret_cast<int*>(s_B + kNB);
+  int* s_poff = s_off + m * NV;
+  int* s_psub = s_poff + m * Z1;
+  int8_t* box = reinterpret_cast<int8_t*>(s_psub + m * Z1);
+
+  int bid = blockIdx.x;
+  const int jx = bid % P.ntc[0];
+  bid /= P.ntc[0];
+  const int jy = bid % P.ntc[1];
+  const int jz = bid / P.ntc[1];
+  const int ti[3] = {2 * jx + (P.tc & 1), 2 * jy + ((P.tc >> 1) & 1), 2 * jz + ((P.tc >> 2) & 1)};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = P.n[a] / P.nt[a], rem = P.n[a] % P.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+
+  if (tid < 3) s_stat[tid] = 0;
+  for (int i = tid; i < nW; i += nth) s_w[i] = P.wtab[i];
+  for (int i = tid; i < P.nA; i += nth) s_A[i] = P.thr[i];
+  for (int i = tid; i < kNB; i += nth) s_B[i] = P.thr[kNA + i];
+  for (int i = tid; i < m * NV; i += nth) s_off[i] = P.off[i / NV][i % NV];
+  for (int i = tid; i < m * Z1; i += nth) {
+    s_poff[i] = P.poff[i / Z1][i % Z1];
+    s_psub[i] = P.psub[i / Z1][i % Z1];
+  }
+  for (int i = tid; i < KM; i += nth) s_wq[i] = Q.W[i];
+  for (int i = tid; i < Z1 * NV; i += nth) {
+    s_k2[i] = Q.k2[i / NV][i % NV];
+    s_ins[i] = Q.in_s[i / NV][i % NV];
+  }
+  for (int i = tid; i < m * NV; i += nth) s_sub[i] = Q.sub[i / NV][i % NV];
+  for (int i = tid; i <= K; i += nth) s_start[i] = Q.start[i];
+
+  const int h = P.h;
+  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
+  for (int i = tid; i < ex * ey * ez; i += nth) {
+    const int xs = i % ex, r = i / ex, ys = r % ey, zs = r / ey;
+    const int gx = wrap_add(t0[0] - h, xs, P.n[0]);
+    const int gy = wrap_add(t0[1] - h, ys, P.n[1]);
+    const int gz = wrap_add(t0[2] - h, zs, P.n[2]);
+    const long long cell = ((long long)gz * P.n[1] + gy) * P.n[0] + gx;
+    const int bi = ((zs * P.BY + ys) * P.BX + xs) * m;
+    if (P.storage == SMCX_INT8) {
+#pragma unroll
+      for (int b = 0; b < m; b++) box[bi + b] = (int8_t)P.sites[cell * m + b];
+    } else {
+#pragma unroll
+      for (int q = 0; q < m / 2; q++) {
+        const uint8_t byte = P.sites[cell * (m / 2) + q];
+        box[bi + 2 * q] = (int8_t)(byte & 15);
+        box[bi + 2 * q + 1] = (int8_t)(byte >> 4);
+      }
+    }
+  }
+  __syncthreads();
+
+  // same-species neighbours of box site i (sublattice bi) in shell k
+  auto count = [&](int i, int bi, int k, int c) {
+    int n = 0;
+    const int* off = s_off + bi * NV;
+    for (int j = s_start[k]; j < s_start[k + 1]; j++) n += (box[i + off[j]] == c);
+    return n;
+  };
+
+  unsigned long long acc = 0, same = 0;
+  long long dsum = 0;
+  const int L = P.L;
+  const int nic = L * L * L * m;
+  for (int ic = 0; ic < nic; ic++) {
+    const int b = ic % m, lc = ic / m;
+    const int cx = lc % L, cy = (lc / L) % L, cz = lc / (L * L);
+    const int nxp = ts[0] > cx ? (ts[0] - cx + L - 1) / L : 0;
+    const int nyp = ts[1] > cy ? (ts[1] - cy + L - 1) / L : 0;
+    const int nzp = ts[2] > cz ? (ts[2] - cz + L - 1) / L : 0;
+    const int np = nxp * nyp * nzp;
+    for (int i = tid; i < np; i += nth) {
+      const int ix = i % nxp, r = i / nxp, iy = r % nyp, iz = r / nyp;
+      const int xr = cx + L * ix, yr = cy + L * iy, zr = cz + L * iz;
+      const int s = (((zr + h) * P.BY + (yr + h)) * P.BX + (xr + h)) * m + b;
+      const unsigned long long gid =
+          ((((unsigned long long)(t0[2] + zr)) * P.n[1] + (t0[1] + yr)) * P.n[0] + (t0[0] + xr)) * m + b;
+      const uint4 rw = attempt_block(gid, P.sweep, P.replica, P.seed_lo, P.seed_hi);
+      const uint32_t rd = (gid & 1) ? rw.z : rw.x;
+      const uint32_t ru = (gid & 1) ? rw.w : rw.y;
+      const int dir = (int)__umulhi(rd, (uint32_t)Z1);
+      const int sp = s + s_poff[b * Z1 + dir];
+      const int bp = s_psub[b * Z1 + dir];
+      const int sa = box[s], sb = box[sp];
+      if (sa == sb) {
+        same++;
+        continue;
+      }
+      // pair part, and the same-species counts of s and s'
+      const int32_t* W = s_w + (sa * M + sb) * KM;
+      int dE = s_w[MM * KM + sa * M + sb];
+      int na_s[K], nb_s[K], na_p[K], nb_p[K];
+      {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          na_s[k] = nb_s[k] = 0;
+#pragma unroll
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            const int t = s + s_off[b * NV + j];
+            const int c = box[t];
+            dE += W[k * M + c];
+            if (t != sp) {
+              na_s[k] += (c == sa);
+              nb_s[k] += (c == sb);
+            }
+          }
+        }
+      }
+      {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          na_p[k] = nb_p[k] = 0;
+#pragma unroll
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            const int t = sp + s_off[bp * NV + j];
+            const int c = box[t];
+            dE -= W[k * M + c];
+            if (t != s) {
+              na_p[k] += (c == sa);
+              nb_p[k] += (c == sb);
+            }
+          }
+        }
+      }
+      // quadratic terms of s and s' (before: a at s, b at s'; after: swapped)
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        dE += s_wq[k * M + sb] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) +
+              s_wq[k * M + sa] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
+      // other sites of the environment of s
+      {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            const int t = s + s_off[b * NV + j];
+            const int c = box[t];
+            if (c != sa && c != sb) continue;
+            const int k2 = s_k2[dir * NV + j];
+            if (k2 == -2 || k2 == k) continue;  // t is s', or sees s and s' in one shell
+            const int bt = s_sub[b * NV + j];
+            const int d1 = (c == sb) ? 1 : -1;
+            dE += s_wq[k * M + c] * (2 * d1 * count(t, bt, k, c) + 1);
+            if (k2 >= 0) dE += s_wq[k2 * M + c] * (-2 * d1 * count(t, bt, k2, c) + 1);
+          }
+        }
+      }
+      // sites that see only s'
+      {
+        int j = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            if (s_ins[dir * NV + j]) continue;
+            const int t = sp + s_off[bp * NV + j];
+            const int c = box[t];
+            if (c != sa && c != sb) continue;
+            const int d2 = (c == sb) ? -1 : 1;
+            dE += s_wq[k * M + c] * (2 * d2 * count(t, s_sub[bp * NV + j], k, c) + 1);
+          }
+        }
+      }
+      if (metropolis_accept(dE, ru, s_A, P.nA, s_B)) {
+        box[s] = (int8_t)sb;
+        box[sp] = (int8_t)sa;
+        acc++;
+        dsum += dE;
+      }
+    }
+    __syncthreads();
+  }
+
+  const int rg = P.ring;
+  const int wx = ts[0] + 2 * rg, wy = ts[1] + 2 * rg, wz = ts[2] + 2 * rg;
+  for (int i = tid; i < wx * wy * wz; i += nth) {
+    const int xw = i % wx, r = i / wx, yw = r % wy, zw = r / wy;
+    const int xs = xw + h - rg, ys = yw + h - rg, zs = zw + h - rg;
+    const int gx = wrap_add(t0[0] - rg, xw, P.n[0]);
+    const int gy = wrap_add(t0[1] - rg, yw, P.n[1]);
+    const int gz = wrap_add(t0[2] - rg, zw, P.n[2]);
+    const long long cell = ((long long)gz * P.n[1] + gy) * P.n[0] + gx;
+    const int bi = ((zs * P.BY + ys) * P.BX + xs) * m;
+    if (P.storage == SMCX_INT8) {
+#pragma unroll
+      for (int b = 0; b < m; b++) P.sites[cell * m + b] = (uint8_t)box[bi + b];
+    } else {
+#pragma unroll
+      for (int q = 0; q < m / 2; q++)
+        P.sites[cell * (m / 2) + q] = (uint8_t)(box[bi + 2 * q] | (box[bi + 2 * q + 1] << 4));
+    }
+  }
+
+  atomicAdd(&s_stat[0], acc);
+  atomicAdd(&s_stat[1], same);
+  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&P.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * m);
+    atomicAdd(&P.stats[1], s_stat[0]);
+    atomicAdd(&P.stats[2], s_stat[1]);
+    atomicAdd(&P.stats[3], s_stat[2]);
+  }
+}
+
+// sum_i sum_k W[k][s_i] n_k(i)^2 added to *E (global-memory gathers).
+template <int KIND, int K>
+__global__ void __launch_bounds__(256) k_qsro_energy(const SweepParams P, const QsroTables Q, long long* E) {
+  constexpr int m = cell_sites(KIND);
+  __shared__ long long part[8];
+  __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
+  for (int i = threadIdx.x; i < K * P.M; i += blockDim.x) s_wq[i] = Q.W[i];
+  __syncthreads();
+  const long long ncell = (long long)P.n[0] * P.n[1] * P.n[2];
+  long long acc = 0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % P.n[0]);
+    const long long r = c / P.n[0];
+    const int y = (int)(r % P.n[1]), z = (int)(r / P.n[1]);
+    for (int b = 0; b < m; b++) {
+      const int p = load_site(P.sites, c * m + b, P.storage);
+      int j = 0;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        int n = 0;
+        for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+          const signed char* d = P.gd[b][j];
+          const long long t =
+              (((long long)wrap_add(z, d[2], P.n[2]) * P.n[1] + wrap_add(y, d[1], P.n[1])) * P.n[0] +
+               wrap_add(x, d[0], P.n[0])) * m + d[3];
+          n += (load_site(P.sites, t, P.storage) == p);
+        }
+        acc += (long long)s_wq[k * P.M + p] * n * n;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) t += part[w];
+    atomicAdd(reinterpret_cast<unsigned long long*>(E), (unsigned long long)t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+
+void fill_offsets_global(const smcx_lattice* hd, SweepParams& P);
+
+namespace {
+
+int shell_index(const Shells& S, int x, int y, int z) {
+  for (int j = 0; j < S.nv; j++)
+    if (S.v[j][0] == x && S.v[j][1] == y && S.v[j][2] == z) return S.shell_of[j];
+  return -1;
+}
+
+QsroTables make_tables(const smcx_lattice* hd) {
+  QsroTables T;
+  memset(&T, 0, sizeof(T));
+  const Shells& S = hd->shells;
+  for (size_t i = 0; i < hd->Wq.size(); i++) T.W[i] = hd->Wq[i];
+  for (int d = 0; d < S.z[0]; d++)
+    for (int j = 0; j < S.nv; j++) {
+      const int* p = S.v[d];
+      const int* v = S.v[j];
+      const int ux = p[0] - v[0], uy = p[1] - v[1], uz = p[2] - v[2];
+      T.k2[d][j] = (ux == 0 && uy == 0 && uz == 0) ? -2 : (signed char)shell_index(S, ux, uy, uz);
+      const int wx = p[0] + v[0], wy = p[1] + v[1], wz = p[2] + v[2];
+      T.in_s[d][j] = ((wx == 0 && wy == 0 && wz == 0) || shell_index(S, wx, wy, wz) >= 0) ? 1 : 0;
+    }
+  for (int b = 0; b < hd->m; b++) {
+    int B[3];
+    basis_of(hd->kind, b, B);
+    for (int j = 0; j < S.nv; j++) {
+      int r[3];
+      for (int a = 0; a < 3; a++) {
+        const int q = B[a] + S.v[j][a];
+        const int d = (q >= 0) ? q / 2 : -((-q + 1) / 2);
+        r[a] = q - 2 * d;
+      }
+      T.sub[b][j] = (signed char)basis_index(hd->kind, r[0], r[1], r[2]);
+    }
+  }
+  int o = 0;
+  for (int k = 0; k < S.K; k++) {
+    T.start[k] = (unsigned char)o;
+    o += S.z[k];
+  }
+  T.start[S.K] = (unsigned char)o;
+  return T;
+}
+
+void fill_tile_offsets(const smcx_lattice* hd, SweepParams& P) {
+  const Shells& S = hd->shells;
+  const int m = hd->m;
+  for (int b = 0; b < m; b++) {
+    int B[3];
+    basis_of(hd->kind, b, B);
+    for (int j = 0; j < S.nv; j++) {
+      int d[3], r[3];
+      for (int a = 0; a < 3; a++) {
+        const int q = B[a] + S.v[j][a];
+        d[a] = (q >= 0) ? q / 2 : -((-q + 1) / 2);
+        r[a] = q - 2 * d[a];
+      }
+      const int bb = basis_index(hd->kind, r[0], r[1], r[2]);
+      P.off[b][j] = ((d[2] * P.BY + d[1]) * P.BX + d[0]) * m + (bb - b);
+      if (j < S.z[0]) {
+        P.poff[b][j] = P.off[b][j];
+        P.psub[b][j] = bb;
+      }
+    }
+  }
+}
+
+template <int KIND, int K>
+void launch_qsro(smcx_lattice* hd, SweepParams& P, const QsroTables& T, int64_t n_sweeps, int n_colours) {
+  constexpr int m = cell_sites(KIND);
+  constexpr int NV = vec_count(KIND, K);
+  constexpr int Z1 = shell_size(KIND, 0);
+  const int nW = P.M * P.M * K * P.M + P.M * P.M;
+  const size_t smem = (size_t)(nW + P.nA + kNB + m * NV + 2 * m * Z1) * 4 + (size_t)P.BX * P.BY * P.BZ * m;
+  if (smem > 200 * 1024) fail(SMCX_E_UNSUPPORTED, "tile too large for shared memory");
+  check_cuda(cudaFuncSetAttribute(k_tile_sweep_qsro<KIND, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem),
+             "qSRO sweep smem attribute");
+  for (int64_t s = 0; s < n_sweeps; s++) {
+    P.sweep = hd->sweep_cum + (uint64_t)s;
+    for (int tc = 0; tc < n_colours; tc++) {
+      P.tc = tc;
+      const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
+      k_tile_sweep_qsro<KIND, K><<<grid, 256, smem, hd->stream>>>(P, T);
+    }
+  }
+  check_cuda(cudaGetLastError(), "qSRO sweep launch");
+}
+
+}  // namespace
+
+void sweep_qsro_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
+  const smcx_sched& sc = hd->sched;
+  if (hd->proposal != SMCX_PROPOSAL_SITE) fail(SMCX_E_UNSUPPORTED, "qSRO sweeps use per-trial directions");
+  for (int a = 0; a < 3; a++)
+    if (sc.nt[a] < 2) fail(SMCX_E_UNSUPPORTED, "qSRO sweeps run tiled schedules (>= 2 tiles per axis)");
+  SweepParams P;
+  memset(&P, 0, sizeof(P));
+  P.sites = hd->d_sites;
+  P.thr = hd->d_thr;
+  P.wtab = hd->d_wtab;
+  P.stats = hd->d_stats;
+  for (int a = 0; a < 3; a++) {
+    P.n[a] = hd->n[a];
+    P.nt[a] = sc.nt[a];
+    P.ntc[a] = sc.nt[a] / 2;
+  }
+  P.L = sc.L;
+  P.h = halo_cells(hd->shells);
+  P.ring = ring_cells(hd->shells);
+  int tmax[3];
+  for (int a = 0; a < 3; a++) tmax[a] = (hd->n[a] + sc.nt[a] - 1) / sc.nt[a];
+  P.BX = tmax[0] + 2 * P.h;
+  P.BY = tmax[1] + 2 * P.h;
+  P.BZ = tmax[2] + 2 * P.h;
+  P.M = hd->M;
+  P.nA = nA;
+  P.storage = hd->storage;
+  P.replica = hd->replica;
+  P.seed_lo = (uint32_t)seed;
+  P.seed_hi = (uint32_t)(seed >> 32);
+  fill_tile_offsets(hd, P);
+  const QsroTables T = make_tables(hd);
+  const int K = hd->shells.K;
+  if (hd->kind == kBCC) {
+    switch (K) {
+      case 1: launch_qsro<kBCC, 1>(hd, P, T, n_sweeps, n_colours); break;
+      case 2: launch_qsro<kBCC, 2>(hd, P, T, n_sweeps, n_colours); break;
+      case 3: launch_qsro<kBCC, 3>(hd, P, T, n_sweeps, n_colours); break;
+      default: launch_qsro<kBCC, 4>(hd, P, T, n_sweeps, n_colours); break;
+    }
+  } else {
+    switch (K) {
+      case 1: launch_qsro<kFCC, 1>(hd, P, T, n_sweeps, n_colours); break;
+      case 2: launch_qsro<kFCC, 2>(hd, P, T, n_sweeps, n_colours); break;
+      default: launch_qsro<kFCC, 3>(hd, P, T, n_sweeps, n_colours); break;
+    }
+  }
+}
+
+void qsro_energy_add(smcx_lattice* hd) {
+  SweepParams P;
+  memset(&P, 0, sizeof(P));
+  P.sites = hd->d_sites;
+  P.M = hd->M;
+  P.storage = hd->storage;
+  for (int a = 0; a < 3; a++) P.n[a] = hd->n[a];
+  fill_offsets_global(hd, P);
+  const QsroTables T = make_tables(hd);
+  int dev = 0, nsm = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  const long long ncell = (long long)hd->n[0] * hd->n[1] * hd->n[2];
+  const int grid = (int)std::max<long long>(1, std::min<long long>((ncell + 255) / 256, (long long)nsm * 8));
+  const int K = hd->shells.K;
+  auto go = [&](auto kern) { kern<<<grid, 256, 0, hd->stream>>>(P, T, hd->d_energy); };
+  if (hd->kind == kBCC) {
+    switch (K) {
+      case 1: go(k_qsro_energy<kBCC, 1>); break;
+      case 2: go(k_qsro_energy<kBCC, 2>); break;
+      case 3: go(k_qsro_energy<kBCC, 3>); break;
+      default: go(k_qsro_energy<kBCC, 4>); break;
+    }
+  } else {
+    switch (K) {
+      case 1: go(k_qsro_energy<kFCC, 1>); break;
+      case 2: go(k_qsro_energy<kFCC, 2>); break;
+      default: go(k_qsro_energy<kFCC, 3>); break;
+    }
+  }
+  check_cuda(cudaGetLastError(), "qSRO energy launch");
+}
+
+}  // namespace smcx

@@ -45,6 +45,7 @@ _SIGS = {
     "smcx_clusters": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "smcx_cluster_summary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
+    "smcx_set_qsro": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -231,6 +232,16 @@ class Lattice:
         assert V.shape == (K, self.M, self.M)
         _check(lib().smcx_set_epi(self._h, K, _p(V)))
         self.K = K
+
+    def set_qsro(self, W):
+        """qSRO weights W [K][M] (0.01 meV), or None for the pair model."""
+        if W is None:
+            _check(lib().smcx_set_qsro(self._h, None))
+        else:
+            W = np.ascontiguousarray(W, np.int32)
+            if self.K and W.shape != (self.K, self.M):
+                raise ValueError(f"W must have shape ({self.K}, {self.M})")
+            _check(lib().smcx_set_qsro(self._h, _p(W)))
 
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))

@@ -1,0 +1,100 @@
+"""qSRO-model sweeps on the GPU against the oracle (Method "The EPI and qSRO
+model", Eq. quadratic_local_SRO, integer form): configuration, trial
+statistics and energy bit-exact after several sweeps, for FCC (the paper's
+qSRO system, 4x4x4 link cells) and BCC, both storages, explicit and
+automatic schedules; the energy change equals the sum of accepted dE."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_12591_gb300 import smcx
+from paper_2503_12591_gb300.inputs import epi_gaussian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.current_stream()
+
+
+def _w(K, M, seed, scale=300):
+    return np.random.default_rng(seed).integers(-scale, scale + 1, (K, M)).astype(np.int32)
+
+
+CASES = [
+    # kind, K, dims, M, storage, schedule (None = library choice), T, sweeps
+    (smcx.FCC, 3, (12, 8, 8), 4, smcx.INT8, (4, (4, 2, 2)), 1000.0, 3),
+    (smcx.FCC, 3, (16, 12, 14), 5, smcx.PACKED4, None, 1200.0, 2),
+    (smcx.FCC, 2, (10, 12, 8), 3, smcx.PACKED4, (4, (2, 2, 2)), 800.0, 3),
+    (smcx.BCC, 2, (12, 12, 12), 4, smcx.INT8, (4, (4, 4, 4)), 1000.0, 3),
+    (smcx.BCC, 4, (20, 16, 16), 4, smcx.PACKED4, None, 1500.0, 2),
+]
+
+
+@pytest.mark.parametrize("kind,K,dims,M,storage,sched,T,n", CASES)
+def test_qsro_sweep_bit_exact(stream, kind, K, dims, M, storage, sched, T, n):
+    V = epi_gaussian(K, M, 20.0, 11)
+    W = _w(K, M, 12)
+    lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, init_seed=5, storage=storage, sched=sched, stream=stream)
+    lat.set_epi(V)
+    lat.set_qsro(W)
+    L, nt = lat.schedule()
+    assert O.schedule_check_model(kind, dims, K, L, nt, 1) == 0
+    cfg = lat.get_config()
+    E0 = lat.energy()
+    assert E0 == O.energy_qsro(kind, dims, M, K, V, W, cfg)
+    lat.sweep(T, n, 21)
+    got = lat.get_config()
+    _, st = lat.state()
+    ref = cfg.copy()
+    rst = O.sweep_qsro(kind, dims, M, K, V, W, ref, T, n, 21, L=L, nt=nt)
+    assert (got == ref).all()
+    assert st.tolist() == rst.tolist()
+    assert lat.energy() == O.energy_qsro(kind, dims, M, K, V, W, ref) == E0 + st[3]
+    lat.close()
+
+
+def test_qsro_schedule_rules(stream):
+    V = epi_gaussian(3, 4, 20.0, 1)
+    # a link cell of 3 serves the pair model but not qSRO on FCC
+    lat = smcx.Lattice(smcx.FCC, (12, 12, 12), 4, [0.25] * 4, sched=(3, (4, 4, 4)), stream=stream)
+    lat.set_epi(V)
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_qsro(_w(3, 4, 1))
+    assert e.value.code == smcx.E_SCHEDULE
+    lat.close()
+    # automatic schedule grows to L = 4; W = None returns to the pair model
+    lat = smcx.Lattice(smcx.FCC, (16, 16, 16), 4, [0.25] * 4, stream=stream)
+    lat.set_epi(V)
+    assert lat.schedule()[0] == 3
+    lat.set_qsro(_w(3, 4, 1))
+    assert lat.schedule()[0] == 4
+    lat.set_qsro(None)
+    assert lat.schedule()[0] == 3
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_qsro(np.full((3, 4), 2_000_000, np.int32))
+    assert e.value.code == smcx.E_RANGE
+    lat.close()
+    lat = smcx.Lattice(smcx.FCC, (8, 8, 8), 4, [0.25] * 4, stream=stream)
+    with pytest.raises(smcx.SmcxError) as e:
+        lat.set_qsro(np.zeros((3, 4), np.int32))
+    assert e.value.code == smcx.E_NO_EPI
+    lat.close()
+
+
+def test_qsro_zero_weights_equal_pair_model(stream):
+    """W = 0 gives the pair model's trajectory through the qSRO kernel."""
+    kind, K, dims, M = smcx.FCC, 3, (12, 12, 12), 4
+    V = epi_gaussian(K, M, 20.0, 3)
+    a = smcx.Lattice(kind, dims, M, [0.25] * 4, init_seed=2, sched=(4, (2, 2, 2)), stream=stream)
+    a.set_epi(V)
+    a.set_qsro(np.zeros((K, M), np.int32))
+    b = smcx.Lattice(kind, dims, M, [0.25] * 4, init_seed=2, sched=(4, (2, 2, 2)), stream=stream)
+    b.set_epi(V)
+    a.sweep(900.0, 2, 4)
+    b.sweep(900.0, 2, 4)
+    assert (a.get_config() == b.get_config()).all()
+    assert a.state()[1].tolist() == b.state()[1].tolist()
