@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-shared", action="store_true")
     ap.add_argument("--no-clusters", action="store_true")
+    ap.add_argument("--no-qsro", action="store_true")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -317,6 +318,47 @@ def run_exchange(stream):
             "replicas": EX_R, "sites": sites, "rounds": EX_ROUNDS, "sweeps_per_round": EX_SPR,
             "workload": f"{EX_R} x BCC {EX_EDGE}^3 int8, shared 4-shell EPI, T slots 600-1400 K linear; "
                         "host wall time per round: batched sweeps + exact energies + exchange step"}
+
+
+def run_qsro(stream):
+    """qSRO model (pair terms + W_k[s_i] n_k(i)^2) on the FCC 400^3 scale
+    workload (256M sites, 5 species, packed 4-bit, 3 shells), W ~ U{-300..300}
+    (0.01 meV, seed 77), 1000 K, library schedule (L = 4): sweeps timed with
+    CUDA events, against the pair model on the same lattice."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W_
+
+    W = np.random.default_rng(77).integers(-300, 301, (W_.K, W_.M)).astype(np.int32)
+    lat = smcx.Lattice(W_.kind, W_.dims, W_.M, W_.comp, init_seed=W_.init_seed, storage=W_.storage, stream=stream)
+    lat.set_epi(W_.epi())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(n):
+        lat.sweep(1000.0, 1, SEED)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.sweep(1000.0, n, SEED)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_pair = timed(3)
+    sched_pair = lat.schedule()
+    lat.set_qsro(W)
+    ms_q = timed(2)
+    sched_q = lat.schedule()
+    st = lat.state()[1]
+    lat.close()
+    N = W_.sites
+    return {"value": N / (ms_q / 1e3), "unit": UNIT, "ms_per_sweep": ms_q,
+            "pair_model_value": N / (ms_pair / 1e3), "slowdown_vs_pair": ms_q / ms_pair,
+            "schedule": {"L": sched_q[0], "tiles": list(sched_q[1])},
+            "pair_schedule": {"L": sched_pair[0], "tiles": list(sched_pair[1])},
+            "acceptance": float(st[1]) / max(1, int(st[0])),
+            "kernel": "k_tile_sweep_qsro<FCC,3>",
+            "workload": "FCC 400^3 = 256M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI N(0,30 meV) + "
+                        "qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}
 
 
 def run_clusters(stream):
@@ -637,6 +679,8 @@ def run_smcx(args, rank, world, local_rank):
         out["gradient"] = run_gradient(stream)
     if not args.no_clusters and world == 1:
         out["clusters"] = run_clusters(stream)
+    if not args.no_qsro and world == 1:
+        out["qsro"] = run_qsro(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

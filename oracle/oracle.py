@@ -55,6 +55,8 @@ def lib():
         L.orc_delta_e_qsro.argtypes = [i32] * 6 + [vp, vp, vp, i64, i32]
         L.orc_delta_e_qsro.restype = i64
         L.orc_schedule_check_model.argtypes = [i32] * 10
+        L.orc_tile_pass_qsro.argtypes = ([i32] * 6 + [vp, vp, vp, dbl, u64, u64, i32, i32, i32, i32, i32, i32, i32,
+                                                      i32, vp])
         L.orc_sweep_qsro.argtypes = ([i32] * 6 + [vp, vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_exchange_round.argtypes = [i32, vp, vp, vp, u64, u64, vp]
         L.orc_sweep_parallel.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp,
@@ -240,6 +242,18 @@ def sweep_qsro(kind, dims, M, K, V, W, sigma, T, n_sweeps, seed, sweep0=0, repli
                               int(sweep0), int(replica), int(L), *[int(t) for t in nt], _p(st))
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
+    return st
+
+
+def tile_pass_qsro(kind, dims, M, K, V, W, sigma, T, seed, sweep, replica, L, nt, tile):
+    """tile_pass for the qSRO model."""
+    assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    st = np.zeros(4, np.int64)
+    rc = lib().orc_tile_pass_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(sigma), float(T), int(seed), int(sweep),
+                                  int(replica), int(L), *[int(t) for t in nt], *[int(t) for t in tile], _p(st))
+    if rc:
+        raise ValueError(f"oracle tile pass rejected the request ({rc})")
     return st
 
 

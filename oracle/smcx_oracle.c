@@ -672,13 +672,32 @@ int orc_phase_direction(uint64_t seed, uint64_t sweep, int replica, int64_t tile
  * `sweep`: the part of the sweep loop below that belongs to this tile.  Tiles
  * of one colour never interact, so on that tile (and its partner ring) the
  * result equals the whole colour pass. */
+static int tile_pass_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                          int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx,
+                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats);
+
 int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                   int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica,
                   int L, int ntx, int nty, int ntz, int tx, int ty, int tz, int64_t* stats) {
+  return tile_pass_impl(kind, nx, ny, nz, M, K, V, NULL, sigma, T, seed, sweep, replica, L, ntx, nty, ntz, tx, ty,
+                        tz, stats);
+}
+
+/* orc_tile_pass for the qSRO model (W [K][M]). */
+int orc_tile_pass_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                       int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx, int nty,
+                       int ntz, int tx, int ty, int tz, int64_t* stats) {
+  return tile_pass_impl(kind, nx, ny, nz, M, K, V, W, sigma, T, seed, sweep, replica, L, ntx, nty, ntz, tx, ty, tz,
+                        stats);
+}
+
+static int tile_pass_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                          int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx,
+                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
-  if (orc_schedule_check(kind, nx, ny, nz, K, L, ntx, nty, ntz) || L == 0) return -2;
+  if (orc_schedule_check_model(kind, nx, ny, nz, K, L, ntx, nty, ntz, W ? 1 : 0) || L == 0) return -2;
   if (tx < 0 || tx >= ntx || ty < 0 || ty >= nty || tz < 0 || tz >= ntz) return -1;
   uint32_t* A = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NA_MAX);
   uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * ORC_NB);
@@ -704,7 +723,7 @@ int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t*
   c.seed = seed;
   c.replica = replica;
   c.stats = stats;
-  c.W = NULL;
+  c.W = W;
   c.sweep = sweep;
   stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int x0, sx, y0, sy, z0, sz;

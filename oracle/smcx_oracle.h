@@ -158,6 +158,10 @@ int64_t orc_delta_e_qsro(int kind, int nx, int ny, int nz, int M, int K, const i
                          int8_t* sigma, int64_t s, int dir);
 /* Schedule check for model 0 (pair) or 1 (qSRO: larger read reach). */
 int orc_schedule_check_model(int kind, int nx, int ny, int nz, int K, int L, int ntx, int nty, int ntz, int model);
+/* orc_tile_pass for the qSRO model. */
+int orc_tile_pass_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                       int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx, int nty,
+                       int ntz, int tx, int ty, int tz, int64_t* stats);
 /* orc_sweep for the qSRO model. */
 int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
                    int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,

@@ -98,3 +98,48 @@ def test_qsro_zero_weights_equal_pair_model(stream):
     b.sweep(900.0, 2, 4)
     assert (a.get_config() == b.get_config()).all()
     assert a.state()[1].tolist() == b.state()[1].tolist()
+
+
+def _tile_bounds(n, nt, i):
+    base, rem = n // nt, n % nt
+    return i * base + min(i, rem), base + (1 if i < rem else 0)
+
+
+def _tile_ring_sites(dims, nt, tile, m):
+    ranges = []
+    for a in range(3):
+        t0, ts = _tile_bounds(dims[a], nt[a], tile[a])
+        ranges.append([(c % dims[a]) for c in range(t0 - 1, t0 + ts + 1)])
+    idx = [((z * dims[1] + y) * dims[0] + x) * m + b
+           for z in ranges[2] for y in ranges[1] for x in ranges[0] for b in range(m)]
+    return np.array(idx, np.int64)
+
+
+def test_qsro_full_size_fcc400_first_colour(stream):
+    """FCC 400^3 (256M sites, the scale workload) under the qSRO model, in the
+    launch configuration bench.py times: after the first tile colour, sampled
+    tiles (tile + partner ring) bit-exact against the oracle's single-tile
+    pass; energy change = sum of accepted dE; trial count."""
+    from paper_2503_12591_gb300.inputs import SCALE_FCC400 as w
+    V = w.epi()
+    W = _w(w.K, w.M, 77)
+    lat = smcx.Lattice(w.kind, w.dims, w.M, w.comp, init_seed=w.init_seed, storage=w.storage, stream=stream)
+    lat.set_epi(V)
+    lat.set_qsro(W)
+    L, nt = lat.schedule()
+    cfg0 = lat.get_config()
+    E0 = lat.energy()
+    lat.sweep_partial(1000.0, 31, 1)
+    _, st = lat.state()
+    cfg1 = lat.get_config()
+    assert lat.energy() - E0 == st[3]
+    colour0 = [(x, y, z) for z in range(0, nt[2], 2) for y in range(0, nt[1], 2) for x in range(0, nt[0], 2)]
+    trials = sum(np.prod([_tile_bounds(w.dims[a], nt[a], t[a])[1] for a in range(3)]) * 4 for t in colour0)
+    assert st[0] == trials
+    rng = np.random.default_rng(8)
+    for i in rng.choice(len(colour0), 2, replace=False):
+        t = colour0[i]
+        O.tile_pass_qsro(w.kind, w.dims, w.M, w.K, V, W, cfg0, 1000.0, 31, 0, 0, L, nt, t)
+        sites = _tile_ring_sites(w.dims, nt, t, 4)
+        assert (cfg1[sites] == cfg0[sites]).all(), f"tile {t}"
+    lat.close()

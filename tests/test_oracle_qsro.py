@@ -203,3 +203,23 @@ def test_fcc_qsro_needs_larger_link_cell():
     assert O.schedule_check_model(O.FCC, dims, 3, 3, (1, 1, 1), 1) != 0   # not for qSRO
     assert _violations_qsro(O.FCC, dims, 3, 3, (1, 1, 1)) > 0
     assert O.schedule_check_model(O.FCC, (12, 8, 8), 3, 4, (6, 2, 2), 1) != 0  # tiles of 2 cells
+
+
+def test_qsro_tile_passes_compose_to_sweep():
+    """Every tile of colour 0, then 1, ... through the single-tile pass equals
+    the qSRO sweep (the single-tile pass is the sweep restricted to a tile)."""
+    kind, K, dims, L, nt, M = O.FCC, 3, (12, 8, 8), 4, (4, 2, 2), 3
+    V = epi_gaussian(K, M, 20.0, 6)
+    W = _w(K, M, 7)
+    sig = O.init_config(kind, dims, M, [1 / 3] * 3, 8)
+    a, b = sig.copy(), sig.copy()
+    st = O.sweep_qsro(kind, dims, M, K, V, W, a, 1100.0, 1, 3, sweep0=5, replica=2, L=L, nt=nt)
+    tot = np.zeros(4, np.int64)
+    for tc in range(8):
+        for z in range(nt[2]):
+            for y in range(nt[1]):
+                for x in range(nt[0]):
+                    if (x & 1) | ((y & 1) << 1) | ((z & 1) << 2) == tc:
+                        tot += O.tile_pass_qsro(kind, dims, M, K, V, W, b, 1100.0, 3, 5, 2, L, nt, (x, y, z))
+    assert (a == b).all()
+    assert tot.tolist() == st.tolist()
