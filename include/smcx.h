@@ -266,7 +266,9 @@ int smcx_sro(smcx_lattice* h, double* alpha);
  * smcx_local_energy: d_e2 (device, [N] int32, caller-owned) receives twice
  *   the local energy of every site, 2 E_i = sum_k sum_{v in shell k}
  *   V_k[s_i][s_{i+v}] (0.01 meV; Eq. Linear_EPI without bias terms, each bond
- *   at both ends, so sum_i 2 E_i = 2 E), canonical site order.
+ *   at both ends, so sum_i 2 E_i = 2 E), canonical site order.  Under the
+ *   qSRO model (smcx_set_qsro) 2 E_i also carries 2 sum_k W[k][s_i]
+ *   n_k(i)^2, and the clusters use these local energies.
  * smcx_clusters: a site's class is (2 E_i < thr2); two shell-1 neighbours of
  *   one class are in one cluster.  d_labels (device, [N] int32, caller-owned)
  *   receives for every site the smallest site id of its cluster (a unique

@@ -48,6 +48,8 @@ def lib():
         L.orc_sweep.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp])
         L.orc_sweep_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32, vp, i32])
         L.orc_local_energy2.argtypes = [i32] * 6 + [vp, vp, vp]
+        L.orc_local_energy2_qsro.argtypes = [i32] * 6 + [vp, vp, vp, vp]
+        L.orc_clusters_qsro.argtypes = [i32] * 6 + [vp, vp, vp, i64, vp, vp]
         L.orc_local_energy2_sample.argtypes = [i32] * 6 + [vp, vp, vp, i64, vp]
         L.orc_clusters.argtypes = [i32] * 6 + [vp, vp, i64, vp, vp]
         L.orc_energy_qsro.argtypes = [i32] * 6 + [vp, vp, vp]
@@ -268,6 +270,17 @@ def local_energy2(kind, dims, M, K, V, sigma):
     return out
 
 
+def local_energy2_qsro(kind, dims, M, K, V, W, sigma):
+    """2 E_i under the qSRO model (pair value + 2 sum_k W[k][s_i] n_k(i)^2)."""
+    N = n_sites(kind, dims)
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    out = np.zeros(N, np.int64)
+    if lib().orc_local_energy2_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(s), _p(out)):
+        raise ValueError("oracle local energy rejected the request")
+    return out
+
+
 def local_energy2_sample(kind, dims, M, K, V, sigma, ids):
     """2 E_i of the listed sites only."""
     Vv = np.ascontiguousarray(V, np.int32)
@@ -287,6 +300,18 @@ def clusters(kind, dims, M, K, V, sigma, thr2):
     lab = np.zeros(N, np.int64)
     nc = np.zeros(1, np.int64)
     if lib().orc_clusters(kind, *dims, M, K, _p(Vv), _p(s), int(thr2), _p(lab), _p(nc)):
+        raise ValueError("oracle clusters rejected the request")
+    return lab, int(nc[0])
+
+
+def clusters_qsro(kind, dims, M, K, V, W, sigma, thr2):
+    """clusters() with the qSRO local energies."""
+    N = n_sites(kind, dims)
+    Vv, Wv = np.ascontiguousarray(V, np.int32), np.ascontiguousarray(W, np.int32)
+    s = np.ascontiguousarray(sigma, np.int8)
+    lab = np.zeros(N, np.int64)
+    nc = np.zeros(1, np.int64)
+    if lib().orc_clusters_qsro(kind, *dims, M, K, _p(Vv), _p(Wv), _p(s), int(thr2), _p(lab), _p(nc)):
         raise ValueError("oracle clusters rejected the request")
     return lab, int(nc[0])
 

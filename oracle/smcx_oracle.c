@@ -1037,6 +1037,20 @@ int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int3
   return 0;
 }
 
+/* Under the qSRO model the local energy also carries the site's quadratic
+ * term: e2[i] += 2 sum_k W[k][s_i] n_k(i)^2, so that sum_i e2[i] = 2 E
+ * still holds for the qSRO energy. */
+int orc_local_energy2_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                           const int8_t* sigma, int64_t* e2) {
+  shells_t S;
+  int m = orc_sites_per_cell(kind);
+  if (m == 0 || load_shells(kind, K, &S)) return -1;
+  if (orc_local_energy2(kind, nx, ny, nz, M, K, V, sigma, e2)) return -1;
+  int64_t N = (int64_t)nx * ny * nz * m;
+  for (int64_t i = 0; i < N; i++) e2[i] += 2 * qsro_site(kind, nx, ny, nz, M, &S, W, sigma, i);
+  return 0;
+}
+
 /* e2 of the sites ids[0..n-1] only (same definition, for lattices too large
  * to evaluate whole). */
 int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
@@ -1059,8 +1073,8 @@ int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, con
 
 /* Breadth-first search from every unvisited site in increasing id order:
  * the start of each search is the smallest id of its cluster. */
-int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
-                 int64_t thr2, int64_t* labels, int64_t* n_clusters) {
+static int clusters_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                         const int8_t* sigma, int64_t thr2, int64_t* labels, int64_t* n_clusters) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
@@ -1072,7 +1086,10 @@ int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* 
     free(queue);
     return -1;
   }
-  orc_local_energy2(kind, nx, ny, nz, M, K, V, sigma, e2);
+  if (W)
+    orc_local_energy2_qsro(kind, nx, ny, nz, M, K, V, W, sigma, e2);
+  else
+    orc_local_energy2(kind, nx, ny, nz, M, K, V, sigma, e2);
   for (int64_t s = 0; s < N; s++) labels[s] = -1;
   int64_t nc = 0;
   for (int64_t s0 = 0; s0 < N; s0++) {
@@ -1096,4 +1113,15 @@ int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* 
   free(e2);
   free(queue);
   return 0;
+}
+
+int orc_clusters(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
+                 int64_t thr2, int64_t* labels, int64_t* n_clusters) {
+  return clusters_impl(kind, nx, ny, nz, M, K, V, NULL, sigma, thr2, labels, n_clusters);
+}
+
+/* Clusters from the qSRO local energies. */
+int orc_clusters_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                      const int8_t* sigma, int64_t thr2, int64_t* labels, int64_t* n_clusters) {
+  return clusters_impl(kind, nx, ny, nz, M, K, V, W, sigma, thr2, labels, n_clusters);
 }

@@ -138,6 +138,14 @@ int orc_exchange_round(int R, const double* T_slot, const int64_t* E, int32_t* s
 int orc_local_energy2(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
                       int64_t* e2);
 
+/* e2 under the qSRO model: the pair value + 2 sum_k W[k][s_i] n_k(i)^2. */
+int orc_local_energy2_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                           const int8_t* sigma, int64_t* e2);
+
+/* orc_clusters with the qSRO local energies. */
+int orc_clusters_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
+                      const int8_t* sigma, int64_t thr2, int64_t* labels, int64_t* n_clusters);
+
 /* e2 of the listed sites only: e2 [n] for ids [n]. */
 int orc_local_energy2_sample(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int8_t* sigma,
                              const int64_t* ids, int64_t n, int64_t* e2);

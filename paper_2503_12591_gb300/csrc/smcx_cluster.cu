@@ -5,8 +5,9 @@
 //
 //  * e2[i] = 2 E_i = sum_k sum_{v in shell k} V_k[s_i][s_{i+v}] (Eq.
 //    Linear_EPI without the bias terms, each bond counted at both ends, so
-//    sum_i e2[i] = 2 E); one thread per cell, neighbours gathered from the
-//    lattice store with periodic wrap.
+//    sum_i e2[i] = 2 E), plus 2 sum_k W_k[s_i] n_k(i)^2 under the qSRO model
+//    (Eq. quadratic_local_SRO); one thread per cell, neighbours gathered from
+//    the lattice store with periodic wrap.
 //  * class(i) = e2[i] < thr2.  Two shell-1 neighbours of one class are in
 //    one cluster.  Concurrent union-find over int32 parents: a root is only
 //    ever linked below a smaller root with a compare-and-swap, so parents
@@ -43,13 +44,22 @@ __device__ __forceinline__ long long nb_gid(const SweepParams& P, int x, int y, 
           wrap_add(x, d[0], P.n[0])) * m + d[3];
 }
 
+// qSRO weights W[k][c] (on = 0: pair model)
+struct QsroWeights {
+  int32_t w[kMaxShells * kMaxSweepM];
+  int on;
+};
+
 template <int KIND, int K>
-__global__ void __launch_bounds__(256) k_local_energy2(const SweepParams P, const int32_t* __restrict__ dV, int32_t* e2,
-                                                       uint8_t* cls, long long thr2) {
+__global__ void __launch_bounds__(256) k_local_energy2(const SweepParams P, const int32_t* __restrict__ dV,
+                                                       const QsroWeights QW, int32_t* e2, uint8_t* cls,
+                                                       long long thr2) {
   constexpr int m = cell_sites(KIND);
   __shared__ int32_t sV[kMaxShells * kMaxSweepM * kMaxSweepM];
+  __shared__ int32_t sW[kMaxShells * kMaxSweepM];
   const int M = P.M;
   for (int i = threadIdx.x; i < K * M * M; i += blockDim.x) sV[i] = dV[i];
+  for (int i = threadIdx.x; i < K * M; i += blockDim.x) sW[i] = QW.on ? QW.w[i] : 0;
   __syncthreads();
   const long long ncell = (long long)P.n[0] * P.n[1] * P.n[2];
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
@@ -64,9 +74,14 @@ __global__ void __launch_bounds__(256) k_local_energy2(const SweepParams P, cons
 #pragma unroll
       for (int k = 0; k < K; k++) {
         const int32_t* row = sV + (k * M + p) * M;
+        int n = 0;
 #pragma unroll 4
-        for (int q = 0; q < shell_size(KIND, k); q++, j++)
-          acc += row[load_site(P.sites, nb_gid(P, x, y, z, P.gd[b][j], m), P.storage)];
+        for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+          const int c = load_site(P.sites, nb_gid(P, x, y, z, P.gd[b][j], m), P.storage);
+          acc += row[c];
+          n += (c == p);
+        }
+        acc += 2 * sW[k * M + p] * n * n;  // qSRO term (W = 0 for the pair model)
       }
       if (e2) e2[c * m + b] = acc;
       if (cls) cls[c * m + b] = (uint8_t)((long long)acc < thr2);
@@ -211,6 +226,11 @@ void need_epi(const smcx_lattice* hd) {
     long long vmax = 0;
     for (int i = 0; i < M * M; i++) vmax = std::max(vmax, std::llabs((long long)hd->V[k * M * M + i]));
     bound += vmax * hd->shells.z[k];
+    if (!hd->Wq.empty()) {
+      long long wmax = 0;
+      for (int p = 0; p < M; p++) wmax = std::max(wmax, std::llabs((long long)hd->Wq[k * M + p]));
+      bound += 2 * wmax * hd->shells.z[k] * hd->shells.z[k];
+    }
   }
   if (bound > 2147483647ll) fail(SMCX_E_RANGE, "local energies do not fit int32 for this EPI table");
 }
@@ -221,10 +241,14 @@ void launch_local_energy(smcx_lattice* hd, int32_t* e2, uint8_t* cls, long long 
   setup_params(hd, P);
   // the plain V table sits after W[a][b][k][c] and X[a][b] in the device EPI table
   const int32_t* dV = hd->d_wtab + (size_t)hd->M * hd->M * hd->shells.K * hd->M + hd->M * hd->M;
+  QsroWeights QW;
+  memset(&QW, 0, sizeof(QW));
+  QW.on = hd->Wq.empty() ? 0 : 1;
+  for (size_t i = 0; i < hd->Wq.size(); i++) QW.w[i] = hd->Wq[i];
   const long long ncell = (long long)hd->n[0] * hd->n[1] * hd->n[2];
   const int grid = grid_for(ncell);
   const int K = hd->shells.K;
-  auto go = [&](auto kern) { kern<<<grid, 256, 0, hd->stream>>>(P, dV, e2, cls, thr2); };
+  auto go = [&](auto kern) { kern<<<grid, 256, 0, hd->stream>>>(P, dV, QW, e2, cls, thr2); };
   if (hd->kind == kBCC) {
     switch (K) {
       case 1: go(k_local_energy2<kBCC, 1>); break;

@@ -37,8 +37,10 @@ struct QsroTables {
   unsigned char start[kMaxShells + 1];  // first vector of each shell
 };
 
-template <int KIND, int K>
-__global__ void __launch_bounds__(256) k_tile_sweep_qsro(const SweepParams P, const QsroTables Q) {
+// NT threads per CTA: 128 when a phase of the tile has at most 128 trials
+// (20-cell tiles, L = 4: 125), else 256; registers capped for 512 threads/SM.
+template <int KIND, int K, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_tile_sweep_qsro(const SweepParams P, const QsroTables Q) {
   constexpr int m = cell_sites(KIND);
   constexpr int NV = vec_count(KIND, K);
   constexpr int Z1 = shell_size(KIND, 0);
@@ -390,17 +392,22 @@ void launch_qsro(smcx_lattice* hd, SweepParams& P, const QsroTables& T, int64_t 
   const int nW = P.M * P.M * K * P.M + P.M * P.M;
   const size_t smem = (size_t)(nW + P.nA + kNB + m * NV + 2 * m * Z1) * 4 + (size_t)P.BX * P.BY * P.BZ * m;
   if (smem > 200 * 1024) fail(SMCX_E_UNSUPPORTED, "tile too large for shared memory");
-  check_cuda(cudaFuncSetAttribute(k_tile_sweep_qsro<KIND, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem),
-             "qSRO sweep smem attribute");
-  for (int64_t s = 0; s < n_sweeps; s++) {
-    P.sweep = hd->sweep_cum + (uint64_t)s;
-    for (int tc = 0; tc < n_colours; tc++) {
-      P.tc = tc;
-      const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
-      k_tile_sweep_qsro<KIND, K><<<grid, 256, smem, hd->stream>>>(P, T);
+  int slots = 1;
+  for (int a = 0; a < 3; a++) slots *= ((P.n[a] + P.nt[a] - 1) / P.nt[a] + P.L - 1) / P.L;
+  auto run = [&](auto kern, int nt) {
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "qSRO sweep smem attribute");
+    for (int64_t s = 0; s < n_sweeps; s++) {
+      P.sweep = hd->sweep_cum + (uint64_t)s;
+      for (int tc = 0; tc < n_colours; tc++) {
+        P.tc = tc;
+        const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
+        kern<<<grid, nt, smem, hd->stream>>>(P, T);
+      }
     }
-  }
+  };
+  if (slots <= 128) run(k_tile_sweep_qsro<KIND, K, 128>, 128);
+  else run(k_tile_sweep_qsro<KIND, K, 256>, 256);
   check_cuda(cudaGetLastError(), "qSRO sweep launch");
 }
 

@@ -143,3 +143,29 @@ def test_qsro_full_size_fcc400_first_colour(stream):
         sites = _tile_ring_sites(w.dims, nt, t, 4)
         assert (cfg1[sites] == cfg0[sites]).all(), f"tile {t}"
     lat.close()
+
+
+@pytest.mark.parametrize("kind,K,dims,M", [(smcx.FCC, 3, (12, 8, 8), 4), (smcx.BCC, 2, (12, 12, 12), 3)])
+def test_qsro_local_energy_and_clusters(stream, kind, K, dims, M):
+    V = epi_gaussian(K, M, 20.0, 11)
+    W = _w(K, M, 12)
+    lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, init_seed=5, stream=stream)
+    lat.set_epi(V)
+    lat.set_qsro(W)
+    lat.sweep(900.0, 2, 3)
+    cfg = lat.get_config()
+    N = cfg.size
+    e2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.local_energy(e2.data_ptr())
+    lat.synchronize()
+    want = O.local_energy2_qsro(kind, dims, M, K, V, W, cfg)
+    got = e2.cpu().numpy().astype(np.int64)
+    assert (got == want).all()
+    assert got.sum() == 2 * lat.energy()
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    thr = int(np.quantile(want, 0.4))
+    nc = lat.clusters(thr, lab.data_ptr())
+    olab, onc = O.clusters_qsro(kind, dims, M, K, V, W, cfg, thr)
+    assert nc == onc
+    assert (lab.cpu().numpy().astype(np.int64) == olab).all()
+    lat.close()

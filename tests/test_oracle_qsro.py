@@ -223,3 +223,17 @@ def test_qsro_tile_passes_compose_to_sweep():
                         tot += O.tile_pass_qsro(kind, dims, M, K, V, W, b, 1100.0, 3, 5, 2, L, nt, (x, y, z))
     assert (a == b).all()
     assert tot.tolist() == st.tolist()
+
+
+def test_qsro_local_energy_sum_rule_and_l12():
+    dims = (3, 3, 4)
+    V = epi_gaussian(3, 2, 30.0, 5)
+    W = _w(3, 2, 6)
+    N = O.n_sites(O.FCC, dims)
+    sig = np.tile(np.array([1, 0, 0, 0], np.int8), N // 4)
+    e2 = O.local_energy2_qsro(O.FCC, dims, 2, 3, V, W, sig)
+    pair = O.local_energy2(O.FCC, dims, 2, 3, V, sig)
+    assert (e2[0::4] - pair[0::4] == 2 * 36 * int(W[1, 1])).all()
+    assert (e2[1::4] - pair[1::4] == 2 * (64 * int(W[0, 0]) + 36 * int(W[1, 0]) + 256 * int(W[2, 0]))).all()
+    rnd = np.random.default_rng(3).integers(0, 2, N).astype(np.int8)
+    assert O.local_energy2_qsro(O.FCC, dims, 2, 3, V, W, rnd).sum() == 2 * O.energy_qsro(O.FCC, dims, 2, 3, V, W, rnd)
