@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--no-shared", action="store_true")
     ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--no-qsro", action="store_true")
+    ap.add_argument("--no-throughput", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
+                                                    "throughput"],
+                    help="profiling only: run one secondary measurement and print its JSON")
+    ap.add_argument("--edge", type=int, default=0,
+                    help="profiling only: FCC edge of the qsro / clusters measurement other than 400")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -320,7 +326,50 @@ def run_exchange(stream):
                         "host wall time per round: batched sweeps + exact energies + exchange step"}
 
 
-def run_qsro(stream):
+def run_throughput256(stream):
+    """The 33.5M-site throughput workload: BCC 256^3 int8, 1000 sweeps at each
+    of 2500, 1500 and 800 K, energy + Warren-Cowley SRO every 100 sweeps;
+    timed with CUDA events with and without the observables (the 33.5 MB
+    lattice fits the 129 MB L2, so this runs from L2, not HBM)."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import THROUGHPUT_BCC256 as W_
+
+    lat = smcx.Lattice(W_.kind, W_.dims, W_.M, W_.comp, init_seed=W_.init_seed, storage=W_.storage, stream=stream)
+    lat.set_epi(W_.epi())
+    lat.sweep(W_.temperatures[0], 3, SEED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_T = []
+    t_all = 0.0
+    n_sw = 0
+    for T in W_.temperatures:
+        e0.record(stream)
+        obs = []
+        for _ in range(10):
+            lat.sweep(T, 100, SEED)
+            obs.append((lat.energy(), lat.sro()[0, 0, 1]))
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        t_all += ms
+        n_sw += 1000
+        per_T.append({"T": T, "ms_1000_sweeps_with_observables": ms,
+                      "final_energy": int(obs[-1][0]), "final_alpha1_01": float(obs[-1][1])})
+    e0.record(stream)
+    lat.sweep(W_.temperatures[-1], 200, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1) / 200
+    N = lat.N
+    lat.close()
+    return {"value": N * n_sw / (t_all / 1e3), "unit": UNIT, "sweep_only_value": N / (ms_plain / 1e3),
+            "per_temperature": per_T,
+            "workload": "BCC 256^3 = 33,554,432 sites int8, 4 species, 4-shell EPI N(0,20 meV); 1000 sweeps at "
+                        "2500/1500/800 K, E + SRO every 100 sweeps (value includes them); L2-resident"}
+
+
+def run_qsro(stream, edge=0):
     """qSRO model (pair terms + W_k[s_i] n_k(i)^2) on the FCC 400^3 scale
     workload (256M sites, 5 species, packed 4-bit, 3 shells), W ~ U{-300..300}
     (0.01 meV, seed 77), 1000 K, library schedule (L = 4): sweeps timed with
@@ -329,6 +378,9 @@ def run_qsro(stream):
     from paper_2503_12591_gb300 import smcx
     from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W_
 
+    if edge:
+        import dataclasses
+        W_ = dataclasses.replace(W_, dims=(edge,) * 3)
     W = np.random.default_rng(77).integers(-300, 301, (W_.K, W_.M)).astype(np.int32)
     lat = smcx.Lattice(W_.kind, W_.dims, W_.M, W_.comp, init_seed=W_.init_seed, storage=W_.storage, stream=stream)
     lat.set_epi(W_.epi())
@@ -361,7 +413,7 @@ def run_qsro(stream):
                         "qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}
 
 
-def run_clusters(stream):
+def run_clusters(stream, edge=0):
     """Local-energy field and union-find clusters on the FCC 400^3 scale
     workload (256M sites, 5 species, packed 4-bit) after one sweep at 1200 K,
     threshold = median of a 1/97 sample of 2 E_i; CUDA events on the stream."""
@@ -369,6 +421,9 @@ def run_clusters(stream):
     from paper_2503_12591_gb300 import smcx
     from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W
 
+    if edge:
+        import dataclasses
+        W = dataclasses.replace(W, dims=(edge,) * 3)
     lat = smcx.Lattice(W.kind, W.dims, W.M, W.comp, init_seed=W.init_seed, storage=W.storage, stream=stream)
     lat.set_epi(W.epi())
     lat.sweep(W.temperatures[0], 1, W.seed)
@@ -681,6 +736,8 @@ def run_smcx(args, rank, world, local_rank):
         out["clusters"] = run_clusters(stream)
     if not args.no_qsro and world == 1:
         out["qsro"] = run_qsro(stream)
+    if not args.no_throughput and world == 1:
+        out["throughput_256"] = run_throughput256(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
@@ -702,6 +759,13 @@ def main():
         world = 1
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.only:
+        import torch
+        stream = torch.cuda.Stream()
+        fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
+              "throughput": run_throughput256,
+              "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
+        print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:
         run_smcx(args, rank, world, local_rank)
 
