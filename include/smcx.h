@@ -235,6 +235,19 @@ int smcx_get_schedule(const smcx_lattice* h, smcx_sched* out);
  */
 int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed);
 
+/*
+ * Pick the fastest schedule for this lattice and model by measurement: for
+ * link cells from the model's minimum to 5 and tiles of about 10..20 cells
+ * (and, for the BCC tile kernel, 0/128/256 threads per CTA), time `trial`
+ * (1..64) sweeps at temperature T on a snapshot of the configuration.  The
+ * configuration, statistics and sweep counter are restored; the fastest
+ * schedule and block size are installed (as if set explicitly) and returned
+ * in *out / *threads (either may be NULL).  Small lattices leave most SMs idle
+ * with the default 20-cell tiles; this is the remedy.  Needs N bytes of
+ * temporary device memory.  SMCX_E_SCHEDULE if no candidate fits.
+ */
+int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* threads);
+
 /* Verification hook: run tile colours 0..n_colours-1 (0..8) of sweep number
  * `cumulative sweep index` without advancing the index, i.e. the first part
  * of the next smcx_sweep.  Tiles of one colour never interact, so after one

@@ -365,6 +365,89 @@ int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed) {
   });
 }
 
+// Times `trial` sweeps for every candidate schedule (link cell from the
+// model's minimum to 5, tiles of about 10..20 cells) and, for the BCC tile
+// kernel, block size, on a snapshot of the configuration; restores the
+// configuration, statistics and sweep counter and installs the fastest.
+int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* threads) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
+    need(T > 0.0 && isfinite(T), SMCX_E_INVALID_ARG, "temperature must be finite and > 0");
+    need(trial >= 1 && trial <= 64, SMCX_E_INVALID_ARG, "trial sweeps must be 1..64");
+    uint8_t* d_copy = nullptr;
+    check_cuda(cudaMalloc(&d_copy, h->site_bytes), "autotune snapshot");
+    unsigned long long st[4];
+    check_cuda(cudaMemcpyAsync(d_copy, h->d_sites, h->site_bytes, cudaMemcpyDeviceToDevice, h->stream),
+               "autotune snapshot copy");
+    check_cuda(cudaMemcpyAsync(st, h->d_stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream), "stats snapshot");
+    check_cuda(cudaStreamSynchronize(h->stream), "autotune snapshot sync");
+    const smcx_sched sched0 = h->sched;
+    const bool auto0 = h->sched_auto;
+    const int threads0 = h->bcc_threads;
+    const uint64_t sweep0 = h->sweep_cum;
+    upload_thresholds(h, T);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    check_cuda(cudaEventCreate(&e0), "event");
+    check_cuda(cudaEventCreate(&e1), "event");
+    double best = 1e300;
+    smcx_sched best_sc = sched0;
+    int best_th = threads0;
+    const int Lmin = min_link_cell(h->shells);
+    for (int L = Lmin; L <= std::max(Lmin, 5); L++)
+      for (int target : {10, 12, 14, 16, 20})
+        for (int th : {0, 128, 256}) {
+          smcx_sched sc;
+          sc.L = L;
+          for (int a = 0; a < 3; a++) {
+            int nt = 2;
+            while ((h->n[a] + nt - 1) / nt > target) nt += 2;
+            sc.nt[a] = nt;
+          }
+          if (!schedule_problem(h->shells, h->n, sc).empty()) continue;
+          h->sched = sc;
+          h->bcc_threads = th;
+          const bool fast = h->kernel_choice != 1 && h->Wq.empty() && bcc_fast_usable(h);
+          if (th != 0 && !fast) continue;  // block size only matters to the BCC tile kernel
+          float ms = 0;
+          try {
+            sweep_device(h, h->thr_nA, 0x5eedull, 1);
+            check_cuda(cudaEventRecord(e0, h->stream), "event");
+            sweep_device(h, h->thr_nA, 0x5eedull, trial);
+            check_cuda(cudaEventRecord(e1, h->stream), "event");
+            check_cuda(cudaEventSynchronize(e1), "event sync");
+            check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+          } catch (const SmcxException&) {
+            continue;
+          }
+          if (ms < best) {
+            best = ms;
+            best_sc = sc;
+            best_th = th;
+          }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    check_cuda(cudaMemcpyAsync(h->d_sites, d_copy, h->site_bytes, cudaMemcpyDeviceToDevice, h->stream),
+               "autotune restore");
+    check_cuda(cudaMemcpyAsync(h->d_stats, st, sizeof(st), cudaMemcpyHostToDevice, h->stream), "stats restore");
+    check_cuda(cudaStreamSynchronize(h->stream), "autotune restore sync");
+    cudaFree(d_copy);
+    h->sweep_cum = sweep0;
+    if (best >= 1e300) {
+      h->sched = sched0;
+      h->sched_auto = auto0;
+      h->bcc_threads = threads0;
+      fail(SMCX_E_SCHEDULE, "no autotuner candidate fits this lattice");
+    }
+    h->sched = best_sc;
+    h->sched_auto = false;
+    h->bcc_threads = best_th;
+    if (out) *out = best_sc;
+    if (threads) *threads = best_th;
+  });
+}
+
 int smcx_sweep_partial(smcx_lattice* h, double T, uint64_t seed, int n_colours) {
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
@@ -393,8 +476,10 @@ int smcx_energy(smcx_lattice* h, int64_t* E) {
   return guarded([&] {
     need(h && E, SMCX_E_INVALID_ARG, "NULL argument");
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
-    pair_counts_device(h);
-    energy_device(h);
+    if (!energy_bcc_direct(h)) {
+      pair_counts_device(h);
+      energy_device(h);
+    }
     if (!h->Wq.empty()) qsro_energy_add(h);
     long long e = 0;
     check_cuda(cudaMemcpyAsync(&e, h->d_energy, 8, cudaMemcpyDeviceToHost, h->stream), "energy download");

@@ -140,7 +140,8 @@ void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // set
 void validate_store(smcx_lattice* h);  // every stored id < M, else sets d_flag
 void local_energy_device(smcx_lattice* h, int32_t* d_e2);
 void sweep_qsro_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
-void qsro_energy_add(smcx_lattice* h);  // adds sum_i sum_k W[k][s_i] n_k(i)^2 to d_energy
+void qsro_energy_add(smcx_lattice* h);
+bool energy_bcc_direct(smcx_lattice* h);  // pair energy into d_energy; false if not applicable  // adds sum_i sum_k W[k][s_i] n_k(i)^2 to d_energy
 void clusters_device(smcx_lattice* h, long long thr2, int32_t* d_labels, int64_t* n_clusters);
 void cluster_summary_device(smcx_lattice* h, const int32_t* d_labels, long long min_size, int max_out,
                             int64_t* roots, int64_t* sizes, int64_t* counts, int* n_out);

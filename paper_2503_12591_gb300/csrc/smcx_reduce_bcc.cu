@@ -19,25 +19,24 @@ namespace smcx {
 
 namespace bccfast {
 
-template <int K>
-__global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned int hist[kMaxShells * 16];
-  uint8_t* box = smem;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+// The tile of this CTA (tiles numbered x fastest) and its staging: tile plus
+// a 2-cell halo into the sublattice byte arrays of the sweep's box layout,
+// species stored as 8 s.
+__device__ __forceinline__ void tile_of_block(const LatDesc& D, int t0[3], int ts[3]) {
   const int ntx = D.nt[0], nty = D.nt[1];
   const int t = blockIdx.x;
   const int ti[3] = {t % ntx, (t / ntx) % nty, t / (ntx * nty)};
-  int t0[3], ts[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     const int base = D.n[a] / D.nt[a], rem = D.n[a] % D.nt[a];
     ts[a] = base + (ti[a] < rem ? 1 : 0);
     t0[a] = ti[a] * base + min(ti[a], rem);
   }
-  for (int i = tid; i < kMaxShells * 16; i += nth) hist[i] = 0;
+}
+
+__device__ __forceinline__ void stage_tile(const LatDesc& D, uint8_t* box, const int t0[3], const int ts[3]) {
   constexpr int h = 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
   const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
   for (int row = warp; row < ey * ez; row += nwarp) {
@@ -60,6 +59,26 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
       box[SUB + bi] = (uint8_t)(s1 << 3);
     }
   }
+}
+
+// Half of a shell: the vectors whose first nonzero half-unit component is
+// positive (one of each +v / -v pair).
+__host__ __device__ constexpr bool half_vec(const Vec& v) {
+  return v.x > 0 || (v.x == 0 && (v.y > 0 || (v.y == 0 && v.z > 0)));
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int hist[kMaxShells * 16];
+  uint8_t* box = smem;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31;
+  int t0[3], ts[3];
+  tile_of_block(D, t0, ts);
+  for (int i = tid; i < kMaxShells * 16; i += nth) hist[i] = 0;
+  constexpr int h = 2;
+  stage_tile(D, box, t0, ts);
   __syncthreads();
 
   // acc[k][p][0] holds bytes 0 and 2 of the per-site counters, acc[k][p][1]
@@ -85,8 +104,7 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
       for (int j = 0; j < T.n; j++) {
         const int k = T.v[j].k;
         if (k >= K) continue;
-        const bool half = T.v[j].x > 0 || (T.v[j].x == 0 && (T.v[j].y > 0 || (T.v[j].y == 0 && T.v[j].z > 0)));
-        if (!half) continue;
+        if (!half_vec(T.v[j])) continue;
         const int off = B == 0 ? nb_offset(0, T.v[j].x, T.v[j].y, T.v[j].z) : nb_offset(1, T.v[j].x, T.v[j].y, T.v[j].z);
         hk[k] += 1u << box[s + off];
       }
@@ -123,6 +141,71 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
       atomicAdd(&counts[(k * D.M + p) * D.M + q], (unsigned long long)hist[i]);
       atomicAdd(&counts[(k * D.M + q) * D.M + p], (unsigned long long)hist[i]);
     }
+  }
+}
+
+// Energy directly (M <= 4): E = sum_i sum_k sum_{v in half shell k}
+// V_k[s_i][s_{i+v}], every unordered pair once.  Per site the half-shell
+// neighbours go into byte-packed per-species counters h_k (at most 12 per
+// byte), and the site's term is sum_k dp4a(h_k, row of V_k for its species)
+// over the byte planes of V (two or three planes, |V| < 2^23), the rows read
+// from a shared table indexed by the site's species.
+template <int K, int PL>
+__global__ void __launch_bounds__(256) k_bcc_energy(const LatDesc D, const Planes Q, long long* __restrict__ E) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t sP[PL * kMaxShells * 4];
+  __shared__ long long part[8];
+  uint8_t* box = smem;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int t0[3], ts[3];
+  tile_of_block(D, t0, ts);
+  for (int i = tid; i < PL * K * 4; i += nth) sP[i] = Q.P[i / (K * 4)][(i / 4) % K][i % 4][0];
+  constexpr int h = 2;
+  stage_tile(D, box, t0, ts);
+  __syncthreads();
+  long long acc = 0;
+  const int ncell = ts[0] * ts[1] * ts[2];
+  constexpr VecTable T = make_vecs();
+  for (int c = tid; c < ncell; c += nth) {
+    const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
+    const int s0 = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+    int g = 0;
+#pragma unroll
+    for (int B = 0; B < 2; B++) {
+      const int s = s0 + B * SUB;
+      const int p = box[s] >> 3;
+      uint32_t hk[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) hk[k] = 0;
+#pragma unroll
+      for (int j = 0; j < T.n; j++) {
+        const int k = T.v[j].k;
+        if (k >= K || !half_vec(T.v[j])) continue;
+        const int off = B == 0 ? nb_offset(0, T.v[j].x, T.v[j].y, T.v[j].z) : nb_offset(1, T.v[j].x, T.v[j].y, T.v[j].z);
+        hk[k] += 1u << box[s + off];
+      }
+      int a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        a0 = dp4a_su((int)hk[k], sP[(0 * K + k) * 4 + p], a0);
+        if (PL == 2) {
+          a1 = dp4a_ss((int)hk[k], sP[(1 * K + k) * 4 + p], a1);
+        } else {
+          a1 = dp4a_su((int)hk[k], sP[(1 * K + k) * 4 + p], a1);
+          a2 = dp4a_ss((int)hk[k], sP[(2 * K + k) * 4 + p], a2);
+        }
+      }
+      g += a0 + (a1 << 8) + (a2 << 16);
+    }
+    acc += g;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) part[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    long long t = 0;
+    for (int w = 0; w < nth / 32; w++) t += part[w];
+    atomicAdd(reinterpret_cast<unsigned long long*>(E), (unsigned long long)t);
   }
 }
 
@@ -170,6 +253,53 @@ void pair_counts_bcc_tiled(smcx_lattice* hd, const int nt[3]) {
     default: go(bccfast::k_bcc_pair_counts<4>); break;
   }
   check_cuda(cudaGetLastError(), "tiled pair-count launch");
+}
+
+int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
+
+// Energy of a BCC lattice with M <= 4 straight from the tiles (no pair-count
+// histogram); false when the tiled path does not apply.
+bool energy_bcc_direct(smcx_lattice* hd) {
+  int nt[3];
+  if (hd->kernel_choice == SMCX_KERNEL_GENERIC || !bcc_counts_usable(hd, nt)) return false;
+  for (int32_t v : hd->V)
+    if (v >= (1 << 23) || v <= -(1 << 23)) return false;
+  bccfast::LatDesc D;
+  memset(&D, 0, sizeof(D));
+  D.sites = hd->d_sites;
+  D.storage = hd->storage;
+  D.M = hd->M;
+  for (int a = 0; a < 3; a++) {
+    D.n[a] = hd->n[a];
+    D.nt[a] = nt[a];
+  }
+  bccfast::Planes Q;
+  const int PL = build_planes(hd, &Q, 2);
+  const int grid = nt[0] * nt[1] * nt[2];
+  const size_t smem = 2 * bccfast::SUB;
+  check_cuda(cudaMemsetAsync(hd->d_energy, 0, sizeof(long long), hd->stream), "clear energy");
+  auto go = [&](auto kern) {
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+    kern<<<grid, 256, smem, hd->stream>>>(D, Q, hd->d_energy);
+  };
+  const int K = hd->shells.K;
+  if (PL == 2) {
+    switch (K) {
+      case 1: go(bccfast::k_bcc_energy<1, 2>); break;
+      case 2: go(bccfast::k_bcc_energy<2, 2>); break;
+      case 3: go(bccfast::k_bcc_energy<3, 2>); break;
+      default: go(bccfast::k_bcc_energy<4, 2>); break;
+    }
+  } else {
+    switch (K) {
+      case 1: go(bccfast::k_bcc_energy<1, 3>); break;
+      case 2: go(bccfast::k_bcc_energy<2, 3>); break;
+      case 3: go(bccfast::k_bcc_energy<3, 3>); break;
+      default: go(bccfast::k_bcc_energy<4, 3>); break;
+    }
+  }
+  check_cuda(cudaGetLastError(), "tiled energy launch");
+  return true;
 }
 
 }  // namespace smcx

@@ -46,6 +46,7 @@ _SIGS = {
     "smcx_cluster_summary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
     "smcx_set_qsro": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_autotune": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -242,6 +243,14 @@ class Lattice:
             if self.K and W.shape != (self.K, self.M):
                 raise ValueError(f"W must have shape ({self.K}, {self.M})")
             _check(lib().smcx_set_qsro(self._h, _p(W)))
+
+    def autotune(self, T, trial_sweeps=2):
+        """Measure candidate schedules and install the fastest (smcx_autotune);
+        returns ((L, tiles), threads)."""
+        sc = Sched()
+        th = np.zeros(1, np.int32)
+        _check(lib().smcx_autotune(self._h, float(T), int(trial_sweeps), C.byref(sc), _p(th)))
+        return (int(sc.L), tuple(int(t) for t in sc.nt)), int(th[0])
 
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))

@@ -288,3 +288,35 @@ def test_edge_shorter_than_reach_rejected(stream):
         smcx.energy_noalloc(smcx.BCC, (1, 8, 8), 4, smcx.INT8, epi_gaussian(4, 4, 20.0, 1), d.data_ptr(),
                             stream=stream)
     assert e.value.code == smcx.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind,K,dims,M,qsro", [
+    (smcx.BCC, 4, (48, 40, 44), 4, False),
+    (smcx.FCC, 3, (24, 24, 28), 5, False),
+    (smcx.FCC, 3, (24, 24, 24), 4, True),
+])
+def test_autotune_restores_state_and_stays_exact(stream, kind, K, dims, M, qsro):
+    V = epi_gaussian(K, M, 20.0, 2)
+    lat = smcx.Lattice(kind, dims, M, [1.0 / M] * M, init_seed=3, storage=smcx.PACKED4, stream=stream)
+    lat.set_epi(V)
+    W = None
+    if qsro:
+        W = np.random.default_rng(1).integers(-200, 201, (K, M)).astype(np.int32)
+        lat.set_qsro(W)
+    lat.sweep(1200.0, 2, 9)
+    cfg = lat.get_config()
+    cum, st = lat.state()
+    (L, nt), th = lat.autotune(1200.0, 1)
+    assert lat.schedule() == (L, nt)
+    assert (lat.get_config() == cfg).all()
+    cum2, st2 = lat.state()
+    assert cum2 == cum and st2.tolist() == st.tolist()
+    lat.sweep(1200.0, 2, 9)
+    ref = cfg.copy()
+    if qsro:
+        rst = O.sweep_qsro(kind, dims, M, K, V, W, ref, 1200.0, 2, 9, sweep0=2, L=L, nt=nt)
+    else:
+        rst = O.sweep(kind, dims, M, K, V, ref, 1200.0, 2, 9, sweep0=2, L=L, nt=nt)
+    assert (lat.get_config() == ref).all()
+    assert (lat.state()[1] - st).tolist() == rst.tolist()
+    lat.close()
