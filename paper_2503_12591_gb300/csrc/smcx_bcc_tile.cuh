@@ -28,11 +28,46 @@ namespace smcx {
 
 namespace bccfast {
 
-constexpr int PX = 27;             // row pitch (cells)
-constexpr int PY = 24;             // rows per plane
+constexpr int PX = 25;             // row pitch (cells)
+constexpr int PP = 613;            // plane pitch (bytes: 24 rows + 13 bytes of padding)
 constexpr int PZ = 24;             // planes
-constexpr int SUB = PX * PY * PZ;  // bytes per sublattice array
+constexpr int SUB = PP * PZ;       // bytes per sublattice array
 constexpr int BOX = 24;            // usable box edge (tile <= 20 with halo 2)
+
+// Lane order of the 5^3 link-cell slots of a 20-cell tile (L = 4) on a
+// 128-thread CTA: slot kSlotOrder[t] for thread t (255: none).  Slot q =
+// (qx, qy, qz) = (q % 5, q / 5 % 5, q / 25) starts at byte qx 4 + qy 4 PX +
+// qz 4 PP of the box, i.e. word qx + qy PX + qz PP; the order gives the 32
+// lanes of every warp 32 different banks, so a neighbour load at a common
+// offset (all loads of the centre environment) is one wavefront.  Any order
+// gives the same result: the trials of a phase are independent.
+#define SMCX_BCC_SLOT_ORDER                                                                                          \
+  0, 1, 2, 3, 4, 21, 22, 23, 24, 29, 46, 15, 16, 17, 18, 19, 40, 41, 10, 11, 12, 13, 14, 35, 36, 5, 6, 7, 8, 9, 30, 31, 32, 33, 34, 55, 20, 25, 26, 27, 28, 45, 50, 47, 48, 49, 54, 71, 72, 73, 42, 43, 44, 65, 66, 67, 68, 37, 38, 39, 60, 61, 62, 63, 64, 85, 86, 87, 56, 57, 58, 59, 80, 81, 82, 51, 52, 53, 70, 75, 76, 77, 74, 79, 96, 97, 98, 99, 104, 69, 90, 91, 92, 93, 94, 115, 116, 117, 118, 119, 88, 89, 110, 111, 112, 113, 114, 83, 84, 105, 106, 107, 108, 109, 78, 95, 100, 101, 102, 103, 120, 121, 122, 123, 124, 255, 255, 255
+constexpr unsigned char kSlotOrder[128] = {SMCX_BCC_SLOT_ORDER};
+static __constant__ unsigned char c_slot_order[128] = {SMCX_BCC_SLOT_ORDER};
+__host__ __device__ constexpr bool slot_order_ok() {
+  for (int w = 0; w < 4; w++) {
+    bool seen[32] = {};
+    for (int l = 0; l < 32; l++) {
+      const int q = kSlotOrder[32 * w + l];
+      if (q == 255) continue;
+      const int bank = (q % 5 + PX * (q / 5 % 5) + PP * (q / 25)) % 32;
+      if (seen[bank]) return false;
+      seen[bank] = true;
+    }
+  }
+  bool used[125] = {};
+  for (int t = 0; t < 128; t++) {
+    const int q = kSlotOrder[t];
+    if (q == 255) continue;
+    if (q >= 125 || used[q]) return false;
+    used[q] = true;
+  }
+  for (int q = 0; q < 125; q++)
+    if (!used[q]) return false;
+  return true;
+}
+static_assert(slot_order_ok(), "slot order must cover the 125 slots with distinct banks per warp");
 constexpr int MAXPLANES = 3;
 
 // Byte planes of the EPI table, shared by every lattice of a launch:
@@ -87,7 +122,7 @@ __host__ __device__ constexpr VecTable make_vecs() {
 __host__ __device__ constexpr int floor2(int p) { return p >= 0 ? p / 2 : -((1 - p) / 2); }
 // byte offset (in the box) from a site of sublattice B to its neighbour along v
 __host__ __device__ constexpr int nb_offset(int B, int x, int y, int z) {
-  return (((B + x) & 1) - B) * SUB + (floor2(B + z) * PY + floor2(B + y)) * PX + floor2(B + x);
+  return (((B + x) & 1) - B) * SUB + floor2(B + z) * PP + floor2(B + y) * PX + floor2(B + x);
 }
 
 __device__ __forceinline__ int dp4a_su(int a, uint32_t b, int c) {
@@ -150,7 +185,7 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   const int dir = (int)(rd >> 29);  // floor(rd * 8 / 2^32)
   // shell-1 vector (+-1,+-1,+-1): bit 2 -> x, bit 1 -> y, bit 0 -> z
   const int dx = ((dir >> 2) & 1) - 1 + B, dy = ((dir >> 1) & 1) - 1 + B, dz = (dir & 1) - 1 + B;
-  const int sp = s + (1 - 2 * B) * SUB + (dz * PY + dy) * PX + dx;
+  const int sp = s + (1 - 2 * B) * SUB + dz * PP + dy * PX + dx;
   const uint32_t a8 = box[s], b8 = box[sp];
   if (a8 == b8) {
     same++;
@@ -362,7 +397,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
         s0 = byte & 15u;
         s1 = byte >> 4;
       }
-      const int bi = (zs * PY + ys) * PX + xs;
+      const int bi = zs * PP + ys * PX + xs;
       box[bi] = (uint8_t)(s0 << 3);
       box[SUB + bi] = (uint8_t)(s1 << 3);
     }
@@ -373,9 +408,12 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   const int NQ = D.NQ, L = D.L;
   int qx[SLOTS], qy[SLOTS], qz[SLOTS];
   bool slot[SLOTS];
+  // the bank-spreading lane order for the default shape (5^3 slots, 128
+  // threads, one slot each); plain order otherwise
+  const bool ordered = SLOTS == 1 && NQ == 5 && nth == 128;
 #pragma unroll
   for (int j = 0; j < SLOTS; j++) {
-    const int q = tid + j * nth;
+    const int q = ordered ? (int)c_slot_order[tid] : tid + j * nth;
     qx[j] = q % NQ;
     qy[j] = (q / NQ) % NQ;
     qz[j] = q / (NQ * NQ);
@@ -398,7 +436,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
             const uint4 rw = attempt_block(cell * 2, sweep, D.replica, D.seed_lo, D.seed_hi);
             keep_d[j] = rw.z;
             keep_u[j] = rw.w;
-            const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+            const int s = (zr + h) * PP + (yr + h) * PX + (xr + h);
             if (PROP == 1)
               trial_shared_dir<0, K, NW, PL>(box, s, s_dir[((cz * L + cy) * L + cx) * 2], rw.y, Q, D.nA, sA, sB, acc,
                                              same, dsum);
@@ -411,7 +449,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
         for (int j = 0; j < SLOTS; j++) {
           const int xr = cx + L * qx[j], yr = cy + L * qy[j], zr = cz + L * qz[j];
           if (slot[j] && xr < ts[0] && yr < ts[1] && zr < ts[2]) {
-            const int s = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+            const int s = (zr + h) * PP + (yr + h) * PX + (xr + h);
             if (PROP == 1)
               trial_shared_dir<1, K, NW, PL>(box, SUB + s, s_dir[((cz * L + cy) * L + cx) * 2 + 1], keep_u[j], Q,
                                              D.nA, sA, sB, acc, same, dsum);
@@ -431,7 +469,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
     for (int xw = lane; xw < wx; xw += 32) {
       const int gx = wrap_add(t0[0] - 1, xw, nx);
       const long long cell = rbase + gx;
-      const int bi = ((zw + h - 1) * PY + (yw + h - 1)) * PX + (xw + h - 1);
+      const int bi = (zw + h - 1) * PP + (yw + h - 1) * PX + (xw + h - 1);
       const uint32_t s0 = box[bi] >> 3, s1 = box[SUB + bi] >> 3;
       if (D.storage == SMCX_INT8) {
         D.sites[2 * cell] = (uint8_t)s0;

@@ -54,7 +54,7 @@ __device__ __forceinline__ void stage_tile(const LatDesc& D, uint8_t* box, const
         s0 = byte & 15u;
         s1 = byte >> 4;
       }
-      const int bi = (zs * PY + ys) * PX + xs;
+      const int bi = zs * PP + ys * PX + xs;
       box[bi] = (uint8_t)(s0 << 3);
       box[SUB + bi] = (uint8_t)(s1 << 3);
     }
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
   constexpr VecTable T = make_vecs();
   for (int c = tid; c < ncell; c += nth) {
     const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
-    const int s0 = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+    const int s0 = (zr + h) * PP + (yr + h) * PX + (xr + h);
 #pragma unroll
     for (int B = 0; B < 2; B++) {
       const int s = s0 + B * SUB;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_bcc_energy(const LatDesc D, const Plane
   constexpr VecTable T = make_vecs();
   for (int c = tid; c < ncell; c += nth) {
     const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
-    const int s0 = ((zr + h) * PY + (yr + h)) * PX + (xr + h);
+    const int s0 = (zr + h) * PP + (yr + h) * PX + (xr + h);
     int g = 0;
 #pragma unroll
     for (int B = 0; B < 2; B++) {
