@@ -664,10 +664,11 @@ def run_smcx(args, rank, world, local_rank):
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
-        host = torch.empty(WORK.sites, dtype=torch.int8, pin_memory=True)
-        lat.get_config_ptr(host.data_ptr())
+        nbytes = lat.store_bytes()
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        lat.get_config_store_ptr(host.data_ptr(), nbytes)
         for _ in range(2):
-            lat.set_config_ptr(host.data_ptr())
+            lat.set_config_store_ptr(host.data_ptr(), nbytes)
             lat.sweep(T_KELVIN, 1, SEED)
             lat.energy()
         barrier()
@@ -676,7 +677,7 @@ def run_smcx(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(ne):
             ta = time.perf_counter()
-            lat.set_config_ptr(host.data_ptr())   # H2D of the step's input configuration (returns after upload + check)
+            lat.set_config_store_ptr(host.data_ptr(), nbytes)  # H2D of the step's input (returns after upload + check)
             t_cfg += time.perf_counter() - ta
             lat.sweep(T_KELVIN, 1, SEED)
             lat.energy()                          # D2H of the step's result
@@ -685,9 +686,10 @@ def run_smcx(args, rank, world, local_rank):
         if dist is not None:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dt = float(tt.item())
-        e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": WORK.sites,
+        e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 8, "steps": ne,
-               "step": "smcx_set_config (int8 ids, pinned host) + smcx_sweep (1 sweep) + smcx_energy",
+               "step": "smcx_set_config_store (packed 4-bit store layout, pinned host) + smcx_sweep (1 sweep) + "
+                       "smcx_energy",
                "ms_per_step": dt * 1e3 / ne, "ms_set_config": t_cfg * 1e3 / ne,
                "ms_sweep_and_energy": (dt - t_cfg) * 1e3 / ne}
         del host

@@ -306,6 +306,16 @@ int smcx_cluster_summary(smcx_lattice* h, const int32_t* d_labels, int64_t min_s
 int smcx_get_config(smcx_lattice* h, int8_t* host);
 int smcx_set_config(smcx_lattice* h, const int8_t* host);
 
+/* The same in the lattice store's own layout (no conversion on either side):
+ * smcx_store_bytes gives its size, N bytes for SMCX_INT8 and N/2 for
+ * SMCX_PACKED4 (two sites per byte, the even site of each pair in the low
+ * nibble).  set_config_store checks every id < M on the device before the
+ * store is touched (SMCX_E_INVALID_ARG otherwise, lattice unchanged); `bytes`
+ * must equal the store size. */
+int smcx_store_bytes(const smcx_lattice* h, size_t* bytes);
+int smcx_get_config_store(smcx_lattice* h, uint8_t* host, size_t bytes);
+int smcx_set_config_store(smcx_lattice* h, const uint8_t* host, size_t bytes);
+
 /* Cumulative sweep index and trial statistics since creation (int64[4]):
  * stats[0] = trials, stats[1] = accepted swaps, stats[2] = proposals whose
  * two sites held the same species (no-ops; counted as trials), stats[3] =

@@ -527,6 +527,42 @@ int smcx_get_config(smcx_lattice* h, int8_t* host) {
   });
 }
 
+static size_t store_bytes(const smcx_lattice* h) {
+  return (size_t)(h->storage == SMCX_INT8 ? h->N : (h->N + 1) / 2);
+}
+
+int smcx_store_bytes(const smcx_lattice* h, size_t* bytes) {
+  return guarded([&] {
+    need(h && bytes, SMCX_E_INVALID_ARG, "NULL argument");
+    *bytes = store_bytes(h);
+  });
+}
+
+int smcx_get_config_store(smcx_lattice* h, uint8_t* host, size_t bytes) {
+  return guarded([&] {
+    need(h && host, SMCX_E_INVALID_ARG, "NULL argument");
+    need(bytes == store_bytes(h), SMCX_E_INVALID_ARG, "buffer size must equal the store size");
+    check_cuda(cudaMemcpyAsync(host, h->d_sites, bytes, cudaMemcpyDeviceToHost, h->stream), "store download");
+    check_cuda(cudaStreamSynchronize(h->stream), "store download sync");
+  });
+}
+
+int smcx_set_config_store(smcx_lattice* h, const uint8_t* host, size_t bytes) {
+  return guarded([&] {
+    need(h && host, SMCX_E_INVALID_ARG, "NULL argument");
+    need(bytes == store_bytes(h), SMCX_E_INVALID_ARG, "buffer size must equal the store size");
+    ensure_stage(h);  // N bytes >= the store size
+    check_cuda(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream), "clear flag");
+    check_cuda(cudaMemcpyAsync(h->d_stage, host, bytes, cudaMemcpyHostToDevice, h->stream), "store upload");
+    validate_store_at(h, h->d_stage);
+    int flag = 0;
+    check_cuda(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "flag download");
+    check_cuda(cudaStreamSynchronize(h->stream), "store upload sync");
+    need(flag == 0, SMCX_E_INVALID_ARG, "configuration holds species ids outside 0..M-1");
+    check_cuda(cudaMemcpyAsync(h->d_sites, h->d_stage, bytes, cudaMemcpyDeviceToDevice, h->stream), "store copy");
+  });
+}
+
 int smcx_set_config(smcx_lattice* h, const int8_t* host) {
   return guarded([&] {
     need(h && host, SMCX_E_INVALID_ARG, "NULL argument");

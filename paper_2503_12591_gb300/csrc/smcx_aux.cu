@@ -270,8 +270,10 @@ __global__ void k_validate_store(const uint8_t* sites, long long count, int stor
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-void validate_store(smcx_lattice* hd) {
-  k_validate_store<<<1024, 256, 0, hd->stream>>>(hd->d_sites, hd->N, hd->storage, hd->M, hd->d_flag);
+void validate_store(smcx_lattice* hd) { validate_store_at(hd, hd->d_sites); }
+
+void validate_store_at(smcx_lattice* hd, const uint8_t* d_store) {
+  k_validate_store<<<1024, 256, 0, hd->stream>>>(d_store, hd->N, hd->storage, hd->M, hd->d_flag);
   check_cuda(cudaGetLastError(), "validate launch");
 }
 

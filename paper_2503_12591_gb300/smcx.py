@@ -47,6 +47,9 @@ _SIGS = {
                                        C.c_void_p, C.c_void_p]),
     "smcx_set_qsro": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_autotune": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_void_p, C.c_void_p]),
+    "smcx_store_bytes": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smcx_get_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "smcx_set_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -251,6 +254,27 @@ class Lattice:
         th = np.zeros(1, np.int32)
         _check(lib().smcx_autotune(self._h, float(T), int(trial_sweeps), C.byref(sc), _p(th)))
         return (int(sc.L), tuple(int(t) for t in sc.nt)), int(th[0])
+
+    def store_bytes(self):
+        n = np.zeros(1, np.uint64)
+        _check(lib().smcx_store_bytes(self._h, _p(n)))
+        return int(n[0])
+
+    def get_config_store(self):
+        """The lattice store as stored (int8 ids or packed nibbles)."""
+        out = np.empty(self.store_bytes(), np.uint8)
+        _check(lib().smcx_get_config_store(self._h, _p(out), out.size))
+        return out
+
+    def get_config_store_ptr(self, ptr, nbytes):
+        _check(lib().smcx_get_config_store(self._h, C.c_void_p(int(ptr)), int(nbytes)))
+
+    def set_config_store(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().smcx_set_config_store(self._h, _p(buf), buf.size))
+
+    def set_config_store_ptr(self, ptr, nbytes):
+        _check(lib().smcx_set_config_store(self._h, C.c_void_p(int(ptr)), int(nbytes)))
 
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))

@@ -320,3 +320,32 @@ def test_autotune_restores_state_and_stays_exact(stream, kind, K, dims, M, qsro)
     assert (lat.get_config() == ref).all()
     assert (lat.state()[1] - st).tolist() == rst.tolist()
     lat.close()
+
+
+@pytest.mark.parametrize("storage", [smcx.INT8, smcx.PACKED4], ids=["int8", "packed4"])
+def test_config_store_layout_io(stream, storage):
+    kind, dims, M = smcx.BCC, (10, 8, 12), 4
+    N = O.n_sites(kind, dims)
+    cfg = np.random.default_rng(4).integers(0, M, N).astype(np.int8)
+    lat = smcx.Lattice(kind, dims, M, [0.25] * 4, storage=storage, stream=stream)
+    lat.set_config(cfg)
+    raw = lat.get_config_store()
+    if storage == smcx.INT8:
+        assert raw.size == N and (raw.view(np.int8) == cfg).all()
+    else:
+        u = cfg.astype(np.uint8)
+        assert raw.size == N // 2 and (raw == (u[0::2] | (u[1::2] << 4))).all()
+    other = smcx.Lattice(kind, dims, M, [0.25] * 4, init_seed=9, storage=storage, stream=stream)
+    before = other.get_config()
+    bad = raw.copy()
+    bad[3] = 0xF7 if storage == smcx.PACKED4 else 9  # an id >= M
+    with pytest.raises(smcx.SmcxError) as e:
+        other.set_config_store(bad)
+    assert e.value.code == smcx.E_INVALID_ARG
+    assert (other.get_config() == before).all()
+    with pytest.raises(smcx.SmcxError):
+        other.set_config_store(raw[:-1])
+    other.set_config_store(raw)
+    assert (other.get_config() == cfg).all()
+    lat.close()
+    other.close()
