@@ -24,9 +24,13 @@ namespace smcx {
 //   dE = sum_k sum_c W_k[c] (n_k(s)[c] - n_k(s')[c]) + X,
 //   W_k[c] = V_k[b][c] - V_k[a][c],  X = 2 V_1[a][b] - V_1[a][a] - V_1[b][b],
 // where n_k(i)[c] counts shell-k neighbours of i with species c (the partner
-// included); X removes the s-s' bond, which a swap leaves unchanged.
+// included); X removes the s-s' bond, which a swap leaves unchanged.  The
+// tile kernel keeps n_k(s) - n_k(s') in byte-packed counters (NW words of
+// four species per shell, each byte biased by 0x80 so that the difference
+// never borrows across bytes: at most z_k <= 24 either way), so a trial reads
+// each neighbour once and the table K*M times.
 
-template <int KIND, int K>
+template <int KIND, int K, int NW>
 __global__ void __launch_bounds__(256) k_tile_sweep(const SweepParams P) {
   constexpr int m = cell_sites(KIND);
   constexpr int NV = vec_count(KIND, K);
@@ -127,12 +131,22 @@ __global__ void __launch_bounds__(256) k_tile_sweep(const SweepParams P) {
       }
       const int32_t* W = s_w + (sa * M + sb) * KM;
       int dE = s_w[MM * KM + sa * M + sb];
+      uint32_t hc[K][NW];
+#pragma unroll
+      for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int w = 0; w < NW; w++) hc[k][w] = 0x80808080u;
       {
         int j = 0;
 #pragma unroll
         for (int k = 0; k < K; k++) {
 #pragma unroll
-          for (int q = 0; q < shell_size(KIND, k); q++, j++) dE += W[k * M + box[s + s_off[b * NV + j]]];
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            const uint32_t c = (uint32_t)box[s + s_off[b * NV + j]];
+            const uint32_t one = 1u << (8 * (c & 3));
+            if (NW == 1 || c < 4) hc[k][0] += one;
+            else hc[k][NW - 1] += one;
+          }
         }
       }
       {
@@ -140,9 +154,19 @@ __global__ void __launch_bounds__(256) k_tile_sweep(const SweepParams P) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
 #pragma unroll
-          for (int q = 0; q < shell_size(KIND, k); q++, j++) dE -= W[k * M + box[sp + s_off[bp * NV + j]]];
+          for (int q = 0; q < shell_size(KIND, k); q++, j++) {
+            const uint32_t c = (uint32_t)box[sp + s_off[bp * NV + j]];
+            const uint32_t one = 1u << (8 * (c & 3));
+            if (NW == 1 || c < 4) hc[k][0] -= one;
+            else hc[k][NW - 1] -= one;
+          }
         }
       }
+#pragma unroll
+      for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int c = 0; c < 4 * NW; c++)
+          if (c < M) dE += ((int)((hc[k][c >> 2] >> (8 * (c & 3))) & 0xFFu) - 0x80) * W[k * M + c];
       if (metropolis_accept(dE, ru, s_A, P.nA, s_B)) {
         box[s] = (int8_t)sb;
         box[sp] = (int8_t)sa;
@@ -309,8 +333,8 @@ static void fill_offsets(const smcx_lattice* hd, SweepParams& P, int BX, int BY)
   }
 }
 
-template <int KIND, int K>
-static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, int n_colours) {
+template <int KIND, int K, int NW>
+static void launch_sweeps_nw(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, int n_colours) {
   const smcx_sched& sc = hd->sched;
   cudaStream_t st = hd->stream;
   if (sc.nt[0] == 1 && sc.nt[1] == 1 && sc.nt[2] == 1) {
@@ -335,18 +359,28 @@ static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, in
   const size_t smem = (size_t)(nW + P.nA + kNB + m * NV + 2 * m * Z1) * 4 +
                       (size_t)P.BX * P.BY * P.BZ * m;
   if (smem > 227 * 1024) fail(SMCX_E_UNSUPPORTED, "tile too large for shared memory");
-  check_cuda(cudaFuncSetAttribute(k_tile_sweep<KIND, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  check_cuda(cudaFuncSetAttribute(k_tile_sweep<KIND, K, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem),
              "tile sweep smem attribute");
+  // a phase has ceil(tile / L)^3 trials: one 128-thread CTA when they fit
+  int slots = 1;
+  for (int a = 0; a < 3; a++) slots *= ((P.n[a] + P.nt[a] - 1) / P.nt[a] + P.L - 1) / P.L;
+  const int threads = slots <= 128 ? 128 : 256;
   for (int64_t s = 0; s < n_sweeps; s++) {
     P.sweep = hd->sweep_cum + (uint64_t)s;
     for (int tc = 0; tc < n_colours; tc++) {
       P.tc = tc;
       const int grid = P.ntc[0] * P.ntc[1] * P.ntc[2];
-      k_tile_sweep<KIND, K><<<grid, 256, smem, st>>>(P);
+      k_tile_sweep<KIND, K, NW><<<grid, threads, smem, st>>>(P);
     }
   }
   check_cuda(cudaGetLastError(), "tile sweep launch");
+}
+
+template <int KIND, int K>
+static void launch_sweeps(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps, int n_colours) {
+  if (hd->M <= 4) launch_sweeps_nw<KIND, K, 1>(hd, P, n_sweeps, n_colours);
+  else launch_sweeps_nw<KIND, K, 2>(hd, P, n_sweeps, n_colours);
 }
 
 void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
