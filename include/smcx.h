@@ -141,7 +141,7 @@ int smcx_lattice_create(smcx_lattice** out, int kind, int nx, int ny, int nz, in
 /*
  * Make a handle over a lattice store the caller already holds on the device
  * (e.g. the storage of a framework tensor), without copying it.
- *   d_sites   device (or managed) pointer to the species of the N sites in
+ *   d_sites   16-byte aligned device (or managed) pointer to the species of the N sites in
  *             canonical site order, in the layout of `storage`: one byte per
  *             site (SMCX_INT8) or two sites per byte, the even site in the
  *             low nibble (SMCX_PACKED4).  The caller keeps ownership; the

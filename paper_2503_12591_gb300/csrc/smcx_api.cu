@@ -180,6 +180,8 @@ int smcx_lattice_wrap(smcx_lattice** out, int kind, int nx, int ny, int nz, int 
     check_cuda(cudaPointerGetAttributes(&attr, d_sites), "pointer attributes");
     need(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged, SMCX_E_INVALID_ARG,
          "lattice store is not device memory");
+    need(reinterpret_cast<uintptr_t>(d_sites) % 16 == 0, SMCX_E_INVALID_ARG,
+         "lattice store must be 16-byte aligned");
     smcx_lattice* h = new smcx_lattice();
     try {
       h->owns_sites = false;

@@ -8,10 +8,11 @@
 // only the data layout and the instruction mix differ.
 //
 //  * Shared memory holds one byte per site, the species id times 8, in two
-//    sublattice arrays with padded pitches (27 x 24 cells per plane) that
-//    spread a phase's lanes over the banks.  The box pitches are compile-time
-//    constants, so every neighbour load is a single LDS with an immediate
-//    offset from the centre (or partner) address.
+//    sublattice arrays with padded pitches (25-byte rows, 613-byte planes)
+//    and a lane order that put the 32 centre sites of a warp on 32 banks.
+//    The box pitches are compile-time constants, so every neighbour load is a
+//    single LDS with an immediate offset from the centre (or partner)
+//    address.
 //  * Each neighbour adds 1 << (8 sigma) to a per-shell register of byte
 //    counters (biased by 0x80 per byte): the s environment adds, the s'
 //    environment subtracts, so byte c ends as 0x80 + n_k(s)[c] - n_k(s')[c].
@@ -377,29 +378,41 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
     }
   }
 
-  // stage tile + 2-cell halo: one box row (fixed y, z) per warp iteration
+  // stage tile + 2-cell halo
   constexpr int h = 2;
   const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
   const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
-  for (int row = warp; row < ey * ez; row += nwarp) {
-    const int ys = row % ey, zs = row / ey;
-    const int gy = wrap_add(t0[1] - h, ys, ny), gz = wrap_add(t0[2] - h, zs, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xs = lane; xs < ex; xs += 32) {
-      const int gx = wrap_add(t0[0] - h, xs, nx);
-      const long long cell = rbase + gx;
-      uint32_t s0, s1;
-      if (D.storage == SMCX_INT8) {
-        s0 = D.sites[2 * cell];
-        s1 = D.sites[2 * cell + 1];
-      } else {
-        const uint32_t byte = D.sites[cell];
-        s0 = byte & 15u;
-        s1 = byte >> 4;
+  // ex <= BOX = 24 < 32: one lane per box column.  Each warp first issues the
+  // loads of U rows, then unpacks and stores them, so U global loads per lane
+  // are in flight instead of one.
+  constexpr int U = 8;
+  const int rows = ey * ez;
+  const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
+  for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
+    uint32_t v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int row = row0 + u;
+      v[u] = 0;
+      if (row < rows && lane < ex) {
+        const int ys = row % ey, zs = row / ey;
+        const long long cell =
+            ((long long)wrap_add(t0[2] - h, zs, nz) * ny + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
+        v[u] = D.storage == SMCX_INT8 ? (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell))
+                                      : (uint32_t)D.sites[cell];
       }
-      const int bi = zs * PP + ys * PX + xs;
-      box[bi] = (uint8_t)(s0 << 3);
-      box[SUB + bi] = (uint8_t)(s1 << 3);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int row = row0 + u;
+      if (row < rows && lane < ex) {
+        const int ys = row % ey, zs = row / ey;
+        const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
+        const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
+        const int bi = zs * PP + ys * PX + lane;
+        box[bi] = (uint8_t)(s0 << 3);
+        box[SUB + bi] = (uint8_t)(s1 << 3);
+      }
     }
   }
   __syncthreads();
