@@ -74,6 +74,30 @@ __device__ __forceinline__ void stage_tile(const LatDesc& D, uint8_t* box, const
   }
 }
 
+// Exact division of 0 <= c < 2^16 by 2 <= d < 2^10 with a 32-bit multiply-high
+// by m = ceil(2^32 / d): c m / 2^32 = c / d + c e / 2^32 with 0 <= e < 1, and
+// c e / 2^32 < 2^-16 < 1 / d, so the floor is c / d (d = 1 passes c through).
+struct FastDiv {
+  uint32_t d, m;
+  __device__ __forceinline__ explicit FastDiv(uint32_t dd)
+      : d(dd), m(dd > 1 ? (uint32_t)((0xFFFFFFFFull) / dd + 1) : 0u) {}
+  __device__ __forceinline__ uint32_t div(uint32_t c) const { return d > 1 ? __umulhi(c, m) : c; }
+};
+
+// Cell c of a tile of ts[0] x ts[1] x ts[2] cells (x fastest).
+struct CellIndex {
+  FastDiv dx, dxy;
+  __device__ __forceinline__ CellIndex(const int ts[3]) : dx((uint32_t)ts[0]), dxy((uint32_t)(ts[0] * ts[1])) {}
+  __device__ __forceinline__ void at(int c, int& xr, int& yr, int& zr) const {
+    const uint32_t z = dxy.div((uint32_t)c);
+    const uint32_t r = (uint32_t)c - z * dxy.d;
+    const uint32_t y = dx.div(r);
+    zr = (int)z;
+    yr = (int)y;
+    xr = (int)(r - y * dx.d);
+  }
+};
+
 // Half of a shell: the vectors whose first nonzero half-unit component is
 // positive (one of each +v / -v pair).
 __host__ __device__ constexpr bool half_vec(const Vec& v) {
@@ -103,8 +127,10 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
     for (int p = 0; p < 4; p++) acc[k][p][0] = acc[k][p][1] = 0;
   const int ncell = ts[0] * ts[1] * ts[2];
   constexpr VecTable T = make_vecs();
+  const CellIndex ci(ts);
   for (int c = tid; c < ncell; c += nth) {
-    const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
+    int xr, yr, zr;
+    ci.at(c, xr, yr, zr);
     const int s0 = (zr + h) * PP + (yr + h) * PX + (xr + h);
 #pragma unroll
     for (int B = 0; B < 2; B++) {
@@ -179,8 +205,10 @@ __global__ void __launch_bounds__(256) k_bcc_energy(const LatDesc D, const Plane
   long long acc = 0;
   const int ncell = ts[0] * ts[1] * ts[2];
   constexpr VecTable T = make_vecs();
+  const CellIndex ci(ts);
   for (int c = tid; c < ncell; c += nth) {
-    const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
+    int xr, yr, zr;
+    ci.at(c, xr, yr, zr);
     const int s0 = (zr + h) * PP + (yr + h) * PX + (xr + h);
     int g = 0;
 #pragma unroll
