@@ -64,8 +64,9 @@ def parse():
     ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--no-qsro", action="store_true")
     ap.add_argument("--no-throughput", action="store_true")
+    ap.add_argument("--no-anneal", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput"],
+                                                    "throughput", "anneal"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
                     help="profiling only: FCC edge of the qsro / clusters measurement other than 400")
@@ -318,7 +319,7 @@ def run_exchange(stream):
     for l in lats:
         l.close()
     att = sites * EX_ROUNDS * EX_SPR
-    n_prop = sum(len(range(i & 1, EX_R - 1, 2)) for i in range(ctr))  # proposals since round 0
+    n_prop = sum(len(range(i & 1, EX_R - 1, 2)) for i in range(ctr))  # proposals since the first exchange round
     return {"value": att / s_ex, "unit": UNIT, "no_exchange_value": att / s_plain, "overhead": s_ex / s_plain,
             "exchange_acceptance": float(acc.sum()) / max(1, n_prop),
             "replicas": EX_R, "sites": sites, "rounds": EX_ROUNDS, "sweeps_per_round": EX_SPR,
@@ -419,6 +420,40 @@ def run_qsro(stream, edge=0):
             "kernel": "k_tile_sweep_qsro<FCC,3>",
             "workload": "FCC 400^3 = 256M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI N(0,30 meV) + "
                         "qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}
+
+
+def run_anneal(stream):
+    """The annealing driver on BCC 320^3 (65.5M sites, packed, the workload's
+    4-species 4-shell EPI): 2000 K down to 1000 K in 50 K steps (the paper's
+    schedule), 20 sweeps discarded and 40 recorded per temperature, exact
+    energy after every recorded sweep, C_V per site from its variance.  (A
+    checkerboard sweep runs (n / 2L)^3 trials at a time whatever the tiling,
+    so lattices much smaller than this leave the GPU idle: 4,096 at 128^3.)"""
+    import time as _t
+
+    import torch
+    from paper_2503_12591_gb300 import anneal, smcx
+
+    lat = smcx.Lattice(smcx.BCC, (320, 320, 320), WORK.M, WORK.comp, init_seed=3, storage=smcx.PACKED4,
+                       stream=stream)
+    lat.set_epi(WORK.epi())
+    temps = anneal.paper_schedule()
+    lat.sweep(temps[0], 2, SEED)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    steps = anneal.anneal(lat, temps, discard=20, record=40, seed=SEED)
+    dt = _t.perf_counter() - t0
+    n_sw = len(temps) * 60
+    N = lat.N
+    lat.close()
+    cv = [s.cv_per_site for s in steps]
+    k = int(np.argmax(cv))
+    return {"value": N * n_sw / dt, "unit": UNIT, "seconds": dt, "sweeps": n_sw, "temperatures": len(temps),
+            "cv_per_site_max": cv[k], "cv_peak_T": steps[k].T,
+            "cv_per_site": [round(c, 4) for c in cv], "acceptance_last_T": steps[-1].accept_rate,
+            "workload": "BCC 320^3 = 65,536,000 sites packed 4-bit, 4 species, 4-shell EPI N(0,20 meV); "
+                        "2000 -> 1000 K in 50 K steps, 20 discarded + 40 recorded sweeps per temperature; "
+                        "host wall time including the per-sweep exact energies (smcx_sweep_energies)"}
 
 
 def run_clusters(stream, edge=0):
@@ -745,6 +780,8 @@ def run_smcx(args, rank, world, local_rank):
         out["qsro"] = run_qsro(stream)
     if not args.no_throughput and world == 1:
         out["throughput_256"] = run_throughput256(stream)
+    if not args.no_anneal and world == 1:
+        out["anneal"] = run_anneal(stream)
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)
@@ -770,7 +807,7 @@ def main():
         import torch
         stream = torch.cuda.Stream()
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
-              "throughput": run_throughput256,
+              "throughput": run_throughput256, "anneal": run_anneal,
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:

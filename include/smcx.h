@@ -248,6 +248,18 @@ int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed);
  */
 int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* threads);
 
+/*
+ * n_sweeps sweeps as smcx_sweep, recording the exact energy after each one in
+ * E [n_sweeps] (host, int64, 0.01 meV) -- the series that energy-fluctuation
+ * observables such as the specific heat C_V = Var(E) / (k_B T^2) (Results,
+ * Fig. C_V) are computed from.  One energy pass at the start; after every
+ * sweep a one-thread kernel writes E_0 + (accepted dE since the start) into a
+ * device buffer that is read once at the end, so the host never waits
+ * between sweeps.  n_sweeps <= 2^24; temporary device memory 8 (n_sweeps + 1)
+ * bytes.
+ */
+int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E);
+
 /* Verification hook: run tile colours 0..n_colours-1 (0..8) of sweep number
  * `cumulative sweep index` without advancing the index, i.e. the first part
  * of the next smcx_sweep.  Tiles of one colour never interact, so after one

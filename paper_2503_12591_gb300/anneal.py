@@ -5,11 +5,11 @@ sweeps at each temperature and records the following ones to compute C_V
 (Method "MC simulation"; Results "Energy model", Fig. CV).  The specific heat
 is the textbook canonical fluctuation formula C_V = (<E^2> - <E>^2) / (k_B T^2).
 
-The energy after every sweep is read without any extra pass over the lattice:
-the library accumulates the exact sum of the accepted energy changes
-(smcx_get_state stats[3]), so E(t) = E(0) + (dsum(t) - dsum(0)).  Every number
-here is computed by the CUDA library; this module only schedules calls and
-sums the int64 energies it returns (FP64 moments).
+The energy after every sweep comes from smcx_sweep_energies: the library
+accumulates the exact sum of the accepted energy changes, so E(t) = E(0) +
+(dsum(t) - dsum(0)), recorded on the device after each sweep and read once.
+Every number here is computed by the CUDA library; this module only
+schedules calls and sums the int64 energies it returns (FP64 moments).
 """
 from dataclasses import dataclass, field
 from typing import List
@@ -33,13 +33,7 @@ class AnnealStep:
 
 def energy_trace(lat, T: float, n: int, seed: int):
     """Sweep n times at T; return the exact energy after each sweep."""
-    E = lat.energy()
-    d0 = int(lat.state()[1][3])
-    out = []
-    for _ in range(n):
-        lat.sweep(T, 1, seed)
-        out.append(E + int(lat.state()[1][3]) - d0)
-    return out
+    return [int(e) for e in lat.sweep_energies(T, n, seed)]
 
 
 def specific_heat(energies, T: float, n_sites: int) -> float:

@@ -450,6 +450,45 @@ int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* th
   });
 }
 
+int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E) {
+  return guarded([&] {
+    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+    need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi before smcx_sweep_energies");
+    need(h->sched.L != 0, SMCX_E_SCHEDULE, "no checkerboard schedule fits this lattice");
+    need(T > 0.0 && isfinite(T), SMCX_E_INVALID_ARG, "temperature must be finite and > 0");
+    need(n_sweeps >= 0 && n_sweeps <= (1 << 24), SMCX_E_INVALID_ARG, "n_sweeps must be 0..2^24");
+    need(n_sweeps == 0 || E != nullptr, SMCX_E_INVALID_ARG, "NULL energy buffer");
+    need(h->sweep_cum + (uint64_t)n_sweeps < (1ull << 63), SMCX_E_INVALID_ARG, "sweep counter overflow");
+    if (n_sweeps == 0) return;
+    // start energy into d_energy, accepted-dE sum at the start beside it
+    if (!energy_bcc_direct(h)) {
+      pair_counts_device(h);
+      energy_device(h);
+    }
+    if (!h->Wq.empty()) qsro_energy_add(h);
+    long long* d_buf = nullptr;
+    check_cuda(cudaMalloc(&d_buf, (size_t)(n_sweeps + 1) * sizeof(long long)), "energy trace");
+    try {
+      check_cuda(cudaMemcpyAsync(d_buf, h->d_stats + 3, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream),
+                 "dE sum snapshot");
+      upload_thresholds(h, T);
+      for (int64_t i = 0; i < n_sweeps; i++) {
+        sweep_device(h, h->thr_nA, seed, 1);
+        h->sweep_cum += 1;
+        record_energy(h, d_buf, d_buf + 1 + i);
+      }
+      check_cuda(cudaMemcpyAsync(E, d_buf + 1, (size_t)n_sweeps * sizeof(long long), cudaMemcpyDeviceToHost,
+                                 h->stream),
+                 "energy trace download");
+      check_cuda(cudaStreamSynchronize(h->stream), "energy trace sync");
+    } catch (...) {
+      cudaFree(d_buf);
+      throw;
+    }
+    cudaFree(d_buf);
+  });
+}
+
 int smcx_sweep_partial(smcx_lattice* h, double T, uint64_t seed, int n_colours) {
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");

@@ -272,6 +272,18 @@ __global__ void k_validate_store(const uint8_t* sites, long long count, int stor
 
 void validate_store(smcx_lattice* hd) { validate_store_at(hd, hd->d_sites); }
 
+// E_i = E_0 + (accepted dE sum now) - (accepted dE sum at the start): one
+// thread, enqueued after each sweep of smcx_sweep_energies.
+__global__ void k_record_energy(const long long* E0, const unsigned long long* stats, const long long* dsum0,
+                                long long* out) {
+  *out = *E0 + (long long)stats[3] - *dsum0;
+}
+
+void record_energy(smcx_lattice* hd, const long long* d_dsum0, long long* d_out) {
+  k_record_energy<<<1, 1, 0, hd->stream>>>(hd->d_energy, hd->d_stats, d_dsum0, d_out);
+  check_cuda(cudaGetLastError(), "energy record launch");
+}
+
 void validate_store_at(smcx_lattice* hd, const uint8_t* d_store) {
   k_validate_store<<<1024, 256, 0, hd->stream>>>(d_store, hd->N, hd->storage, hd->M, hd->d_flag);
   check_cuda(cudaGetLastError(), "validate launch");

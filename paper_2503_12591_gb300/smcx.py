@@ -50,6 +50,7 @@ _SIGS = {
     "smcx_store_bytes": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_get_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_set_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "smcx_sweep_energies": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -275,6 +276,12 @@ class Lattice:
 
     def set_config_store_ptr(self, ptr, nbytes):
         _check(lib().smcx_set_config_store(self._h, C.c_void_p(int(ptr)), int(nbytes)))
+
+    def sweep_energies(self, T, n_sweeps, seed):
+        """n_sweeps sweeps; the exact energy after each (int64 [n_sweeps])."""
+        E = np.zeros(max(1, int(n_sweeps)), np.int64)
+        _check(lib().smcx_sweep_energies(self._h, float(T), int(n_sweeps), int(seed), _p(E)))
+        return E[:int(n_sweeps)]
 
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))

@@ -169,3 +169,21 @@ def test_qsro_local_energy_and_clusters(stream, kind, K, dims, M):
     assert nc == onc
     assert (lab.cpu().numpy().astype(np.int64) == olab).all()
     lat.close()
+
+
+def test_qsro_sweep_energies_trace(stream):
+    """smcx_sweep_energies under the qSRO model: the recorded energy after
+    each sweep equals the oracle's qSRO energy of its configuration."""
+    kind, K, dims, M, sched = smcx.FCC, 3, (12, 8, 8), 4, (4, (4, 2, 2))
+    V = epi_gaussian(K, M, 20.0, 11)
+    W = _w(K, M, 12)
+    lat = smcx.Lattice(kind, dims, M, [0.25] * 4, init_seed=5, sched=sched, stream=stream)
+    lat.set_epi(V)
+    lat.set_qsro(W)
+    ref = lat.get_config()
+    E = lat.sweep_energies(900.0, 4, 13)
+    for i in range(4):
+        O.sweep_qsro(kind, dims, M, K, V, W, ref, 900.0, 1, 13, sweep0=i, L=sched[0], nt=sched[1])
+        assert E[i] == O.energy_qsro(kind, dims, M, K, V, W, ref)
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[0] == 4
