@@ -699,23 +699,33 @@ def run_smcx(args, rank, world, local_rank):
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
     if not args.no_e2e:
+        # Two handles on two streams: the upload of step i+1's input overlaps
+        # the sweep of step i (double buffering); every step still uploads its
+        # own input and reads back its own energy inside the timed region.
         nbytes = lat.store_bytes()
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        lat.get_config_store_ptr(host.data_ptr(), nbytes)
-        for _ in range(2):
-            lat.set_config_store_ptr(host.data_ptr(), nbytes)
-            lat.sweep(T_KELVIN, 1, SEED)
-            lat.energy()
+        stream2 = torch.cuda.Stream()
+        with torch.cuda.stream(stream2):
+            lat2 = smcx.Lattice(smcx.BCC, WORK.dims, WORK.M, WORK.comp, init_seed=WORK.init_seed + rank + 7,
+                                storage=smcx.PACKED4, stream=stream2)
+            lat2.set_epi(V)
+        hosts = [torch.empty(nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        lat.get_config_store_ptr(hosts[0].data_ptr(), nbytes)
+        lat2.get_config_store_ptr(hosts[1].data_ptr(), nbytes)
+        pair = [lat, lat2]
+        for i in range(2):  # warm-up of both handles
+            pair[i].set_config_store_ptr(hosts[i].data_ptr(), nbytes)
+            pair[i].sweep(T_KELVIN, 1, SEED)
+            pair[i].energy()
         barrier()
-        ne = max(2, min(args.steps, 5))
-        t_cfg = 0.0
+        ne = max(4, min(args.steps, 8))
         t0 = time.perf_counter()
-        for _ in range(ne):
-            ta = time.perf_counter()
-            lat.set_config_store_ptr(host.data_ptr(), nbytes)  # H2D of the step's input (returns after upload + check)
-            t_cfg += time.perf_counter() - ta
-            lat.sweep(T_KELVIN, 1, SEED)
-            lat.energy()                          # D2H of the step's result
+        pair[0].set_config_store_ptr(hosts[0].data_ptr(), nbytes)   # H2D of step 0's input
+        for i in range(ne):
+            cur, nxt = pair[i % 2], pair[(i + 1) % 2]
+            cur.sweep(T_KELVIN, 1, SEED)                              # enqueued; runs while the next upload goes
+            if i + 1 < ne:
+                nxt.set_config_store_ptr(hosts[(i + 1) % 2].data_ptr(), nbytes)  # H2D of step i+1's input
+            cur.energy()                                              # D2H of step i's result
         dt = time.perf_counter() - t0
         tt = torch.tensor([dt], device="cuda")
         if dist is not None:
@@ -724,9 +734,11 @@ def run_smcx(args, rank, world, local_rank):
         e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 8, "steps": ne,
                "step": "smcx_set_config_store (packed 4-bit store layout, pinned host) + smcx_sweep (1 sweep) + "
-                       "smcx_energy",
-               "ms_per_step": dt * 1e3 / ne, "ms_set_config": t_cfg * 1e3 / ne,
-               "ms_sweep_and_energy": (dt - t_cfg) * 1e3 / ne}
+                       "smcx_energy; two handles on two streams, the next step's upload overlapping this "
+                       "step's sweep",
+               "ms_per_step": dt * 1e3 / ne}
+        lat2.close()
+        host = hosts
         del host
 
     if rank != 0:
