@@ -31,7 +31,7 @@ namespace smcx {
 // each neighbour once and the table K*M times.
 
 template <int KIND, int K, int NW>
-__global__ void __launch_bounds__(256) k_tile_sweep(const SweepParams P) {
+__global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
   constexpr int m = cell_sites(KIND);
   constexpr int NV = vec_count(KIND, K);
   constexpr int Z1 = shell_size(KIND, 0);
@@ -362,10 +362,11 @@ static void launch_sweeps_nw(smcx_lattice* hd, SweepParams& P, int64_t n_sweeps,
   check_cuda(cudaFuncSetAttribute(k_tile_sweep<KIND, K, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem),
              "tile sweep smem attribute");
-  // a phase has ceil(tile / L)^3 trials: one 128-thread CTA when they fit
+  // a phase has up to ceil(tile / L)^3 trials: one thread each (whole warps,
+  // at most 512), so that a phase is one round of the CTA
   int slots = 1;
   for (int a = 0; a < 3; a++) slots *= ((P.n[a] + P.nt[a] - 1) / P.nt[a] + P.L - 1) / P.L;
-  const int threads = slots <= 128 ? 128 : 256;
+  const int threads = std::min(512, std::max(32, (slots + 31) / 32 * 32));
   for (int64_t s = 0; s < n_sweeps; s++) {
     P.sweep = hd->sweep_cum + (uint64_t)s;
     for (int tc = 0; tc < n_colours; tc++) {
