@@ -652,6 +652,10 @@ def run_smcx(args, rank, world, local_rank):
     for _ in range(args.warmup):
         lat.sweep(T_KELVIN, 1, SEED)
     lat.synchronize()
+    try:
+        lds_measured = smcx.probe_lds_rate(stream) / 1e9  # G lane-loads/s
+    except smcx.SmcxError:
+        lds_measured = None
 
     def barrier():
         if dist is not None:
@@ -750,7 +754,8 @@ def run_smcx(args, rank, world, local_rank):
     bytes_per_launch = ALG_BYTES_PER_ATTEMPT * WORK.sites / launches_per_sweep
     achieved_gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     gathers_per_launch = ALG_GATHERS_PER_ATTEMPT * WORK.sites / launches_per_sweep
-    lds_peak = SM_COUNT_NOMINAL * 32 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e9  # G lane-loads/s
+    lds_nominal = SM_COUNT_NOMINAL * 32 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e9  # G lane-loads/s
+    lds_peak = lds_measured if lds_measured else lds_nominal
     achieved_g = gathers_per_launch / (per_launch_ms / 1e3) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
@@ -769,8 +774,11 @@ def run_smcx(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved_g, "peak": lds_peak, "unit": "Gload/s",
                      "frac": achieved_g / lds_peak, "traffic": traffic,
                      "kernel": "k_bcc_tile_sweep",
-                     "note": "shared-memory gather roof: 70 lane-loads per trial (s, s' and 68 distinct "
-                             "neighbours) against 152 SMs x 32 lanes x 2070 MHz"},
+                     "peak_source": "measured (smcx_probe_lds_rate: conflict-free LDS.U8 stream on every SM)"
+                                    if lds_measured else "nominal (152 SMs x 32 lanes x 2070 MHz)",
+                     "peak_nominal": lds_nominal,
+                     "note": "shared-memory gather roof: 70 algorithmic lane-loads per trial (s, s' and 68 "
+                             "distinct neighbours) x trials per launch / launch time"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
                          "note": "1 B per trial (packed 4-bit read + write) per launch / launch time"},

@@ -474,6 +474,14 @@ int smcx_fluct_gradient(const double* d_acc, int K, int M, double T, double* d_g
 int smcx_energy_noalloc(int kind, int nx, int ny, int nz, int M, int storage, int K, const int32_t* V,
                         const void* d_sites, int64_t* E, void* stream);
 
+/*
+ * Measured shared-memory byte-load rate of the current device (entry point
+ * outside the paper: the denominator of the sweep kernels' on-chip roofline).
+ * Runs a conflict-free LDS.U8 stream on every SM (a few milliseconds,
+ * enqueued on `stream` and waited for) and returns lane-loads per second.
+ */
+int smcx_probe_lds_rate(double* lane_loads_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

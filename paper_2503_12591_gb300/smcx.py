@@ -51,6 +51,7 @@ _SIGS = {
     "smcx_get_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_set_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_sweep_energies": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
+    "smcx_probe_lds_rate": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
     "smcx_lattice_destroy": (C.c_int, [C.c_void_p]),
@@ -110,6 +111,13 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def probe_lds_rate(stream=None):
+    """Measured shared-memory byte-load rate of the device (lane-loads/s)."""
+    v = np.zeros(1, np.float64)
+    _check(lib().smcx_probe_lds_rate(_p(v), _stream_ptr(stream)))
+    return float(v[0])
 
 
 def exported_symbols():

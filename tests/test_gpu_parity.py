@@ -349,3 +349,12 @@ def test_config_store_layout_io(stream, storage):
     assert (other.get_config() == cfg).all()
     lat.close()
     other.close()
+
+
+def test_lds_probe_near_nominal_peak(stream):
+    """The measured shared-memory load rate is within a plausible band of the
+    nominal one (SMs x 32 lanes x SM clock)."""
+    rate = smcx.probe_lds_rate(stream)
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 32 * 2.07e9
+    assert 0.3 * nominal < rate < 1.2 * nominal, (rate, nominal)
