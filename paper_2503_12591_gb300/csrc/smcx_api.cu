@@ -388,60 +388,66 @@ int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* th
     const bool auto0 = h->sched_auto;
     const int threads0 = h->bcc_threads;
     const uint64_t sweep0 = h->sweep_cum;
-    upload_thresholds(h, T);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    check_cuda(cudaEventCreate(&e0), "event");
-    check_cuda(cudaEventCreate(&e1), "event");
     double best = 1e300;
     smcx_sched best_sc = sched0;
     int best_th = threads0;
-    const int Lmin = min_link_cell(h->shells);
-    for (int L = Lmin; L <= std::max(Lmin, 5); L++)
-      for (int target : {10, 12, 14, 16, 20})
-        for (int th : {0, 128, 256}) {
-          smcx_sched sc;
-          sc.L = L;
-          for (int a = 0; a < 3; a++) {
-            int nt = 2;
-            while ((h->n[a] + nt - 1) / nt > target) nt += 2;
-            sc.nt[a] = nt;
-          }
-          if (!schedule_problem(h->shells, h->n, sc).empty()) continue;
-          h->sched = sc;
-          h->bcc_threads = th;
-          const bool fast = h->kernel_choice != 1 && h->Wq.empty() && bcc_fast_usable(h);
-          if (th != 0 && !fast) continue;  // block size only matters to the BCC tile kernel
-          float ms = 0;
-          try {
-            sweep_device(h, h->thr_nA, 0x5eedull, 1);
-            check_cuda(cudaEventRecord(e0, h->stream), "event");
-            sweep_device(h, h->thr_nA, 0x5eedull, trial);
-            check_cuda(cudaEventRecord(e1, h->stream), "event");
-            check_cuda(cudaEventSynchronize(e1), "event sync");
-            check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
-          } catch (const SmcxException&) {
-            continue;
-          }
-          if (ms < best) {
-            best = ms;
-            best_sc = sc;
-            best_th = th;
-          }
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    check_cuda(cudaMemcpyAsync(h->d_sites, d_copy, h->site_bytes, cudaMemcpyDeviceToDevice, h->stream),
-               "autotune restore");
-    check_cuda(cudaMemcpyAsync(h->d_stats, st, sizeof(st), cudaMemcpyHostToDevice, h->stream), "stats restore");
-    check_cuda(cudaStreamSynchronize(h->stream), "autotune restore sync");
-    cudaFree(d_copy);
-    h->sweep_cum = sweep0;
-    if (best >= 1e300) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // put back the configuration, statistics and settings whatever happens
+    auto restore = [&]() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      cudaMemcpyAsync(h->d_sites, d_copy, h->site_bytes, cudaMemcpyDeviceToDevice, h->stream);
+      cudaMemcpyAsync(h->d_stats, st, sizeof(st), cudaMemcpyHostToDevice, h->stream);
+      cudaStreamSynchronize(h->stream);
+      cudaFree(d_copy);
+      h->sweep_cum = sweep0;
       h->sched = sched0;
       h->sched_auto = auto0;
       h->bcc_threads = threads0;
-      fail(SMCX_E_SCHEDULE, "no autotuner candidate fits this lattice");
+    };
+    try {
+      upload_thresholds(h, T);
+      check_cuda(cudaEventCreate(&e0), "event");
+      check_cuda(cudaEventCreate(&e1), "event");
+      const int Lmin = min_link_cell(h->shells);
+      for (int L = Lmin; L <= std::max(Lmin, 5); L++)
+        for (int target : {10, 12, 14, 16, 20})
+          for (int th : {0, 128, 256}) {
+            smcx_sched sc;
+            sc.L = L;
+            for (int a = 0; a < 3; a++) {
+              int nt = 2;
+              while ((h->n[a] + nt - 1) / nt > target) nt += 2;
+              sc.nt[a] = nt;
+            }
+            if (!schedule_problem(h->shells, h->n, sc).empty()) continue;
+            h->sched = sc;
+            h->bcc_threads = th;
+            const bool fast = h->kernel_choice != 1 && h->Wq.empty() && bcc_fast_usable(h);
+            if (th != 0 && !fast) continue;  // block size only matters to the BCC tile kernel
+            float ms = 0;
+            try {
+              sweep_device(h, h->thr_nA, 0x5eedull, 1);
+              check_cuda(cudaEventRecord(e0, h->stream), "event");
+              sweep_device(h, h->thr_nA, 0x5eedull, trial);
+              check_cuda(cudaEventRecord(e1, h->stream), "event");
+              check_cuda(cudaEventSynchronize(e1), "event sync");
+              check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+            } catch (const SmcxException&) {
+              continue;
+            }
+            if (ms < best) {
+              best = ms;
+              best_sc = sc;
+              best_th = th;
+            }
+          }
+    } catch (...) {
+      restore();
+      throw;
     }
+    restore();
+    if (best >= 1e300) fail(SMCX_E_SCHEDULE, "no autotuner candidate fits this lattice");
     h->sched = best_sc;
     h->sched_auto = false;
     h->bcc_threads = best_th;
