@@ -412,6 +412,16 @@ int smcx_batch_energy(smcx_batch* b, int64_t* E);
  */
 int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int64_t n_rounds,
                         int64_t sweeps_per_round, uint64_t seed, uint64_t* round_ctr, int64_t* accepts);
+
+/*
+ * smcx_lattice_fluct_accumulate for every replica of the batch in two launches
+ * (the tiled pair counts of all replicas' tiles, then one FP64 accumulator per
+ * replica): d_acc is a device array [R][1 + M^2 + K M^2 + M^2 K M^2], replica
+ * r's sums at offset r times that size, laid out as for
+ * smcx_fluct_accumulate (each replica with its own site count).  Needs
+ * M <= 4 (SMCX_E_UNSUPPORTED otherwise).  Returns after the sums are done.
+ */
+int smcx_batch_fluct_accumulate(smcx_batch* b, int shell, double* d_acc);
 int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_graph);
 int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
 

@@ -36,7 +36,15 @@ struct smcx_batch {
   bool items_dirty = true;
   int last_grid = 0;
   bool last_graph = false;
+  // fluctuation accumulation: per-replica descriptors, (replica, tile) items, counts
+  smcx::bccfast::LatDesc* d_fdesc = nullptr;
+  int2* d_fitems = nullptr;
+  unsigned long long* d_fcounts = nullptr;
+  size_t fitems_cap = 0;
 };
+
+void fluct_launch_per_sample(const long long* C, long long R, int K, int M, int shell, int z0, int zs, double* acc,
+                             cudaStream_t st);
 
 namespace smcx {
 
@@ -298,6 +306,9 @@ void batch_release(smcx_batch* b) {
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
   cudaFree(b->d_desc);
   cudaFree(b->d_items);
+  cudaFree(b->d_fdesc);
+  cudaFree(b->d_fitems);
+  cudaFree(b->d_fcounts);
   cudaFree(b->d_bar);
   cudaFree(b->d_status);
 }
@@ -476,6 +487,65 @@ void batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int6
   }
 }
 
+void pair_counts_bcc_multi(const bccfast::LatDesc* d_descs, const int2* d_items, int n_items, int K, int M,
+                           unsigned long long* d_counts, cudaStream_t st);  // smcx_reduce_bcc.cu
+
+// Fluctuation sums of every replica in two launches: the tiled pair counts of
+// all replicas' tiles in one grid, then one accumulator CTA per replica
+// (d_acc [R][1 + MM + KMM + MM KMM]).
+void batch_fluct_accumulate(smcx_batch* b, int shell, double* d_acc) {
+  check_batch(b);
+  const int R = (int)b->lat.size();
+  const smcx_lattice* h0 = b->lat[0];
+  const int K = h0->shells.K, M = h0->M;
+  if (shell < 0 || shell >= K) fail(SMCX_E_INVALID_ARG, "shell out of range");
+  if (M > 4) fail(SMCX_E_UNSUPPORTED, "batched fluctuation sums run M <= 4 (use smcx_lattice_fluct_accumulate)");
+  std::vector<bccfast::LatDesc> desc(R);
+  std::vector<int2> items;
+  for (int r = 0; r < R; r++) {
+    const smcx_lattice* h = b->lat[r];
+    bccfast::LatDesc& D = desc[r];
+    memset(&D, 0, sizeof(D));
+    D.sites = h->d_sites;
+    D.storage = h->storage;
+    D.M = M;
+    int ntiles = 1;
+    for (int a = 0; a < 3; a++) {
+      D.n[a] = h->n[a];
+      D.nt[a] = h->sched.nt[a];
+      if (D.nt[a] < 2 || h->n[a] < 6 || (h->n[a] + D.nt[a] - 1) / D.nt[a] + 4 > bccfast::BOX)
+        fail(SMCX_E_UNSUPPORTED, "replica tiles do not fit the tiled pair counts");
+      ntiles *= D.nt[a];
+    }
+    for (int t = 0; t < ntiles; t++) items.push_back(make_int2(r, t));
+  }
+  if (!b->d_fdesc) {
+    check_cuda(cudaMalloc(&b->d_fdesc, R * sizeof(bccfast::LatDesc)), "fluctuation descriptors");
+    check_cuda(cudaMalloc(&b->d_fcounts, (size_t)R * kMaxShells * 16 * sizeof(unsigned long long)),
+               "fluctuation counts");
+  }
+  if (items.size() > b->fitems_cap) {
+    cudaFree(b->d_fitems);
+    b->d_fitems = nullptr;
+    check_cuda(cudaMalloc(&b->d_fitems, items.size() * sizeof(int2)), "fluctuation items");
+    b->fitems_cap = items.size();
+  }
+  check_cuda(cudaMemcpyAsync(b->d_fdesc, desc.data(), R * sizeof(bccfast::LatDesc), cudaMemcpyHostToDevice,
+                             b->stream),
+             "fluctuation descriptor upload");
+  check_cuda(cudaMemcpyAsync(b->d_fitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                             b->stream),
+             "fluctuation item upload");
+  const int kmm = K * M * M;
+  check_cuda(cudaMemsetAsync(b->d_fcounts, 0, (size_t)R * kmm * sizeof(unsigned long long), b->stream),
+             "clear counts");
+  pair_counts_bcc_multi(b->d_fdesc, b->d_fitems, (int)items.size(), K, M, b->d_fcounts, b->stream);
+  fluct_launch_per_sample(reinterpret_cast<const long long*>(b->d_fcounts), R, K, M, shell, h0->shells.z[0],
+                          h0->shells.z[shell], d_acc, b->stream);
+  // the host descriptor and item arrays are pageable: wait before they go
+  check_cuda(cudaStreamSynchronize(b->stream), "fluctuation sync");
+}
+
 }  // namespace smcx
 
 namespace {
@@ -546,6 +616,13 @@ int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, 
     need_(b && T_slot && slot_rep && round_ctr, SMCX_E_INVALID_ARG, "NULL argument");
     need_(n_rounds >= 0 && sweeps_per_round >= 0, SMCX_E_INVALID_ARG, "negative round or sweep count");
     batch_exchange(b, T_slot, slot_rep, n_rounds, sweeps_per_round, seed, round_ctr, accepts);
+  });
+}
+
+int smcx_batch_fluct_accumulate(smcx_batch* b, int shell, double* d_acc) {
+  return guarded_call([&] {
+    need_(b && d_acc, SMCX_E_INVALID_ARG, "NULL argument");
+    batch_fluct_accumulate(b, shell, d_acc);
   });
 }
 

@@ -96,16 +96,31 @@ __global__ void k_epi_grad(const float* __restrict__ g, const long long* __restr
 //   acc[1 + MM + KMM + a * KMM + i] += sum w A_a C_i.
 // Each thread owns fixed entries and sums samples in order (deterministic).
 constexpr int kFluctOwn = 8;
+// With acc_stride > 0, CTA r takes sample r alone into acc + r acc_stride
+// (one accumulator per replica) and, for N <= 0, the site count of that
+// sample from its shell-1 counts (sum_pq C_1[p][q] = z_1 N).
 __global__ void k_fluct_accumulate(const long long* __restrict__ C, long long B, const double* __restrict__ w, int K,
-                                   int M, int sh, int z0, int zs, double N, double* __restrict__ acc) {
+                                   int M, int sh, int z0, int zs, double N, double* __restrict__ acc,
+                                   long long acc_stride) {
   extern __shared__ double sA[];  // MM
   const int MM = M * M, KMM = K * MM;
   const int total = 1 + MM + KMM + MM * KMM;
   double loc[kFluctOwn];
 #pragma unroll
   for (int j = 0; j < kFluctOwn; j++) loc[j] = 0.0;
-  for (long long b = 0; b < B; b++) {
+  long long b_lo = 0, b_hi = B;
+  if (acc_stride > 0) {
+    b_lo = blockIdx.x;
+    b_hi = b_lo + 1;
+    acc += b_lo * acc_stride;
+  }
+  for (long long b = b_lo; b < b_hi; b++) {
     const long long* Cb = C + b * KMM;
+    if (N <= 0.0) {
+      double n1 = 0.0;
+      for (int i = 0; i < MM; i++) n1 += (double)Cb[i];
+      N = n1 / z0;
+    }
     for (int a = threadIdx.x; a < MM; a += blockDim.x) {
       const int p = a / M, q = a % M;
       double Np = 0.0, Nq = 0.0;
@@ -240,15 +255,33 @@ int smcx_epi_grad_batch(const float* d_g, const int64_t* d_counts, int64_t B, in
   });
 }
 
+}  // extern "C"
+
 static void fluct_launch(const long long* C, long long B, const double* w, int K, int M, int shell, int z0, int zs,
                          double N, double* acc, cudaStream_t st) {
   const int MM = M * M, KMM = K * MM;
   const int total = 1 + MM + KMM + MM * KMM;
   const int threads = std::min(1024, std::max(128, ((total + kFluctOwn - 1) / kFluctOwn + 31) / 32 * 32));
   if ((long long)threads * kFluctOwn < total) fail(SMCX_E_UNSUPPORTED, "K*M*M too large for the accumulator");
-  k_fluct_accumulate<<<1, threads, MM * sizeof(double), st>>>(C, B, w, K, M, shell, z0, zs, N, acc);
+  k_fluct_accumulate<<<1, threads, MM * sizeof(double), st>>>(C, B, w, K, M, shell, z0, zs, N, acc, 0);
   check_cuda(cudaGetLastError(), "fluctuation accumulate launch");
 }
+
+// One accumulator per sample: sample r of C [R][K][M][M] into acc + r * (1 +
+// MM + KMM + MM KMM), each with its own site count.
+void fluct_launch_per_sample(const long long* C, long long R, int K, int M, int shell, int z0, int zs, double* acc,
+                             cudaStream_t st) {
+  const int MM = M * M, KMM = K * MM;
+  const long long total = 1 + MM + KMM + (long long)MM * KMM;
+  const int threads = std::min(1024, std::max(128, (int)((total + kFluctOwn - 1) / kFluctOwn + 31) / 32 * 32));
+  if ((long long)threads * kFluctOwn < total) fail(SMCX_E_UNSUPPORTED, "K*M*M too large for the accumulator");
+  if (R == 0) return;
+  k_fluct_accumulate<<<(unsigned)R, threads, MM * sizeof(double), st>>>(C, R, nullptr, K, M, shell, z0, zs, 0.0, acc,
+                                                                        total);
+  check_cuda(cudaGetLastError(), "fluctuation accumulate launch");
+}
+
+extern "C" {
 
 int smcx_fluct_accumulate(const int64_t* d_counts, int64_t B, const double* d_weights, int kind, int K, int M,
                           int shell, int64_t n_sites, double* d_acc, void* stream) {

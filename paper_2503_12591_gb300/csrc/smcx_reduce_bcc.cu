@@ -22,9 +22,8 @@ namespace bccfast {
 // The tile of this CTA (tiles numbered x fastest) and its staging: tile plus
 // a 2-cell halo into the sublattice byte arrays of the sweep's box layout,
 // species stored as 8 s.
-__device__ __forceinline__ void tile_of_block(const LatDesc& D, int t0[3], int ts[3]) {
+__device__ __forceinline__ void tile_of_index(const LatDesc& D, int t, int t0[3], int ts[3]) {
   const int ntx = D.nt[0], nty = D.nt[1];
-  const int t = blockIdx.x;
   const int ti[3] = {t % ntx, (t / ntx) % nty, t / (ntx * nty)};
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -104,15 +103,14 @@ __host__ __device__ constexpr bool half_vec(const Vec& v) {
   return v.x > 0 || (v.x == 0 && (v.y > 0 || (v.y == 0 && v.z > 0)));
 }
 
+// Pair counts of tile t of lattice D added into counts [K][M][M].
 template <int K>
-__global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned int hist[kMaxShells * 16];
-  uint8_t* box = smem;
+__device__ __forceinline__ void pair_counts_tile(const LatDesc& D, int t, unsigned long long* __restrict__ counts,
+                                                 uint8_t* box, unsigned int* hist) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31;
   int t0[3], ts[3];
-  tile_of_block(D, t0, ts);
+  tile_of_index(D, t, t0, ts);
   for (int i = tid; i < kMaxShells * 16; i += nth) hist[i] = 0;
   constexpr int h = 2;
   stage_tile(D, box, t0, ts);
@@ -183,6 +181,26 @@ __global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsign
   }
 }
 
+template <int K>
+__global__ void __launch_bounds__(256) k_bcc_pair_counts(const LatDesc D, unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int hist[kMaxShells * 16];
+  pair_counts_tile<K>(D, blockIdx.x, counts, smem, hist);
+}
+
+// Many lattices in one launch: CTA i takes tile items[i].y of lattice
+// items[i].x and adds into counts + items[i].x * kmm.
+template <int K>
+__global__ void __launch_bounds__(256) k_bcc_pair_counts_multi(const LatDesc* __restrict__ descs,
+                                                              const int2* __restrict__ items, int kmm,
+                                                              unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int hist[kMaxShells * 16];
+  const int2 it = items[blockIdx.x];
+  const LatDesc D = descs[it.x];
+  pair_counts_tile<K>(D, it.y, counts + (size_t)it.x * kmm, smem, hist);
+}
+
 // Energy directly (M <= 4): E = sum_i sum_k sum_{v in half shell k}
 // V_k[s_i][s_{i+v}], every unordered pair once.  Per site the half-shell
 // neighbours go into byte-packed per-species counters h_k (at most 12 per
@@ -197,7 +215,7 @@ __global__ void __launch_bounds__(256) k_bcc_energy(const LatDesc D, const Plane
   uint8_t* box = smem;
   const int tid = threadIdx.x, nth = blockDim.x;
   int t0[3], ts[3];
-  tile_of_block(D, t0, ts);
+  tile_of_index(D, blockIdx.x, t0, ts);
   for (int i = tid; i < PL * K * 4; i += nth) sP[i] = Q.P[i / (K * 4)][(i / 4) % K][i % 4][0];
   constexpr int h = 2;
   stage_tile(D, box, t0, ts);
@@ -297,6 +315,26 @@ void pair_counts_bcc_tiled(smcx_lattice* hd, const int nt[3]) {
 }
 
 int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
+
+// Pair counts of many BCC lattices (M <= 4, K shells) in one launch: d_descs
+// [R] and d_items [n_items] (lattice, tile) on the device, counts [R][K][M][M]
+// zeroed by the caller.
+void pair_counts_bcc_multi(const bccfast::LatDesc* d_descs, const int2* d_items, int n_items, int K, int M,
+                           unsigned long long* d_counts, cudaStream_t st) {
+  const size_t smem = 2 * bccfast::SUB;
+  const int kmm = K * M * M;
+  auto go = [&](auto kern) {
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "smem attr");
+    kern<<<n_items, 256, smem, st>>>(d_descs, d_items, kmm, d_counts);
+  };
+  switch (K) {
+    case 1: go(bccfast::k_bcc_pair_counts_multi<1>); break;
+    case 2: go(bccfast::k_bcc_pair_counts_multi<2>); break;
+    case 3: go(bccfast::k_bcc_pair_counts_multi<3>); break;
+    default: go(bccfast::k_bcc_pair_counts_multi<4>); break;
+  }
+  check_cuda(cudaGetLastError(), "batched pair-count launch");
+}
 
 // Energy of a BCC lattice with M <= 4 straight from the tiles (no pair-count
 // histogram); false when the tiled path does not apply.

@@ -90,3 +90,25 @@ class FluctuationEstimator:
     def mean_A(self) -> torch.Tensor:
         MM = self.M * self.M
         return (self.acc[1:1 + MM] / self.acc[0]).view(self.M, self.M)
+
+
+class BatchFluctuationEstimator:
+    """FluctuationEstimator for every replica of a smcx.Batch at once
+    (smcx_batch_fluct_accumulate): one accumulator row per replica."""
+
+    def __init__(self, batch: "smcx.Batch", K: int, M: int, shell: int, device="cuda"):
+        self.batch, self.K, self.M, self.shell = batch, K, M, shell
+        MM, KMM = M * M, K * M * M
+        R = len(batch.lattices)
+        self.acc = torch.zeros(R, 1 + MM + KMM + MM * KMM, dtype=torch.float64, device=device)
+
+    def add(self):
+        self.batch.fluct_accumulate(self.shell, self.acc.data_ptr())
+
+    def gradients(self, T: float) -> torch.Tensor:
+        """d<A>/dV per replica, [R, M*M, K, M, M] in 1/meV."""
+        MM, KMM = self.M * self.M, self.K * self.M * self.M
+        out = torch.empty(self.acc.shape[0], MM * KMM, dtype=torch.float64, device=self.acc.device)
+        for r in range(self.acc.shape[0]):
+            smcx.fluct_gradient(self.acc[r].data_ptr(), self.K, self.M, T, out[r].data_ptr(), _stream())
+        return out.view(-1, MM, self.K, self.M, self.M)

@@ -66,6 +66,7 @@ _SIGS = {
     "smcx_batch_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "smcx_batch_exchange": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_uint64,
                                       C.c_void_p, C.c_void_p]),
+    "smcx_batch_fluct_accumulate": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "smcx_batch_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smcx_batch_set_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
@@ -424,6 +425,11 @@ class Batch:
         _check(lib().smcx_batch_exchange(self._h, _p(T), _p(rep), int(n_rounds), int(sweeps_per_round), int(seed),
                                          _p(ctr), _p(acc)))
         return rep, int(ctr[0]), acc
+
+    def fluct_accumulate(self, shell, d_acc):
+        """Per-replica fluctuation sums into the device FP64 array at d_acc
+        ([R][1 + MM + KMM + MM*KMM])."""
+        _check(lib().smcx_batch_fluct_accumulate(self._h, int(shell), C.c_void_p(int(d_acc))))
 
     def energy(self):
         e = np.zeros(len(self.lattices), np.int64)

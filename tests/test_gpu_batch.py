@@ -152,3 +152,28 @@ def test_replica_exchange_rejects_bad_input(stream):
         b2.exchange([1000.0, 1100.0], [0, 0], 1, 1, 3)  # not a permutation
     with pytest.raises(smcx.SmcxError):
         b2.exchange([1000.0, -1.0], [0, 1], 1, 1, 3)
+
+
+def test_batch_fluct_accumulate_equals_per_lattice(stream):
+    """smcx_batch_fluct_accumulate gives every replica the same FP64 sums as
+    smcx_lattice_fluct_accumulate on that replica alone (same integer counts,
+    same accumulation order)."""
+    from paper_2503_12591_gb300 import diff
+    V = epi_gaussian(4, 4, 20.0, 1)
+    dims_list = [(12, 12, 12), (24, 14, 16), (13, 20, 18)]
+    scheds = [_sched(d, L=3 + (i % 2)) for i, d in enumerate(dims_list)]
+    lats = [_make(d, r, V, stream, scheds[r]) for r, d in enumerate(dims_list)]
+    b = smcx.Batch(lats, stream)
+    T = [900.0, 1100.0, 1300.0]
+    est = diff.BatchFluctuationEstimator(b, 4, 4, 1)
+    single = [diff.FluctuationEstimator(smcx.BCC, 4, 4, 1, l.N) for l in lats]
+    for _ in range(3):
+        b.sweep(T, 2, 5)
+        est.add()
+        for l, e in zip(lats, single):
+            e.add_lattice(l)
+    torch.cuda.synchronize()
+    for r, e in enumerate(single):
+        assert torch.equal(est.acc[r], e.acc), f"replica {r}"
+    g = est.gradients(1000.0)
+    assert torch.equal(g[1], single[1].gradient(1000.0))
