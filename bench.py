@@ -65,11 +65,12 @@ def parse():
     ap.add_argument("--no-qsro", action="store_true")
     ap.add_argument("--no-throughput", action="store_true")
     ap.add_argument("--no-anneal", action="store_true")
+    ap.add_argument("--no-fcc", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput", "anneal"],
+                                                    "throughput", "anneal", "fcc"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
-                    help="profiling only: FCC edge of the qsro / clusters measurement other than 400")
+                    help="profiling only: FCC edge of the fcc / qsro / clusters measurement other than 400")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -372,6 +373,45 @@ def run_throughput256(stream):
                          "default": {"L": default_sched[0], "tiles": list(default_sched[1])}},
             "workload": "BCC 256^3 = 33,554,432 sites int8, 4 species, 4-shell EPI N(0,20 meV); 1000 sweeps at "
                         "2500/1500/800 K, E + SRO every 100 sweeps (value includes them); L2-resident"}
+
+
+def run_fcc(stream, edge=0):
+    """The FCC scale workload (400^3 = 256M sites, 5 species, 3 shells, packed
+    4-bit, 1200 K; the paper's FeCoNiAlTi-like system): pair-model sweeps with
+    the library's schedule (FCC tile kernel), then with the autotuned one."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W_
+
+    if edge:
+        import dataclasses
+        W_ = dataclasses.replace(W_, dims=(edge,) * 3)
+    lat = smcx.Lattice(W_.kind, W_.dims, W_.M, W_.comp, init_seed=W_.init_seed, storage=W_.storage, stream=stream)
+    lat.set_epi(W_.epi())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    T = W_.temperatures[0]
+
+    def timed(n):
+        lat.sweep(T, 2, SEED)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.sweep(T, n, SEED)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    sched = lat.schedule()
+    ms = timed(10)
+    (L, nt), _ = lat.autotune(T, 2)
+    ms_t = timed(10)
+    N = lat.N
+    lat.close()
+    return {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms,
+            "schedule": {"L": sched[0], "tiles": list(sched[1])},
+            "autotuned_value": N / (ms_t / 1e3), "autotuned_schedule": {"L": L, "tiles": list(nt)},
+            "kernel": "k_fcc_tile_sweep",
+            "workload": f"FCC {W_.dims[0]}^3 = {N:,} sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI "
+                        "N(0,30 meV), packed 4-bit, 1200 K"}
 
 
 def run_qsro(stream, edge=0):
@@ -795,6 +835,8 @@ def run_smcx(args, rank, world, local_rank):
         out["gradient"] = run_gradient(stream)
     if not args.no_clusters and world == 1:
         out["clusters"] = run_clusters(stream)
+    if not args.no_fcc and world == 1:
+        out["fcc_400"] = run_fcc(stream)
     if not args.no_qsro and world == 1:
         out["qsro"] = run_qsro(stream)
     if not args.no_throughput and world == 1:
@@ -827,6 +869,7 @@ def main():
         stream = torch.cuda.Stream()
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
               "throughput": run_throughput256, "anneal": run_anneal,
+              "fcc": lambda st: run_fcc(st, args.edge),
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:

@@ -142,6 +142,8 @@ void validate_store_at(smcx_lattice* h, const uint8_t* d_store);  // same for a 
 void record_energy(smcx_lattice* h, const long long* d_dsum0, long long* d_out);  // d_energy + stats[3] - dsum0
 void local_energy_device(smcx_lattice* h, int32_t* d_e2);
 void sweep_qsro_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
+bool fcc_fast_usable(const smcx_lattice* h);
+void sweep_fcc_fast(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
 void qsro_energy_add(smcx_lattice* h);
 bool energy_bcc_direct(smcx_lattice* h);  // pair energy into d_energy; false if not applicable  // adds sum_i sum_k W[k][s_i] n_k(i)^2 to d_energy
 void clusters_device(smcx_lattice* h, long long thr2, int32_t* d_labels, int64_t* n_clusters);

@@ -389,6 +389,10 @@ void sweep_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int
     sweep_qsro_device(hd, nA, seed, n_sweeps, n_colours);
     return;
   }
+  if (hd->kernel_choice != 1 && fcc_fast_usable(hd)) {
+    sweep_fcc_fast(hd, nA, seed, n_sweeps, n_colours);
+    return;
+  }
   if (hd->kernel_choice != 1 && bcc_fast_usable(hd)) {
     sweep_bcc_fast(hd, nA, seed, n_sweeps, n_colours);
     return;

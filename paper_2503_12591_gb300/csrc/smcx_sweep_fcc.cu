@@ -1,0 +1,337 @@
+// FCC tile pass specialised for throughput (pair model, M <= 8 species,
+// K <= 3 shells, tiles up to 15 cells, link cells >= 3, one link-cell slot
+// per thread).  Same trials, same order of phases, same Philox words and the
+// same integer arithmetic as k_tile_sweep in smcx_sweep.cu: the result is
+// bit-identical; only the data layout and the instruction mix differ.
+//
+//  * FCC sites are the even points (x + y + z even) of the half-unit cubic
+//    grid.  Shared memory stores the box (tile + 2-cell halo, at most 38
+//    half units per axis) with the site at half-unit box position (x, y, z)
+//    in byte (x + y PXF + z PPF) / 2; PXF and PPF are odd, so the numerator
+//    of every site is even and no byte is wasted.  A neighbour along the
+//    lattice vector v is then at the constant offset (vx + vy PXF + vz PPF) /
+//    2 from any site, whatever its sublattice: every load of the centre and
+//    of the partner environment is one LDS with an immediate offset, and the
+//    partner itself is one table entry away.
+//  * Species are stored as 8 sigma; each neighbour adds 1 << (8 sigma) to a
+//    per-shell register of byte counters (biased by 0x80), the s environment
+//    adding and the s' environment subtracting; dE = G_b - G_a by dp4a
+//    against the byte planes of V (finish_trial of the BCC pass).
+//  * A thread owns one link-cell slot of the tile for the whole pass; the
+//    Philox block of a site pair (sublattices 0/1 and 2/3 of a cell) is drawn
+//    in the even phase and its second half used in the odd phase after it.
+#include "smcx_bcc_tile.cuh"
+
+namespace smcx {
+
+namespace fccfast {
+
+using bccfast::LatDesc;
+using bccfast::Planes;
+
+constexpr int H = 2;                  // halo cells
+constexpr int TMAX = 15;              // largest tile edge (cells)
+constexpr int EXT = 2 * (TMAX + 2 * H);  // box edge in half units (38)
+constexpr int PXF = EXT + 1;          // 39, odd
+constexpr int PPF = PXF * EXT + 1;    // 1483, odd
+constexpr int BOXB = ((EXT - 1) + (EXT - 1) * PXF + (EXT - 1) * PPF) / 2 + 1;  // bytes used
+constexpr int BOX_BYTES = (BOXB + 15) / 16 * 16;
+
+__host__ __device__ constexpr int hoff(int x, int y, int z) { return (x + y * PXF + z * PPF) / 2; }
+// FCC basis (0,0,0), (1,1,0), (1,0,1), (0,1,1) in half units: offset of site b in its cell
+__host__ __device__ constexpr int boff(int b) {
+  return hoff((b == 1 || b == 2) ? 1 : 0, (b == 1 || b == 3) ? 1 : 0, (b == 2 || b == 3) ? 1 : 0);
+}
+
+// FCC lattice vectors of shells 1..3 (|v|^2 = 2, 4, 6 half units squared),
+// shell-major, lexicographic inside a shell: the canonical order of the
+// library and the oracle (shell-1 index = partner direction).
+struct FVec {
+  int x, y, z, k;
+};
+struct FTable {
+  FVec v[42];
+  int n;
+};
+__host__ __device__ constexpr FTable make_fvecs() {
+  FTable t{};
+  t.n = 0;
+  for (int k = 0; k < 3; k++)
+    for (int x = -2; x <= 2; x++)
+      for (int y = -2; y <= 2; y++)
+        for (int z = -2; z <= 2; z++) {
+          if ((x + y + z) & 1) continue;
+          if (x * x + y * y + z * z == 2 * (k + 1)) {
+            t.v[t.n] = FVec{x, y, z, k};
+            t.n++;
+          }
+        }
+  return t;
+}
+
+template <int K, int NW, int SIGN>
+__device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[kMaxShells][2]) {
+  constexpr FTable T = make_fvecs();
+#pragma unroll
+  for (int j = 0; j < T.n; j++) {
+    const int k = T.v[j].k;
+    if (k >= K) continue;
+    const uint32_t v = box[c + hoff(T.v[j].x, T.v[j].y, T.v[j].z)];
+    if (NW == 1) {
+      const uint32_t one = 1u << v;
+      if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
+    } else {
+      uint32_t lo, hi;
+      asm("shl.b32 %0, 1, %1;" : "=r"(lo) : "r"(v));
+      asm("shl.b32 %0, 1, %1;" : "=r"(hi) : "r"(v - 32u));
+      if (SIGN > 0) {
+        h[k][0] += lo;
+        h[k][1] += hi;
+      } else {
+        h[k][0] -= lo;
+        h[k][1] -= hi;
+      }
+    }
+  }
+}
+
+template <int K, int NW, int PL>
+__device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t ru, const int* s_poff,
+                                      const Planes& P, int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc,
+                                      unsigned& same, long long& dsum) {
+  const int dir = (int)__umulhi(rd, 12u);
+  const int sp = s + s_poff[dir];
+  const uint32_t a8 = box[s], b8 = box[sp];
+  if (a8 == b8) {
+    same++;
+    return;
+  }
+  uint32_t h[kMaxShells][2];
+#pragma unroll
+  for (int k = 0; k < kMaxShells; k++) {
+    h[k][0] = 0x80808080u;
+    h[k][1] = 0x80808080u;
+  }
+  gather<K, NW, +1>(box, s, h);
+  gather<K, NW, -1>(box, sp, h);
+  // the s-s' bond is not part of either environment after the swap
+  bccfast::add_one<NW>(h[0], b8, -1);
+  bccfast::add_one<NW>(h[0], a8, +1);
+  bccfast::finish_trial<K, NW, PL>(box, s, sp, a8, b8, h, ru, P, nA, sA, sB, acc, dsum);
+}
+
+__host__ __device__ constexpr size_t smem_bytes(int nA) { return BOX_BYTES + (size_t)(nA + kNB) * 4 + 16 * 4; }
+
+template <int K, int NW, int PL>
+__global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_stat[3];
+  uint8_t* box = smem;
+  int* s_poff = reinterpret_cast<int*>(smem + BOX_BYTES);
+  uint32_t* sA = reinterpret_cast<uint32_t*>(s_poff + 16);
+  uint32_t* sB = sA + D.nA;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int jt = blockIdx.x;
+  const int ntc0 = D.nt[0] / 2, ntc1 = D.nt[1] / 2;
+  const int jx = jt % ntc0, jy = (jt / ntc0) % ntc1, jz = jt / (ntc0 * ntc1);
+  const int ti[3] = {2 * jx + (tc & 1), 2 * jy + ((tc >> 1) & 1), 2 * jz + ((tc >> 2) & 1)};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = D.n[a] / D.nt[a], rem = D.n[a] % D.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+  if (tid < 3) s_stat[tid] = 0;
+  for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
+  for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+  if (tid < 12) {
+    constexpr FTable T = make_fvecs();
+    int o = 0;
+#pragma unroll
+    for (int d = 0; d < 12; d++)
+      if (d == tid) o = hoff(T.v[d].x, T.v[d].y, T.v[d].z);
+    s_poff[tid] = o;
+  }
+
+  // stage tile + 2-cell halo: one box column (cell x) per lane, rows (y, z)
+  // per warp, 8 rows of global loads in flight per lane
+  const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  {
+    constexpr int U = 8;
+    const int rows = ey * ez;
+    const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
+    for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
+      uint32_t v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int row = row0 + u;
+        v[u] = 0;
+        if (row < rows && lane < ex) {
+          const int ys = row % ey, zs = row / ey;
+          const long long cell =
+              ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+          v[u] = D.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(D.sites + 4 * cell)
+                                        : (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int row = row0 + u;
+        if (row < rows && lane < ex) {
+          const int ys = row % ey, zs = row / ey;
+          const int base = hoff(2 * lane, 2 * ys, 2 * zs);
+#pragma unroll
+          for (int b = 0; b < 4; b++) {
+            const uint32_t sp = D.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
+            box[base + boff(b)] = (uint8_t)(sp << 3);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // this thread's link-cell slot
+  const int NQ = D.NQ, L = D.L;
+  const int qx = tid % NQ, qy = (tid / NQ) % NQ, qz = tid / (NQ * NQ);
+  const bool slot = tid < NQ * NQ * NQ;
+  unsigned acc = 0, same = 0;
+  long long dsum = 0;
+  for (int cz = 0; cz < L; cz++)
+    for (int cy = 0; cy < L; cy++)
+      for (int cx = 0; cx < L; cx++) {
+        const int xr = cx + L * qx, yr = cy + L * qy, zr = cz + L * qz;
+        const bool here = slot && xr < ts[0] && yr < ts[1] && zr < ts[2];
+        const int cbase = hoff(2 * (xr + H), 2 * (yr + H), 2 * (zr + H));
+        const unsigned long long cell = ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
+#pragma unroll
+        for (int pr = 0; pr < 2; pr++) {
+          // sublattices 2 pr and 2 pr + 1 share the Philox block of pair cell*2 + pr
+          uint4 rw = make_uint4(0, 0, 0, 0);
+          if (here) {
+            rw = attempt_block(cell * 4 + 2 * pr, D.sweep, D.replica, D.seed_lo, D.seed_hi);
+            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, Q, D.nA,
+                             sA, sB, acc, same, dsum);
+          }
+          __syncthreads();
+          if (here)
+            trial<K, NW, PL>(box, cbase + boff(2 * pr + 1), rw.z, rw.w, s_poff,
+                             Q, D.nA, sA, sB, acc, same, dsum);
+          __syncthreads();
+        }
+      }
+
+  // write back tile + 1-cell partner ring
+  const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
+  for (int row = warp; row < wy * wz; row += nwarp) {
+    const int yw = row % wy, zw = row / wy;
+    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
+    const long long rbase = ((long long)gz * ny + gy) * nx;
+    for (int xw = lane; xw < wx; xw += 32) {
+      const long long cell = rbase + wrap_add(t0[0] - 1, xw, nx);
+      const int base = hoff(2 * (xw + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
+      uint32_t s4[4];
+#pragma unroll
+      for (int b = 0; b < 4; b++) s4[b] = box[base + boff(b)] >> 3;
+      if (D.storage == SMCX_INT8) {
+        *reinterpret_cast<uint32_t*>(D.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
+      } else {
+        *reinterpret_cast<uint16_t*>(D.sites + 2 * cell) =
+            (uint16_t)(s4[0] | (s4[1] << 4) | (s4[2] << 8) | (s4[3] << 12));
+      }
+    }
+  }
+
+  atomicAdd(&s_stat[0], (unsigned long long)acc);
+  atomicAdd(&s_stat[1], (unsigned long long)same);
+  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&D.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 4);
+    atomicAdd(&D.stats[1], s_stat[0]);
+    atomicAdd(&D.stats[2], s_stat[1]);
+    atomicAdd(&D.stats[3], s_stat[2]);
+  }
+}
+
+}  // namespace fccfast
+
+int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
+
+// FCC pair model, M <= 8, K <= 3, |V| < 2^23, per-trial directions, a tiled
+// schedule with tiles of at most 15 cells and link cells of at least 3 (one
+// slot of at most 5^3 per thread of a 128-thread CTA), 16-byte aligned store.
+bool fcc_fast_usable(const smcx_lattice* hd) {
+  const smcx_sched& sc = hd->sched;
+  if (hd->kind != kFCC || hd->M > kMaxSweepM || !hd->have_epi || !hd->Wq.empty()) return false;
+  if (hd->proposal != SMCX_PROPOSAL_SITE || hd->shells.K > 3) return false;
+  if (sc.L < 3 || sc.nt[0] < 2 || sc.nt[1] < 2 || sc.nt[2] < 2) return false;
+  if (halo_cells(hd->shells) != 2 || ring_cells(hd->shells) != 1) return false;
+  if (reinterpret_cast<uintptr_t>(hd->d_sites) % 4 != 0) return false;
+  for (int32_t v : hd->V)
+    if (v >= (1 << 23) || v <= -(1 << 23)) return false;
+  int nq = 0;
+  for (int a = 0; a < 3; a++) {
+    const int tmax = (hd->n[a] + sc.nt[a] - 1) / sc.nt[a];
+    if (tmax > fccfast::TMAX) return false;
+    nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
+  }
+  return nq * nq * nq <= 128;
+}
+
+void sweep_fcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, int n_colours) {
+  bccfast::LatDesc D;
+  memset(&D, 0, sizeof(D));
+  const smcx_sched& sc = hd->sched;
+  D.sites = hd->d_sites;
+  D.thr = hd->d_thr;
+  D.stats = hd->d_stats;
+  int nq = 0;
+  for (int a = 0; a < 3; a++) {
+    D.n[a] = hd->n[a];
+    D.nt[a] = sc.nt[a];
+    nq = std::max(nq, ((hd->n[a] + sc.nt[a] - 1) / sc.nt[a] + sc.L - 1) / sc.L);
+  }
+  D.L = sc.L;
+  D.NQ = nq;
+  D.nA = nA;
+  D.storage = hd->storage;
+  D.replica = hd->replica;
+  D.seed_lo = (uint32_t)seed;
+  D.seed_hi = (uint32_t)(seed >> 32);
+  D.M = hd->M;
+  bccfast::Planes Q;
+  const int K = hd->shells.K;
+  const int PL = build_planes(hd, &Q, K == 3 ? 2 : 3);
+  const int NW = (K == 3 && hd->M <= 4) ? 1 : 2;
+  const size_t smem = fccfast::smem_bytes(nA);
+  const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
+  auto run = [&](auto kern) {
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "fcc sweep smem attribute");
+    const unsigned long long first = hd->sweep_cum;
+    for (int64_t s = 0; s < n_sweeps; s++) {
+      D.sweep = first + (unsigned long long)s;
+      for (int tc = 0; tc < n_colours; tc++) kern<<<grid, 128, smem, hd->stream>>>(D, Q, tc);
+    }
+  };
+  if (K == 3) {
+    if (NW == 1) {
+      if (PL == 2) run(fccfast::k_fcc_tile_sweep<3, 1, 2>);
+      else run(fccfast::k_fcc_tile_sweep<3, 1, 3>);
+    } else {
+      if (PL == 2) run(fccfast::k_fcc_tile_sweep<3, 2, 2>);
+      else run(fccfast::k_fcc_tile_sweep<3, 2, 3>);
+    }
+  } else if (K == 2) {
+    run(fccfast::k_fcc_tile_sweep<2, 2, 3>);
+  } else {
+    run(fccfast::k_fcc_tile_sweep<1, 2, 3>);
+  }
+  check_cuda(cudaGetLastError(), "fcc sweep launch");
+}
+
+}  // namespace smcx
