@@ -1,11 +1,11 @@
 // FCC tile pass specialised for throughput (pair model, M <= 8 species,
-// K <= 3 shells, tiles up to 15 cells, link cells >= 3, one link-cell slot
+// K <= 3 shells, tiles up to 14 cells, link cells >= 3, one link-cell slot
 // per thread).  Same trials, same order of phases, same Philox words and the
 // same integer arithmetic as k_tile_sweep in smcx_sweep.cu: the result is
 // bit-identical; only the data layout and the instruction mix differ.
 //
 //  * FCC sites are the even points (x + y + z even) of the half-unit cubic
-//    grid.  Shared memory stores the box (tile + 2-cell halo, at most 38
+//    grid.  Shared memory stores the box (tile + 2-cell halo, at most 36
 //    half units per axis) with the site at half-unit box position (x, y, z)
 //    in byte (x + y PXF + z PPF) / 2; PXF and PPF are odd, so the numerator
 //    of every site is even and no byte is wasted.  A neighbour along the
@@ -29,11 +29,16 @@ namespace fccfast {
 using bccfast::LatDesc;
 using bccfast::Planes;
 
-constexpr int H = 2;                  // halo cells
-constexpr int TMAX = 15;              // largest tile edge (cells)
-constexpr int EXT = 2 * (TMAX + 2 * H);  // box edge in half units (38)
-constexpr int PXF = EXT + 1;          // 39, odd
-constexpr int PPF = PXF * EXT + 1;    // 1483, odd
+constexpr int H = 2;                     // halo cells
+constexpr int TMAX = 14;                 // largest tile edge (cells)
+constexpr int EXT = 2 * (TMAX + 2 * H);  // box edge in half units (36)
+// Odd pitches (>= EXT and >= EXT * PXF) chosen by simulating the banks of a
+// warp's 32 slot origins (link cell 3, 5^3 slots): every centre-environment
+// load is one wavefront; the partner loads, scattered by the per-lane
+// directions, about 3.1.
+constexpr int PXF = 37;
+constexpr int PPF = 1379;
+static_assert(PXF % 2 == 1 && PPF % 2 == 1 && PXF > EXT - 1 && PPF >= EXT * PXF, "FCC box pitches");
 constexpr int BOXB = ((EXT - 1) + (EXT - 1) * PXF + (EXT - 1) * PPF) / 2 + 1;  // bytes used
 constexpr int BOX_BYTES = (BOXB + 15) / 16 * 16;
 
@@ -95,10 +100,52 @@ __device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[
   }
 }
 
+// dE = G_b - G_a with only the two V rows needed: the byte planes of V_k[p]
+// are read from shared memory (sP [PL][K][8][NW]) at rows a and b, instead
+// of forming G_p for every species slot in registers (8 NW K PL dp4a).  The
+// FCC pass is bound by ALU issue, not by its shared-memory pipe, so the loads
+// are the cheaper side.
+template <int K, int NW, int PL>
+__device__ __forceinline__ void finish_rows(uint8_t* box, int s, int sp, uint32_t a8, uint32_t b8,
+                                            const uint32_t (&h)[kMaxShells][2], uint32_t ru, const uint32_t* sP,
+                                            int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc,
+                                            long long& dsum) {
+  const int a = (int)(a8 >> 3), b = (int)(b8 >> 3);
+  int ga0 = 0, ga1 = 0, ga2 = 0, gb0 = 0, gb1 = 0, gb2 = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+      const int d = (int)(h[k][w] ^ 0x80808080u);
+      const uint32_t* r0 = sP + ((0 * K + k) * 8) * NW + w;
+      ga0 = bccfast::dp4a_su(d, r0[a * NW], ga0);
+      gb0 = bccfast::dp4a_su(d, r0[b * NW], gb0);
+      const uint32_t* r1 = sP + ((1 * K + k) * 8) * NW + w;
+      if (PL == 2) {
+        ga1 = bccfast::dp4a_ss(d, r1[a * NW], ga1);
+        gb1 = bccfast::dp4a_ss(d, r1[b * NW], gb1);
+      } else {
+        ga1 = bccfast::dp4a_su(d, r1[a * NW], ga1);
+        gb1 = bccfast::dp4a_su(d, r1[b * NW], gb1);
+        const uint32_t* r2 = sP + ((2 * K + k) * 8) * NW + w;
+        ga2 = bccfast::dp4a_ss(d, r2[a * NW], ga2);
+        gb2 = bccfast::dp4a_ss(d, r2[b * NW], gb2);
+      }
+    }
+  }
+  const int dE = (gb0 + (gb1 << 8) + (gb2 << 16)) - (ga0 + (ga1 << 8) + (ga2 << 16));
+  if (metropolis_accept(dE, ru, sA, nA, sB)) {
+    box[s] = (uint8_t)b8;
+    box[sp] = (uint8_t)a8;
+    acc++;
+    dsum += dE;
+  }
+}
+
 template <int K, int NW, int PL>
 __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t ru, const int* s_poff,
-                                      const Planes& P, int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc,
-                                      unsigned& same, long long& dsum) {
+                                      const uint32_t* sP, int nA, const uint32_t* sA, const uint32_t* sB,
+                                      unsigned& acc, unsigned& same, long long& dsum) {
   const int dir = (int)__umulhi(rd, 12u);
   const int sp = s + s_poff[dir];
   const uint32_t a8 = box[s], b8 = box[sp];
@@ -117,10 +164,14 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   // the s-s' bond is not part of either environment after the swap
   bccfast::add_one<NW>(h[0], b8, -1);
   bccfast::add_one<NW>(h[0], a8, +1);
-  bccfast::finish_trial<K, NW, PL>(box, s, sp, a8, b8, h, ru, P, nA, sA, sB, acc, dsum);
+  finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
 }
 
-__host__ __device__ constexpr size_t smem_bytes(int nA) { return BOX_BYTES + (size_t)(nA + kNB) * 4 + 16 * 4; }
+// box, partner offsets (16 ints), plane rows (3 x 3 x 8 x 2 words), sA, sB
+constexpr int kPlaneWords = 3 * 3 * 8 * 2;
+__host__ __device__ constexpr size_t smem_bytes(int nA) {
+  return BOX_BYTES + 16 * 4 + kPlaneWords * 4 + (size_t)(nA + kNB) * 4;
+}
 
 template <int K, int NW, int PL>
 __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
@@ -128,7 +179,8 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
   __shared__ unsigned long long s_stat[3];
   uint8_t* box = smem;
   int* s_poff = reinterpret_cast<int*>(smem + BOX_BYTES);
-  uint32_t* sA = reinterpret_cast<uint32_t*>(s_poff + 16);
+  uint32_t* sP = reinterpret_cast<uint32_t*>(s_poff + 16);
+  uint32_t* sA = sP + kPlaneWords;
   uint32_t* sB = sA + D.nA;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -144,6 +196,10 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
     t0[a] = ti[a] * base + min(ti[a], rem);
   }
   if (tid < 3) s_stat[tid] = 0;
+  for (int i = tid; i < PL * K * 8 * NW; i += nth) {
+    const int w = i % NW, p = (i / NW) % 8, k = (i / (NW * 8)) % K, j = i / (NW * 8 * K);
+    sP[i] = Q.P[j][k][p][w];
+  }
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
   if (tid < 12) {
@@ -213,13 +269,13 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
           uint4 rw = make_uint4(0, 0, 0, 0);
           if (here) {
             rw = attempt_block(cell * 4 + 2 * pr, D.sweep, D.replica, D.seed_lo, D.seed_hi);
-            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, Q, D.nA,
+            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, sP, D.nA,
                              sA, sB, acc, same, dsum);
           }
           __syncthreads();
           if (here)
             trial<K, NW, PL>(box, cbase + boff(2 * pr + 1), rw.z, rw.w, s_poff,
-                             Q, D.nA, sA, sB, acc, same, dsum);
+                             sP, D.nA, sA, sB, acc, same, dsum);
           __syncthreads();
         }
       }
@@ -262,7 +318,7 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
 int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
 
 // FCC pair model, M <= 8, K <= 3, |V| < 2^23, per-trial directions, a tiled
-// schedule with tiles of at most 15 cells and link cells of at least 3 (one
+// schedule with tiles of at most 14 cells and link cells of at least 3 (one
 // slot of at most 5^3 per thread of a 128-thread CTA), 16-byte aligned store.
 bool fcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;
