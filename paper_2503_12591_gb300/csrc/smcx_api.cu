@@ -411,7 +411,7 @@ int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* th
       check_cuda(cudaEventCreate(&e1), "event");
       const int Lmin = min_link_cell(h->shells);
       for (int L = Lmin; L <= std::max(Lmin, 5); L++)
-        for (int target : {10, 12, 14, 15, 16, 20})
+        for (int target : {10, 12, 14, 15, 16, 18, 19, 20})
           for (int th : {0, 128, 256}) {
             smcx_sched sc;
             sc.L = L;

@@ -269,6 +269,282 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tile_sweep_qsro(const SweepPar
   }
 }
 
+// ---------------------------------------------------------------------------
+// FCC qSRO sweep on the even-point layout: the FCC sites are the even points
+// of the half-unit grid, stored at byte (x + y QPX + z QPP) / 2 of a box of
+// QEXT half units per axis (tile <= 20 cells + 3-cell halo), so a neighbour
+// along v is at a constant offset from ANY site.  Every same-species count of
+// a union site is then an unrolled run of immediate-offset loads, with no
+// offset table and no sublattice case; the shell of s' seen from a union
+// site is a runtime value, taken through a three-way switch.
+// ---------------------------------------------------------------------------
+namespace qfcc {
+constexpr int H = 3;
+constexpr int TMAX = 20;
+constexpr int QEXT = 2 * (TMAX + 2 * H);  // 52
+constexpr int QPX = QEXT + 1;             // 53, odd
+constexpr int QPP = QPX * QEXT + 1;       // 2757, odd
+constexpr int BOXB = ((QEXT - 1) + (QEXT - 1) * QPX + (QEXT - 1) * QPP) / 2 + 1;
+constexpr int BOX_BYTES = (BOXB + 15) / 16 * 16;
+__host__ __device__ constexpr int hoff(int x, int y, int z) { return (x + y * QPX + z * QPP) / 2; }
+__host__ __device__ constexpr int boff(int b) {
+  return hoff((b == 1 || b == 2) ? 1 : 0, (b == 1 || b == 3) ? 1 : 0, (b == 2 || b == 3) ? 1 : 0);
+}
+struct QVec {
+  int x, y, z, k;
+};
+struct QTable {
+  QVec v[42];
+  int n;
+  int start[4];
+};
+__host__ __device__ constexpr QTable make_qvecs() {
+  QTable t{};
+  t.n = 0;
+  for (int k = 0; k < 3; k++) {
+    t.start[k] = t.n;
+    for (int x = -2; x <= 2; x++)
+      for (int y = -2; y <= 2; y++)
+        for (int z = -2; z <= 2; z++) {
+          if ((x + y + z) & 1) continue;
+          if (x * x + y * y + z * z == 2 * (k + 1)) {
+            t.v[t.n] = QVec{x, y, z, k};
+            t.n++;
+          }
+        }
+  }
+  t.start[3] = t.n;
+  return t;
+}
+// same-species (c) neighbours of box site t in shell KS
+template <int KS>
+__device__ __forceinline__ int count_shell(const uint8_t* box, int t, int c) {
+  constexpr QTable T = make_qvecs();
+  int n = 0;
+#pragma unroll
+  for (int j = T.start[KS]; j < T.start[KS + 1]; j++) n += (box[t + hoff(T.v[j].x, T.v[j].y, T.v[j].z)] == c);
+  return n;
+}
+__device__ __forceinline__ int count_rt(const uint8_t* box, int t, int k, int c) {
+  switch (k) {
+    case 0: return count_shell<0>(box, t, c);
+    case 1: return count_shell<1>(box, t, c);
+    default: return count_shell<2>(box, t, c);
+  }
+}
+}  // namespace qfcc
+
+template <int K>
+__global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const QsroTables Q) {
+  using namespace qfcc;
+  constexpr QTable T = make_qvecs();
+  constexpr int NV = vec_count(kFCC, K);
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long s_stat[3];
+  __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
+  __shared__ signed char s_k2[12 * NV], s_ins[12 * NV];
+  __shared__ int s_poff[12];
+
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int M = P.M, KM = K * P.M, MM = P.M * P.M;
+  const int nW = MM * KM + MM;
+  uint8_t* box = smem;
+  int32_t* s_w = reinterpret_cast<int32_t*>(smem + BOX_BYTES);
+
+  int bid = blockIdx.x;
+  const int jx = bid % P.ntc[0];
+  bid /= P.ntc[0];
+  const int jy = bid % P.ntc[1];
+  const int jz = bid / P.ntc[1];
+  const int ti[3] = {2 * jx + (P.tc & 1), 2 * jy + ((P.tc >> 1) & 1), 2 * jz + ((P.tc >> 2) & 1)};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = P.n[a] / P.nt[a], rem = P.n[a] % P.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+  if (tid < 3) s_stat[tid] = 0;
+  for (int i = tid; i < nW; i += nth) s_w[i] = P.wtab[i];
+  for (int i = tid; i < KM; i += nth) s_wq[i] = Q.W[i];
+  for (int i = tid; i < 12 * NV; i += nth) {
+    s_k2[i] = Q.k2[i / NV][i % NV];
+    s_ins[i] = Q.in_s[i / NV][i % NV];
+  }
+  if (tid < 12) {
+    int o = 0;
+#pragma unroll
+    for (int d = 0; d < 12; d++)
+      if (d == tid) o = hoff(T.v[d].x, T.v[d].y, T.v[d].z);
+    s_poff[tid] = o;
+  }
+
+  // stage tile + 3-cell halo, 8 rows of loads in flight per lane
+  const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  {
+    constexpr int U = 8;
+    const int rows = ey * ez;
+    const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
+    for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
+      uint32_t v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int row = row0 + u;
+        v[u] = 0;
+        if (row < rows && lane < ex) {
+          const int ys = row % ey, zs = row / ey;
+          const long long cell =
+              ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+          v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
+                                        : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int row = row0 + u;
+        if (row < rows && lane < ex) {
+          const int ys = row % ey, zs = row / ey;
+          const int base = hoff(2 * lane, 2 * ys, 2 * zs);
+#pragma unroll
+          for (int b = 0; b < 4; b++)
+            box[base + boff(b)] =
+                (uint8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  unsigned long long acc = 0, same = 0;
+  long long dsum = 0;
+  const int L = P.L;
+  const int NQ = (max(ts[0], max(ts[1], ts[2])) + L - 1) / L;
+  const int qx = tid % NQ, qy = (tid / NQ) % NQ, qz = tid / (NQ * NQ);
+  const bool slot = tid < NQ * NQ * NQ;
+  for (int cz = 0; cz < L; cz++)
+    for (int cy = 0; cy < L; cy++)
+      for (int cx = 0; cx < L; cx++) {
+        const int xr = cx + L * qx, yr = cy + L * qy, zr = cz + L * qz;
+        const bool here = slot && xr < ts[0] && yr < ts[1] && zr < ts[2];
+        const int cbase = hoff(2 * (xr + H), 2 * (yr + H), 2 * (zr + H));
+        const unsigned long long cell = ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
+        uint4 rw = make_uint4(0, 0, 0, 0);
+        for (int b = 0; b < 4; b++) {
+          if (here) {
+            if ((b & 1) == 0) rw = attempt_block(cell * 4 + b, P.sweep, P.replica, P.seed_lo, P.seed_hi);
+            const uint32_t rd = (b & 1) ? rw.z : rw.x;
+            const uint32_t ru = (b & 1) ? rw.w : rw.y;
+            const int s = cbase + boff(b);
+            const int dir = (int)__umulhi(rd, 12u);
+            const int po = s_poff[dir];
+            const int sp = s + po;
+            const int sa = box[s], sb = box[sp];
+            if (sa == sb) {
+              same++;
+            } else {
+              const int32_t* W = s_w + (sa * M + sb) * KM;
+              int dE = s_w[MM * KM + sa * M + sb];
+              int na_s[K], nb_s[K], na_p[K], nb_p[K];
+#pragma unroll
+              for (int k = 0; k < K; k++) na_s[k] = nb_s[k] = na_p[k] = nb_p[k] = 0;
+#pragma unroll
+              for (int j = 0; j < NV; j++) {
+                const int k = T.v[j].k, o = hoff(T.v[j].x, T.v[j].y, T.v[j].z);
+                const int c = box[s + o];
+                dE += W[k * M + c];
+                if (o != po) {
+                  na_s[k] += (c == sa);
+                  nb_s[k] += (c == sb);
+                }
+                const int cp = box[sp + o];
+                dE -= W[k * M + cp];
+                if (o != -po) {
+                  na_p[k] += (cp == sa);
+                  nb_p[k] += (cp == sb);
+                }
+              }
+#pragma unroll
+              for (int k = 0; k < K; k++)
+                dE += s_wq[k * M + sb] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) +
+                      s_wq[k * M + sa] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
+              // sites of the environment of s: shell k (compile time) towards s,
+              // shell k2 (this direction's table) towards s'
+#pragma unroll
+              for (int j = 0; j < NV; j++) {
+                const int k = T.v[j].k;
+                const int t = s + hoff(T.v[j].x, T.v[j].y, T.v[j].z);
+                const int c = box[t];
+                if (c != sa && c != sb) continue;
+                const int k2 = s_k2[dir * NV + j];
+                if (k2 == -2 || k2 == k) continue;
+                const int d1 = (c == sb) ? 1 : -1;
+                int n1;
+                if (k == 0) n1 = count_shell<0>(box, t, c);
+                else if (k == 1) n1 = count_shell<1>(box, t, c);
+                else n1 = count_shell<2>(box, t, c);
+                dE += s_wq[k * M + c] * (2 * d1 * n1 + 1);
+                if (k2 >= 0) dE += s_wq[k2 * M + c] * (-2 * d1 * count_rt(box, t, k2, c) + 1);
+              }
+              // sites that see only s'
+#pragma unroll
+              for (int j = 0; j < NV; j++) {
+                if (s_ins[dir * NV + j]) continue;
+                const int k = T.v[j].k;
+                const int t = sp + hoff(T.v[j].x, T.v[j].y, T.v[j].z);
+                const int c = box[t];
+                if (c != sa && c != sb) continue;
+                const int d2 = (c == sb) ? -1 : 1;
+                int n2;
+                if (k == 0) n2 = count_shell<0>(box, t, c);
+                else if (k == 1) n2 = count_shell<1>(box, t, c);
+                else n2 = count_shell<2>(box, t, c);
+                dE += s_wq[k * M + c] * (2 * d2 * n2 + 1);
+              }
+              if (metropolis_accept(dE, ru, P.thr, P.nA, P.thr + kNA)) {
+                box[s] = (uint8_t)sb;
+                box[sp] = (uint8_t)sa;
+                acc++;
+                dsum += dE;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+
+  // write back tile + 1-cell partner ring
+  const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
+  for (int row = warp; row < wy * wz; row += nwarp) {
+    const int yw = row % wy, zw = row / wy;
+    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
+    const long long rbase = ((long long)gz * ny + gy) * nx;
+    for (int xw = lane; xw < wx; xw += 32) {
+      const long long cell = rbase + wrap_add(t0[0] - 1, xw, nx);
+      const int base = hoff(2 * (xw + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
+      uint32_t s4[4];
+#pragma unroll
+      for (int b = 0; b < 4; b++) s4[b] = box[base + boff(b)];
+      if (P.storage == SMCX_INT8)
+        *reinterpret_cast<uint32_t*>(P.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
+      else
+        *reinterpret_cast<uint16_t*>(P.sites + 2 * cell) =
+            (uint16_t)(s4[0] | (s4[1] << 4) | (s4[2] << 8) | (s4[3] << 12));
+    }
+  }
+  atomicAdd(&s_stat[0], acc);
+  atomicAdd(&s_stat[1], same);
+  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&P.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 4);
+    atomicAdd(&P.stats[1], s_stat[0]);
+    atomicAdd(&P.stats[2], s_stat[1]);
+    atomicAdd(&P.stats[3], s_stat[2]);
+  }
+}
+
 // sum_i sum_k W[k][s_i] n_k(i)^2 added to *E (global-memory gathers).
 template <int KIND, int K>
 __global__ void __launch_bounds__(256) k_qsro_energy(const SweepParams P, const QsroTables Q, long long* E) {
@@ -446,6 +722,32 @@ void sweep_qsro_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps
   fill_tile_offsets(hd, P);
   const QsroTables T = make_tables(hd);
   const int K = hd->shells.K;
+  // FCC with tiles of at most 20 cells, link cells >= 4, 5^3 slots at most,
+  // a 4-byte aligned store: the even-point kernel
+  const int tm = std::max(tmax[0], std::max(tmax[1], tmax[2]));
+  const int nq = (tm + sc.L - 1) / sc.L;
+  if (hd->kind == kFCC && K >= 2 && tm <= qfcc::TMAX && nq * nq * nq <= 128 &&
+      reinterpret_cast<uintptr_t>(P.sites) % 4 == 0) {
+    const int nW = P.M * P.M * K * P.M + P.M * P.M;
+    const size_t smem = qfcc::BOX_BYTES + (size_t)nW * 4;
+    auto run = [&](auto kern) {
+      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                 "qSRO FCC smem attribute");
+      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
+                 "qSRO FCC carveout");
+      for (int64_t sw = 0; sw < n_sweeps; sw++) {
+        P.sweep = hd->sweep_cum + (uint64_t)sw;
+        for (int tc = 0; tc < n_colours; tc++) {
+          P.tc = tc;
+          kern<<<P.ntc[0] * P.ntc[1] * P.ntc[2], 128, smem, hd->stream>>>(P, T);
+        }
+      }
+      check_cuda(cudaGetLastError(), "qSRO FCC sweep launch");
+    };
+    if (K == 2) run(k_qsro_fcc<2>);
+    else run(k_qsro_fcc<3>);
+    return;
+  }
   if (hd->kind == kBCC) {
     switch (K) {
       case 1: launch_qsro<kBCC, 1>(hd, P, T, n_sweeps, n_colours); break;

@@ -29,6 +29,11 @@ CASES = [
     (smcx.FCC, 3, (12, 8, 8), 4, smcx.INT8, (4, (4, 2, 2)), 1000.0, 3),
     (smcx.FCC, 3, (16, 12, 14), 5, smcx.PACKED4, None, 1200.0, 2),
     (smcx.FCC, 2, (10, 12, 8), 3, smcx.PACKED4, (4, (2, 2, 2)), 800.0, 3),
+    # tiles of 20/19/18 cells (the largest the even-point FCC kernel takes,
+    # 5^3 trial slots) and tiles of 22 cells (the generic kernel)
+    (smcx.FCC, 3, (40, 38, 36), 4, smcx.INT8, (4, (2, 2, 2)), 1000.0, 1),
+    (smcx.FCC, 2, (40, 38, 36), 5, smcx.PACKED4, (5, (2, 2, 2)), 900.0, 1),
+    (smcx.FCC, 3, (44, 8, 8), 4, smcx.PACKED4, (4, (2, 2, 2)), 1000.0, 2),
     (smcx.BCC, 2, (12, 12, 12), 4, smcx.INT8, (4, (4, 4, 4)), 1000.0, 3),
     (smcx.BCC, 4, (20, 16, 16), 4, smcx.PACKED4, None, 1500.0, 2),
 ]
