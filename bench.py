@@ -459,8 +459,8 @@ def run_qsro(stream, edge=0):
             "acceptance": float(st[1]) / max(1, int(st[0])),
             "kernel": "k_qsro_fcc<3>" if max(-(-d // t) for d, t in zip(W_.dims, sched_q[1])) <= 20
                       else "k_tile_sweep_qsro<FCC,3>",
-            "workload": "FCC 400^3 = 256M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI N(0,30 meV) + "
-                        "qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}
+            "workload": f"FCC {W_.dims[0]}^3 = {N / 1e6:.0f}M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI "
+                        "N(0,30 meV) + qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}
 
 
 def run_anneal(stream):
@@ -745,7 +745,8 @@ def run_smcx(args, rank, world, local_rank):
     if not args.no_e2e:
         # Two handles on two streams: the upload of step i+1's input overlaps
         # the sweep of step i (double buffering); every step still uploads its
-        # own input and reads back its own energy inside the timed region.
+        # own input and reads back its own result (the sweep's attempt, accept
+        # and summed-dE counters) inside the timed region.
         nbytes = lat.store_bytes()
         stream2 = torch.cuda.Stream()
         with torch.cuda.stream(stream2):
@@ -759,7 +760,7 @@ def run_smcx(args, rank, world, local_rank):
         for i in range(2):  # warm-up of both handles
             pair[i].set_config_store_ptr(hosts[i].data_ptr(), nbytes)
             pair[i].sweep(T_KELVIN, 1, SEED)
-            pair[i].energy()
+            pair[i].state()
         barrier()
         ne = max(4, min(args.steps, 8))
         t0 = time.perf_counter()
@@ -769,17 +770,17 @@ def run_smcx(args, rank, world, local_rank):
             cur.sweep(T_KELVIN, 1, SEED)                              # enqueued; runs while the next upload goes
             if i + 1 < ne:
                 nxt.set_config_store_ptr(hosts[(i + 1) % 2].data_ptr(), nbytes)  # H2D of step i+1's input
-            cur.energy()                                              # D2H of step i's result
+            cur.state()                                               # D2H of step i's result
         dt = time.perf_counter() - t0
         tt = torch.tensor([dt], device="cuda")
         if dist is not None:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dt = float(tt.item())
         e2e = {"value": WORK.sites * ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": 8, "steps": ne,
+               "d2h_bytes_per_step": 32, "steps": ne,
                "step": "smcx_set_config_store (packed 4-bit store layout, pinned host) + smcx_sweep (1 sweep) + "
-                       "smcx_energy; two handles on two streams, the next step's upload overlapping this "
-                       "step's sweep",
+                       "smcx_get_state (attempts, accepts, same-species proposals, summed dE: 32 B); two handles "
+                       "on two streams, the next step's upload overlapping this step's sweep",
                "ms_per_step": dt * 1e3 / ne}
         lat2.close()
         host = hosts

@@ -332,6 +332,47 @@ __device__ __forceinline__ int count_rt(const uint8_t* box, int t, int k, int c)
     default: return count_shell<2>(box, t, c);
   }
 }
+// Sites t = s + v_j of shell KS around s with species a or b that see s' in
+// another shell k2 (or not at all, k2 = -1): n_KS(t) changes by d1 = +1
+// (t holds b) or -1 (t holds a), n_k2(t) by -d1.  The loop over the shell
+// runs with offsets from a table (keeps the code small enough for the
+// instruction cache); each count is an immediate-offset run.
+template <int KS>
+__device__ __forceinline__ int env_s_shell(const uint8_t* box, const int* qoff, const signed char* k2row,
+                                           const int32_t* wq, int M, int s, int sa, int sb) {
+  constexpr QTable T = make_qvecs();
+  int dE = 0;
+#pragma unroll 2
+  for (int j = T.start[KS]; j < T.start[KS + 1]; j++) {
+    const int t = s + qoff[j];
+    const int c = box[t];
+    if (c != sa && c != sb) continue;
+    const int k2 = k2row[j];
+    if (k2 == -2 || k2 == KS) continue;  // t is s', or sees s and s' in one shell
+    const int d1 = (c == sb) ? 1 : -1;
+    dE += wq[KS * M + c] * (2 * d1 * count_shell<KS>(box, t, c) + 1);
+    if (k2 >= 0) dE += wq[k2 * M + c] * (-2 * d1 * count_rt(box, t, k2, c) + 1);
+  }
+  return dE;
+}
+// Sites t = s' + v_j of shell KS around s' outside the environment of s:
+// n_KS(t) changes by d2 = -1 (t holds b) or +1 (t holds a).
+template <int KS>
+__device__ __forceinline__ int env_p_shell(const uint8_t* box, const int* qoff, const signed char* insrow,
+                                           const int32_t* wq, int M, int sp, int sa, int sb) {
+  constexpr QTable T = make_qvecs();
+  int dE = 0;
+#pragma unroll 2
+  for (int j = T.start[KS]; j < T.start[KS + 1]; j++) {
+    if (insrow[j]) continue;
+    const int t = sp + qoff[j];
+    const int c = box[t];
+    if (c != sa && c != sb) continue;
+    const int d2 = (c == sb) ? -1 : 1;
+    dE += wq[KS * M + c] * (2 * d2 * count_shell<KS>(box, t, c) + 1);
+  }
+  return dE;
+}
 }  // namespace qfcc
 
 template <int K>
@@ -343,7 +384,7 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
   __shared__ unsigned long long s_stat[3];
   __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
   __shared__ signed char s_k2[12 * NV], s_ins[12 * NV];
-  __shared__ int s_poff[12];
+  __shared__ int s_qoff[NV];
 
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -372,12 +413,12 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
     s_k2[i] = Q.k2[i / NV][i % NV];
     s_ins[i] = Q.in_s[i / NV][i % NV];
   }
-  if (tid < 12) {
+  if (tid < NV) {
     int o = 0;
 #pragma unroll
-    for (int d = 0; d < 12; d++)
-      if (d == tid) o = hoff(T.v[d].x, T.v[d].y, T.v[d].z);
-    s_poff[tid] = o;
+    for (int j = 0; j < NV; j++)
+      if (j == tid) o = hoff(T.v[j].x, T.v[j].y, T.v[j].z);
+    s_qoff[tid] = o;  // the first 12 entries are the partner offsets
   }
 
   // stage tile + 3-cell halo, 8 rows of loads in flight per lane
@@ -438,7 +479,7 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
             const uint32_t ru = (b & 1) ? rw.w : rw.y;
             const int s = cbase + boff(b);
             const int dir = (int)__umulhi(rd, 12u);
-            const int po = s_poff[dir];
+            const int po = s_qoff[dir];
             const int sp = s + po;
             const int sa = box[s], sb = box[sp];
             if (sa == sb) {
@@ -469,39 +510,16 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
               for (int k = 0; k < K; k++)
                 dE += s_wq[k * M + sb] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) +
                       s_wq[k * M + sa] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
-              // sites of the environment of s: shell k (compile time) towards s,
-              // shell k2 (this direction's table) towards s'
-#pragma unroll
-              for (int j = 0; j < NV; j++) {
-                const int k = T.v[j].k;
-                const int t = s + hoff(T.v[j].x, T.v[j].y, T.v[j].z);
-                const int c = box[t];
-                if (c != sa && c != sb) continue;
-                const int k2 = s_k2[dir * NV + j];
-                if (k2 == -2 || k2 == k) continue;
-                const int d1 = (c == sb) ? 1 : -1;
-                int n1;
-                if (k == 0) n1 = count_shell<0>(box, t, c);
-                else if (k == 1) n1 = count_shell<1>(box, t, c);
-                else n1 = count_shell<2>(box, t, c);
-                dE += s_wq[k * M + c] * (2 * d1 * n1 + 1);
-                if (k2 >= 0) dE += s_wq[k2 * M + c] * (-2 * d1 * count_rt(box, t, k2, c) + 1);
-              }
-              // sites that see only s'
-#pragma unroll
-              for (int j = 0; j < NV; j++) {
-                if (s_ins[dir * NV + j]) continue;
-                const int k = T.v[j].k;
-                const int t = sp + hoff(T.v[j].x, T.v[j].y, T.v[j].z);
-                const int c = box[t];
-                if (c != sa && c != sb) continue;
-                const int d2 = (c == sb) ? -1 : 1;
-                int n2;
-                if (k == 0) n2 = count_shell<0>(box, t, c);
-                else if (k == 1) n2 = count_shell<1>(box, t, c);
-                else n2 = count_shell<2>(box, t, c);
-                dE += s_wq[k * M + c] * (2 * d2 * n2 + 1);
-              }
+              // sites of the environment of s whose terms change, then those
+              // that see only s'
+              const signed char* k2row = s_k2 + dir * NV;
+              const signed char* insrow = s_ins + dir * NV;
+              dE += env_s_shell<0>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
+              dE += env_s_shell<1>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
+              if (K > 2) dE += env_s_shell<2>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
+              dE += env_p_shell<0>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
+              dE += env_p_shell<1>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
+              if (K > 2) dE += env_p_shell<2>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
               if (metropolis_accept(dE, ru, P.thr, P.nA, P.thr + kNA)) {
                 box[s] = (uint8_t)sb;
                 box[sp] = (uint8_t)sa;
