@@ -492,6 +492,9 @@ def run_anneal(stream):
     return {"value": N * n_sw / dt, "unit": UNIT, "seconds": dt, "sweeps": n_sw, "temperatures": len(temps),
             "cv_per_site_max": cv[k], "cv_peak_T": steps[k].T,
             "cv_per_site": [round(c, 4) for c in cv], "acceptance_last_T": steps[-1].accept_rate,
+            "note": "a throughput measurement of the driver: 20 + 40 sweeps per temperature are far too few for "
+                    "equilibrium (the paper discards 4e5-1.5e6 sweeps per temperature), so these C_V values "
+                    "include the relaxation drift after each temperature step and are not physical",
             "workload": "BCC 320^3 = 65,536,000 sites packed 4-bit, 4 species, 4-shell EPI N(0,20 meV); "
                         "2000 -> 1000 K in 50 K steps, 20 discarded + 40 recorded sweeps per temperature; "
                         "host wall time including the per-sweep exact energies (smcx_sweep_energies)"}
