@@ -34,6 +34,8 @@ CASES = [
     (smcx.FCC, 3, (40, 38, 36), 4, smcx.INT8, (4, (2, 2, 2)), 1000.0, 1),
     (smcx.FCC, 2, (40, 38, 36), 5, smcx.PACKED4, (5, (2, 2, 2)), 900.0, 1),
     (smcx.FCC, 3, (44, 8, 8), 4, smcx.PACKED4, (4, (2, 2, 2)), 1000.0, 2),
+    # 8 species: the largest pair and quadratic tables
+    (smcx.FCC, 3, (12, 16, 8), 8, smcx.INT8, (4, (2, 2, 2)), 1100.0, 2),
     (smcx.BCC, 2, (12, 12, 12), 4, smcx.INT8, (4, (4, 4, 4)), 1000.0, 3),
     (smcx.BCC, 4, (20, 16, 16), 4, smcx.PACKED4, None, 1500.0, 2),
 ]
