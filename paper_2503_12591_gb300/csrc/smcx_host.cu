@@ -139,7 +139,7 @@ std::string schedule_problem(const Shells& s, const int n[3], const smcx_sched& 
   return "";
 }
 
-// Library choice: link cell of 4 (BCC) or the minimum size (FCC); tiles of at most 20 cells (14 for the FCC pair model)
+// Library choice: link cell of 4 (BCC) or the minimum size (FCC); tiles of at most 20 cells (15 for the FCC pair model)
 // (the sweep kernel stages (tile + 2 halo)^3 cells in shared memory).  When
 // the lattice is too small to tile, the paper's link-cell schedule with the
 // smallest L that divides every edge; L = 0 when neither exists.
@@ -148,8 +148,8 @@ smcx_sched choose_schedule(const Shells& s, const int n[3]) {
   // BCC: L = 4 gives 5^3 = 125 link-cell slots per 20-cell tile (one 128-thread
   // CTA); measured faster than L = 3 on GB300.  FCC keeps the smallest valid L.
   sc.L = s.kind == kBCC ? std::max(min_link_cell(s), 4) : std::max(min_link_cell(s), 3);
-  // FCC pair model: tiles of at most 14 cells fit the FCC tile kernel's box
-  const int target = (s.kind == kFCC && s.model == 0) ? 14 : 20;
+  // FCC pair model: tiles of at most 15 cells fit the FCC tile kernel's box
+  const int target = (s.kind == kFCC && s.model == 0) ? 15 : 20;
   bool ok = true;
   for (int a = 0; a < 3; a++) {
     int nt = std::max(2, (n[a] + target - 1) / target);  // tiles of at most `target` cells

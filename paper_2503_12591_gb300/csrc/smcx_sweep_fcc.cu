@@ -1,11 +1,11 @@
 // FCC tile pass specialised for throughput (pair model, M <= 8 species,
-// K <= 3 shells, tiles up to 14 cells, link cells >= 3, one link-cell slot
+// K <= 3 shells, tiles up to 15 cells, link cells >= 3, one link-cell slot
 // per thread).  Same trials, same order of phases, same Philox words and the
 // same integer arithmetic as k_tile_sweep in smcx_sweep.cu: the result is
 // bit-identical; only the data layout and the instruction mix differ.
 //
 //  * FCC sites are the even points (x + y + z even) of the half-unit cubic
-//    grid.  Shared memory stores the box (tile + 2-cell halo, at most 36
+//    grid.  Shared memory stores the box (tile + 2-cell halo, at most 38
 //    half units per axis) with the site at half-unit box position (x, y, z)
 //    in byte (x + y PXF + z PPF) / 2; PXF and PPF are odd, so the numerator
 //    of every site is even and no byte is wasted.  A neighbour along the
@@ -30,14 +30,15 @@ using bccfast::LatDesc;
 using bccfast::Planes;
 
 constexpr int H = 2;                     // halo cells
-constexpr int TMAX = 14;                 // largest tile edge (cells)
-constexpr int EXT = 2 * (TMAX + 2 * H);  // box edge in half units (36)
+constexpr int TMAX = 15;                 // largest tile edge (cells)
+constexpr int EXT = 2 * (TMAX + 2 * H);  // box edge in half units (38)
 // Odd pitches (>= EXT and >= EXT * PXF) chosen by simulating the banks of a
 // warp's 32 slot origins (link cell 3, 5^3 slots): every centre-environment
 // load is one wavefront; the partner loads, scattered by the per-lane
-// directions, about 3.1.
-constexpr int PXF = 37;
-constexpr int PPF = 1379;
+// directions, are not.  No odd row pitch from 39 to 47 has such a plane
+// pitch within 3000 bytes of the minimum; 49 / 1867 is the smallest box.
+constexpr int PXF = 49;
+constexpr int PPF = 1867;
 static_assert(PXF % 2 == 1 && PPF % 2 == 1 && PXF > EXT - 1 && PPF >= EXT * PXF, "FCC box pitches");
 constexpr int BOXB = ((EXT - 1) + (EXT - 1) * PXF + (EXT - 1) * PPF) / 2 + 1;  // bytes used
 constexpr int BOX_BYTES = (BOXB + 15) / 16 * 16;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
 int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
 
 // FCC pair model, M <= 8, K <= 3, |V| < 2^23, per-trial directions, a tiled
-// schedule with tiles of at most 14 cells and link cells of at least 3 (one
+// schedule with tiles of at most 15 cells and link cells of at least 3 (one
 // slot of at most 5^3 per thread of a 128-thread CTA), 16-byte aligned store.
 bool fcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;

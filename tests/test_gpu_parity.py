@@ -81,6 +81,8 @@ SWEEP_CASES = [
     (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 5),
     (smcx.FCC, 3, (9, 10, 11), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.INT8, (3, (2, 4, 2)), 1200.0, 4),
     (smcx.FCC, 3, (9, 9, 9), 4, [0.25] * 4, smcx.PACKED4, (3, (1, 1, 1)), 1000.0, 4),      # link-cell
+    # tiles of 15/14-15/14 cells: the largest box of the FCC tile kernel
+    (smcx.FCC, 3, (30, 29, 28), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (2, 2, 2)), 1200.0, 3),
 ]
 
 
