@@ -83,7 +83,7 @@ __device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[
     const int k = T.v[j].k;
     if (k >= K) continue;
     const uint32_t v = box[c + hoff(T.v[j].x, T.v[j].y, T.v[j].z)];
-    if (NW == 1) {
+    if (NW <= 1) {
       const uint32_t one = 1u << v;
       if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
     } else {
@@ -143,10 +143,47 @@ __device__ __forceinline__ void finish_rows(uint8_t* box, int s, int sp, uint32_
   }
 }
 
+// Six-bit counters (NW = 0, M <= 5): the box holds 6 sigma, each neighbour
+// adds 1 << (6 sigma) to one word per shell (fields biased by 32; a count
+// difference stays within +-24, so no field borrows from the next), and dE =
+// sum_k sum_c (V_k[b][c] - V_k[a][c]) (field_kc - 32) from one row of the
+// (a, b) table: K*5 differences and the bias term.  Rows sit 17 words apart
+// in shared memory, so the lanes of a warp, whatever their (a, b), read
+// distinct banks or the same word: every word load is one wavefront (16-byte
+// loads of 16-word rows cost four or more).  Half the counter instructions
+// of two byte-counter words.  The sum wraps modulo 2^32 like the int32 dE it
+// ends as.
+constexpr uint32_t kBias6 = 0x20820820u;  // 32 in each of the five 6-bit fields
+struct Rows6 {
+  int32_t r[25][16];  // r[a * 5 + b][k * 5 + c] = V_k[b][c] - V_k[a][c]; [15] = -32 sum
+};
+constexpr int kRowStride = 17;  // words between rows in shared memory
+__device__ __forceinline__ int species6(uint32_t v6) { return (int)((v6 * 43u) >> 8); }  // v6 / 6, v6 <= 24
+
+template <int K>
+__device__ __forceinline__ void finish_six(uint8_t* box, int s, int sp, uint32_t a6, uint32_t b6,
+                                           const uint32_t (&h)[kMaxShells][2], uint32_t ru, const int32_t* sR,
+                                           int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc,
+                                           long long& dsum) {
+  const int32_t* row = sR + (species6(a6) * 5 + species6(b6)) * kRowStride;
+  uint32_t e = (uint32_t)row[15];
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int c = 0; c < 5; c++) e += (uint32_t)row[k * 5 + c] * ((h[k][0] >> (6 * c)) & 63u);
+  const int dE = (int)e;
+  if (metropolis_accept(dE, ru, sA, nA, sB)) {
+    box[s] = (uint8_t)b6;
+    box[sp] = (uint8_t)a6;
+    acc++;
+    dsum += dE;
+  }
+}
+
 template <int K, int NW, int PL>
 __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t ru, const int* s_poff,
-                                      const uint32_t* sP, int nA, const uint32_t* sA, const uint32_t* sB,
-                                      unsigned& acc, unsigned& same, long long& dsum) {
+                                      const uint32_t* sP, const int32_t* sR, int nA, const uint32_t* sA,
+                                      const uint32_t* sB, unsigned& acc, unsigned& same, long long& dsum) {
   const int dir = (int)__umulhi(rd, 12u);
   const int sp = s + s_poff[dir];
   const uint32_t a8 = box[s], b8 = box[sp];
@@ -157,30 +194,36 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   uint32_t h[kMaxShells][2];
 #pragma unroll
   for (int k = 0; k < kMaxShells; k++) {
-    h[k][0] = 0x80808080u;
+    h[k][0] = NW == 0 ? kBias6 : 0x80808080u;
     h[k][1] = 0x80808080u;
   }
   gather<K, NW, +1>(box, s, h);
   gather<K, NW, -1>(box, sp, h);
   // the s-s' bond is not part of either environment after the swap
-  bccfast::add_one<NW>(h[0], b8, -1);
-  bccfast::add_one<NW>(h[0], a8, +1);
-  finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
+  bccfast::add_one<NW == 0 ? 1 : NW>(h[0], b8, -1);
+  bccfast::add_one<NW == 0 ? 1 : NW>(h[0], a8, +1);
+  if constexpr (NW == 0)
+    finish_six<K>(box, s, sp, a8, b8, h, ru, sR, nA, sA, sB, acc, dsum);
+  else
+    finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
 }
 
-// box, partner offsets (16 ints), plane rows (3 x 3 x 8 x 2 words), sA, sB
+// box, partner offsets (16 ints), six-bit rows (25 x 17 words), plane rows
+// (3 x 3 x 8 x 2 words), sA, sB
 constexpr int kPlaneWords = 3 * 3 * 8 * 2;
+constexpr int kRowWords = 25 * 17;
 __host__ __device__ constexpr size_t smem_bytes(int nA) {
-  return BOX_BYTES + 16 * 4 + kPlaneWords * 4 + (size_t)(nA + kNB) * 4;
+  return BOX_BYTES + 16 * 4 + kRowWords * 4 + kPlaneWords * 4 + (size_t)(nA + kNB) * 4;
 }
 
 template <int K, int NW, int PL>
-__global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
+__global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, const Rows6 R, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   uint8_t* box = smem;
   int* s_poff = reinterpret_cast<int*>(smem + BOX_BYTES);
-  uint32_t* sP = reinterpret_cast<uint32_t*>(s_poff + 16);
+  int32_t* sR = s_poff + 16;
+  uint32_t* sP = reinterpret_cast<uint32_t*>(sR + kRowWords);
   uint32_t* sA = sP + kPlaneWords;
   uint32_t* sB = sA + D.nA;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -197,9 +240,13 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
     t0[a] = ti[a] * base + min(ti[a], rem);
   }
   if (tid < 3) s_stat[tid] = 0;
-  for (int i = tid; i < PL * K * 8 * NW; i += nth) {
-    const int w = i % NW, p = (i / NW) % 8, k = (i / (NW * 8)) % K, j = i / (NW * 8 * K);
-    sP[i] = Q.P[j][k][p][w];
+  if constexpr (NW > 0) {
+    for (int i = tid; i < PL * K * 8 * NW; i += nth) {
+      const int w = i % NW, p = (i / NW) % 8, k = (i / (NW * 8)) % K, j = i / (NW * 8 * K);
+      sP[i] = Q.P[j][k][p][w];
+    }
+  } else {
+    for (int i = tid; i < 25 * 16; i += nth) sR[(i / 16) * kRowStride + i % 16] = R.r[i / 16][i % 16];
   }
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
@@ -243,7 +290,7 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
 #pragma unroll
           for (int b = 0; b < 4; b++) {
             const uint32_t sp = D.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
-            box[base + boff(b)] = (uint8_t)(sp << 3);
+            box[base + boff(b)] = (uint8_t)(NW == 0 ? sp * 6 : sp << 3);
           }
         }
       }
@@ -270,13 +317,13 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
           uint4 rw = make_uint4(0, 0, 0, 0);
           if (here) {
             rw = attempt_block(cell * 4 + 2 * pr, D.sweep, D.replica, D.seed_lo, D.seed_hi);
-            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, sP, D.nA,
+            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, sP, sR, D.nA,
                              sA, sB, acc, same, dsum);
           }
           __syncthreads();
           if (here)
             trial<K, NW, PL>(box, cbase + boff(2 * pr + 1), rw.z, rw.w, s_poff,
-                             sP, D.nA, sA, sB, acc, same, dsum);
+                             sP, sR, D.nA, sA, sB, acc, same, dsum);
           __syncthreads();
         }
       }
@@ -292,7 +339,10 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
       const int base = hoff(2 * (xw + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
       uint32_t s4[4];
 #pragma unroll
-      for (int b = 0; b < 4; b++) s4[b] = box[base + boff(b)] >> 3;
+      for (int b = 0; b < 4; b++) {
+        const uint32_t v = box[base + boff(b)];
+        s4[b] = NW == 0 ? (uint32_t)species6(v) : v >> 3;
+      }
       if (D.storage == SMCX_INT8) {
         *reinterpret_cast<uint32_t*>(D.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
       } else {
@@ -363,7 +413,24 @@ void sweep_fcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
   bccfast::Planes Q;
   const int K = hd->shells.K;
   const int PL = build_planes(hd, &Q, K == 3 ? 2 : 3);
-  const int NW = (K == 3 && hd->M <= 4) ? 1 : 2;
+  // counters: one byte-counter word (3 shells, M <= 4), six-bit fields in one
+  // word (M <= 5), else two byte-counter words
+  const int M = hd->M;
+  const int NW = (K == 3 && M <= 4) ? 1 : M <= 5 ? 0 : 2;
+  fccfast::Rows6 R;
+  memset(&R, 0, sizeof(R));
+  if (NW == 0)
+    for (int a = 0; a < M; a++)
+      for (int b = 0; b < M; b++) {
+        int32_t* r = R.r[a * 5 + b];
+        uint32_t sum = 0;
+        for (int k = 0; k < K; k++)
+          for (int c = 0; c < M; c++) {
+            r[k * 5 + c] = hd->V[((size_t)k * M + b) * M + c] - hd->V[((size_t)k * M + a) * M + c];
+            sum += (uint32_t)r[k * 5 + c];
+          }
+        r[15] = (int32_t)(0u - 32u * sum);
+      }
   const size_t smem = fccfast::smem_bytes(nA);
   const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
   auto run = [&](auto kern) {
@@ -372,10 +439,14 @@ void sweep_fcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
     const unsigned long long first = hd->sweep_cum;
     for (int64_t s = 0; s < n_sweeps; s++) {
       D.sweep = first + (unsigned long long)s;
-      for (int tc = 0; tc < n_colours; tc++) kern<<<grid, 128, smem, hd->stream>>>(D, Q, tc);
+      for (int tc = 0; tc < n_colours; tc++) kern<<<grid, 128, smem, hd->stream>>>(D, Q, R, tc);
     }
   };
-  if (K == 3) {
+  if (NW == 0) {
+    if (K == 3) run(fccfast::k_fcc_tile_sweep<3, 0, 0>);
+    else if (K == 2) run(fccfast::k_fcc_tile_sweep<2, 0, 0>);
+    else run(fccfast::k_fcc_tile_sweep<1, 0, 0>);
+  } else if (K == 3) {
     if (NW == 1) {
       if (PL == 2) run(fccfast::k_fcc_tile_sweep<3, 1, 2>);
       else run(fccfast::k_fcc_tile_sweep<3, 1, 3>);

@@ -83,6 +83,11 @@ SWEEP_CASES = [
     (smcx.FCC, 3, (9, 9, 9), 4, [0.25] * 4, smcx.PACKED4, (3, (1, 1, 1)), 1000.0, 4),      # link-cell
     # tiles of 15/14-15/14 cells: the largest box of the FCC tile kernel
     (smcx.FCC, 3, (30, 29, 28), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (2, 2, 2)), 1200.0, 3),
+    # fewer shells on the FCC tile kernel (six-bit counters, M <= 5)
+    (smcx.FCC, 2, (16, 14, 12), 3, [0.5, 0.3, 0.2], smcx.INT8, (3, (2, 2, 2)), 900.0, 4),
+    (smcx.FCC, 1, (12, 12, 10), 2, [0.5, 0.5], smcx.PACKED4, (3, (2, 2, 2)), 700.0, 4),
+    (smcx.FCC, 3, (18, 12, 12), 4, [0.25] * 4, smcx.PACKED4, (3, (2, 2, 2)), 1100.0, 3),
+    (smcx.FCC, 3, (12, 12, 12), 6, [1 / 6] * 6, smcx.INT8, (3, (2, 2, 2)), 1300.0, 3),
 ]
 
 
@@ -103,6 +108,24 @@ def test_sweep_bit_exact(stream, case, kernel):
     assert (got == ref).all(), f"{(got != ref).sum()} sites differ"
     assert st.tolist() == rst.tolist()
     assert lat.energy() == O.energy(kind, dims, M, K, V, ref)
+
+
+@pytest.mark.parametrize("M", [4, 5])
+def test_fcc_large_epi_bit_exact(stream, M):
+    """EPI entries near the 2^23 limit of the FCC tile kernel: the kernel's
+    intermediate sums leave int32 and must wrap back to the exact dE."""
+    kind, K, dims = smcx.FCC, 3, (15, 12, 12)
+    comp = [1.0 / M] * M
+    V = epi_gaussian(K, M, 20000.0, 4)
+    assert np.abs(V).max() < 2**23
+    lat = smcx.Lattice(kind, dims, M, comp, init_seed=3, storage=smcx.PACKED4, sched=(3, (2, 2, 2)), stream=stream)
+    lat.set_epi(V)
+    lat.sweep(2.0e5, 3, 9)
+    ref, rst = _oracle_run(kind, dims, M, K, V, comp, 3, 2.0e5, 3, 9, (3, (2, 2, 2)))
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[1].tolist() == rst.tolist()
+    assert lat.energy() == O.energy(kind, dims, M, K, V, ref)
+    lat.close()
 
 
 def test_oracle_sized_workload(stream):
