@@ -145,15 +145,37 @@ __global__ void __launch_bounds__(256) k_hook(const SweepParams P, const HalfShe
   }
 }
 
+// Root without writing: every pointer read is an ancestor, so the walk ends
+// at the root whatever other threads write meanwhile, as long as they write
+// ancestors too.
+__device__ __forceinline__ int find_root_ro(const int32_t* lab, int x, int* flag) {
+  const volatile int32_t* p = lab;
+  for (int it = 0; it < kFindLimit; it++) {
+    const int px = p[x];
+    if (px == x) return x;
+    x = px;
+  }
+  atomicOr(flag, 1);
+  return x;
+}
+
+// Labels to roots in two launches.  The first shortens the paths (halving)
+// and points every site at its root; a concurrent halving step elsewhere can
+// still overwrite such a final write with an intermediate ancestor.  The
+// second walks without halving, so every write is a root and stays one, and
+// counts the roots.
+template <bool FINAL>
 __global__ void k_compress(int32_t* lab, long long N, int* flag, unsigned long long* n_roots) {
   unsigned long long roots = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int r = find_root(lab, (int)i, flag);
+    const int r = FINAL ? find_root_ro(lab, (int)i, flag) : find_root(lab, (int)i, flag);
     lab[i] = r;
     roots += (r == (int)i);
   }
-  for (int o = 16; o > 0; o >>= 1) roots += __shfl_down_sync(0xffffffffu, roots, o);
-  if ((threadIdx.x & 31) == 0 && roots) atomicAdd(n_roots, roots);
+  if (FINAL) {
+    for (int o = 16; o > 0; o >>= 1) roots += __shfl_down_sync(0xffffffffu, roots, o);
+    if ((threadIdx.x & 31) == 0 && roots) atomicAdd(n_roots, roots);
+  }
 }
 
 // size[label]++ with one atomic per distinct label in a warp
@@ -324,7 +346,8 @@ void clusters_device(smcx_lattice* hd, long long thr2, int32_t* d_lab, int64_t* 
     k_hook<kBCC><<<grid_for(ncell), 256, 0, hd->stream>>>(P, H, cls.p, d_lab, hd->d_flag);
   else
     k_hook<kFCC><<<grid_for(ncell), 256, 0, hd->stream>>>(P, H, cls.p, d_lab, hd->d_flag);
-  k_compress<<<grid, 256, 0, hd->stream>>>(d_lab, hd->N, hd->d_flag, roots.p);
+  k_compress<false><<<grid, 256, 0, hd->stream>>>(d_lab, hd->N, hd->d_flag, roots.p);
+  k_compress<true><<<grid, 256, 0, hd->stream>>>(d_lab, hd->N, hd->d_flag, roots.p);
   check_cuda(cudaGetLastError(), "cluster launches");
   int flag = 0;
   unsigned long long nr = 0;

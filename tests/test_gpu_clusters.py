@@ -76,6 +76,28 @@ def test_local_energy_clusters_summary(stream, kind, K, dims, M, storage, sweeps
     lat.close()
 
 
+def test_cluster_labels_repeatable(stream):
+    """Labels are the cluster minima on every call: the compression writes
+    must not be overtaken by path-halving writes of other threads (a race
+    that left an intermediate ancestor as the label of a few sites).  Large
+    clusters, many launches."""
+    kind, K, dims, M = smcx.BCC, 4, (24, 22, 20), 2
+    lat, V = _lattice(stream, kind, K, dims, M, smcx.INT8)
+    cfg = lat.get_config()
+    N = cfg.size
+    e2 = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.local_energy(e2.data_ptr())
+    want = e2.cpu().numpy().astype(np.int64)
+    lab = torch.empty(N, dtype=torch.int32, device="cuda")
+    for q in (0.3, 0.5, 0.7):
+        thr = int(np.quantile(want, q))
+        olab, onc = O.clusters(kind, dims, M, K, V, cfg, thr)
+        for _ in range(15):
+            assert lat.clusters(thr, lab.data_ptr()) == onc
+            assert (lab.cpu().numpy().astype(np.int64) == olab).all()
+    lat.close()
+
+
 def test_cluster_errors(stream):
     lat = smcx.Lattice(smcx.BCC, (8, 8, 8), 4, [0.25] * 4, stream=stream)
     buf = torch.empty(lat.N, dtype=torch.int32, device="cuda")
