@@ -96,8 +96,13 @@ static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Plane
                                    : launch_bcc<4, 2, 2, 2>(hd, D, Q, threads, n, nc);
     return slots == 1 ? launch_bcc<4, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<4, 2, 3, 2>(hd, D, Q, threads, n, nc);
   }
-  // fewer shells: one general variant each (any M <= 8, three planes)
+  // fewer shells: one counter word and two planes (M <= 4, |V| < 2^15), or
+  // the general variant (any M <= 8, two words, three planes)
   if (slots == 4) fail(SMCX_E_UNSUPPORTED, "block shape");
+  if (nw == 1 && pl == 2) {
+    if (K == 3) return slots == 1 ? launch_bcc<3, 1, 2, 1>(hd, D, Q, threads, n, nc) : launch_bcc<3, 1, 2, 2>(hd, D, Q, threads, n, nc);
+    if (K == 2) return slots == 1 ? launch_bcc<2, 1, 2, 1>(hd, D, Q, threads, n, nc) : launch_bcc<2, 1, 2, 2>(hd, D, Q, threads, n, nc);
+  }
   if (K == 3) return slots == 1 ? launch_bcc<3, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<3, 2, 3, 2>(hd, D, Q, threads, n, nc);
   if (K == 2) return slots == 1 ? launch_bcc<2, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<2, 2, 3, 2>(hd, D, Q, threads, n, nc);
   return slots == 1 ? launch_bcc<1, 2, 3, 1>(hd, D, Q, threads, n, nc) : launch_bcc<1, 2, 3, 2>(hd, D, Q, threads, n, nc);
@@ -124,13 +129,20 @@ void sweep_bcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
   D.sweep = hd->sweep_cum;
   D.proposal = hd->proposal;
   bccfast::Planes Q;
-  // fewer than 4 shells: one general variant (three planes, two words)
-  const int PL = build_planes(hd, &Q, hd->shells.K == 4 ? 2 : 3);
-  const int nw = hd->M <= 4 ? 1 : 2;
+  // 4 shells: every (words, planes) pair is compiled.  2 or 3 shells: one
+  // counter word and two planes (M <= 4, |V| < 2^15), else the general
+  // variant (two words, three planes); 1 shell: the general variant.
+  const int K = hd->shells.K;
+  int nw = hd->M <= 4 ? 1 : 2;
+  int PL = build_planes(hd, &Q, 2);
+  if (K < 4 && !(nw == 1 && PL == 2 && K >= 2)) {
+    nw = 2;
+    PL = build_planes(hd, &Q, 3);
+  }
   int threads, slots;
   bcc_block_shape(D.NQ, hd->bcc_threads, &threads, &slots);
 
-  dispatch(hd, D, Q, hd->shells.K == 4 ? nw : 2, PL, threads, slots, n_sweeps, n_colours);
+  dispatch(hd, D, Q, nw, PL, threads, slots, n_sweeps, n_colours);
 }
 
 }  // namespace smcx

@@ -74,6 +74,8 @@ SWEEP_CASES = [
     (smcx.BCC, 4, (12, 12, 12), 4, [0.25] * 4, smcx.INT8, (3, (1, 1, 1)), 800.0, 6),       # link-cell
     (smcx.BCC, 4, (12, 12, 16), 4, [0.25] * 4, smcx.PACKED4, (4, (1, 1, 1)), 2500.0, 4),   # link-cell
     (smcx.BCC, 2, (12, 10, 8), 3, [0.5, 0.3, 0.2], smcx.INT8, (3, (2, 2, 2)), 1200.0, 5),
+    (smcx.BCC, 2, (40, 36, 32), 4, [0.25] * 4, smcx.PACKED4, (4, (2, 2, 2)), 1000.0, 2),  # 20-cell tiles
+    (smcx.BCC, 3, (20, 18, 16), 4, [0.25] * 4, smcx.PACKED4, (4, (2, 2, 2)), 1300.0, 3),
     (smcx.BCC, 1, (10, 12, 8), 2, [0.5, 0.5], smcx.PACKED4, (3, (2, 2, 2)), 600.0, 5),
     (smcx.BCC, 3, (24, 20, 22), 6, [1 / 6] * 6, smcx.PACKED4, (4, (2, 2, 2)), 1500.0, 3),
     (smcx.BCC, 4, (40, 24, 26), 8, [0.125] * 8, smcx.INT8, (3, (2, 2, 2)), 2000.0, 2),
@@ -108,6 +110,23 @@ def test_sweep_bit_exact(stream, case, kernel):
     assert (got == ref).all(), f"{(got != ref).sum()} sites differ"
     assert st.tolist() == rst.tolist()
     assert lat.energy() == O.energy(kind, dims, M, K, V, ref)
+
+
+@pytest.mark.parametrize("K", [2, 3])
+def test_bcc_fewer_shells_large_epi_bit_exact(stream, K):
+    """2 and 3 BCC shells with |V| >= 2^15: the tile kernel falls back from
+    one counter word and two byte planes to two words and three planes."""
+    kind, dims, M = smcx.BCC, (16, 14, 12), 4
+    comp = [0.25] * 4
+    V = epi_gaussian(K, M, 2000.0, 4)
+    assert np.abs(V).max() >= 2**15
+    lat = smcx.Lattice(kind, dims, M, comp, init_seed=3, storage=smcx.PACKED4, sched=(3, (2, 2, 2)), stream=stream)
+    lat.set_epi(V)
+    lat.sweep(5.0e4, 3, 9)
+    ref, rst = _oracle_run(kind, dims, M, K, V, comp, 3, 5.0e4, 3, 9, (3, (2, 2, 2)))
+    assert (lat.get_config() == ref).all()
+    assert lat.state()[1].tolist() == rst.tolist()
+    lat.close()
 
 
 @pytest.mark.parametrize("M", [4, 5])
