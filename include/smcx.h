@@ -68,7 +68,7 @@ extern "C" {
 #define SMCX_E_OOM (-5)         /* device allocation failed                    */
 #define SMCX_E_TIMEOUT (-6)     /* a bounded device wait gave up               */
 #define SMCX_E_RANGE (-7)       /* |dE| of this EPI table may overflow int32   */
-#define SMCX_E_UNSUPPORTED (-8) /* valid request this build does not run       */
+#define SMCX_E_UNSUPPORTED (-8) /* valid request this library does not run     */
 
 /* ---- enumerations ---------------------------------------------------- */
 #define SMCX_BCC 0
@@ -120,7 +120,7 @@ int smcx_version(void);
  * Create a lattice with an exact-composition initial configuration.
  *   kind      SMCX_BCC or SMCX_FCC;  nx, ny, nz >= 1 cubic cells.
  *   M         species count, 1 <= M <= 15 (PACKED4) or 127 (INT8); the sweep
- *             kernels of this build run M <= 8.
+ *             kernels of this library run M <= 8.
  *   comp      [M] fractions summing to 1; counts are floor(c_p N) plus one for
  *             the largest remainders (ties to the lower index).
  *   init_seed species are placed by the rank of a 64-bit Philox key per site

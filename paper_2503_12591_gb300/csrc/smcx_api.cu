@@ -217,7 +217,7 @@ int smcx_set_epi(smcx_lattice* h, int K, const int32_t* V) {
     need(h && V, SMCX_E_INVALID_ARG, "NULL argument");
     need(K >= 1 && K <= kind_max_shells(h->kind), SMCX_E_INVALID_ARG, "shell count out of range");
     const int M = h->M;
-    need(M <= kMaxSweepM, SMCX_E_UNSUPPORTED, "sweep kernels of this build run at most 8 species");
+    need(M <= kMaxSweepM, SMCX_E_UNSUPPORTED, "sweep kernels of this library run at most 8 species");
     for (int k = 0; k < K; k++)
       for (int p = 0; p < M; p++)
         for (int q = 0; q < M; q++)

@@ -1,7 +1,7 @@
 """Oracle Philox4x32-10 pinned to an independent implementation.
 
 The paper draws its trial random numbers with cuRAND (Method "Implementation
-of SMC-GPU", random-number item) without naming the generator; this build
+of SMC-GPU", random-number item) without naming the generator; this library
 uses Philox4x32-10 (Salmon et al., SC'11).  The oracle's generator is checked
 against ATen's ``philox_engine`` (shipped as a header with PyTorch), compiled
 and run here on the same counters and keys.
