@@ -377,6 +377,12 @@ int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
  *   smcx_batch_energy   E[R], one smcx_energy per replica.
  *   smcx_batch_info     grid size, threads per CTA and whether the last call
  *                       replayed a graph.
+ *   smcx_batch_set_block threads per CTA of the next sweeps: 0 (the fewest
+ *                       128-thread-or-smaller CTAs that cover a tile's link
+ *                       cells with at most 2 slots per thread), 128, or 256
+ *                       (one slot per thread; SMCX_E_UNSUPPORTED at the next
+ *                       sweep if a tile has more than 256 link cells).
+ *                       SMCX_E_INVALID_ARG for other values.
  *   smcx_batch_set_fault test hook: CTA `skip_cta` (>= 0) skips the first grid
  *                       barrier, which then times out after timeout_ms and the
  *                       next smcx_batch_sweep returns SMCX_E_TIMEOUT; -1 turns
@@ -423,6 +429,7 @@ int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, 
  */
 int smcx_batch_fluct_accumulate(smcx_batch* b, int shell, double* d_acc);
 int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_graph);
+int smcx_batch_set_block(smcx_batch* b, int threads);
 int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
 
 /*

@@ -89,9 +89,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
 }
 
 template <int K, int NW, int PL, int SLOTS>
-__global__ void __launch_bounds__(128, 6)
-    k_bcc_batch(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
-                int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
+__device__ __forceinline__ void batch_body(const Planes& Q, const LatDesc* __restrict__ descs,
+                                           const int2* __restrict__ items, int n_items, int n_sweeps, unsigned* bar,
+                                           int* status, long long timeout_ns, int skip_cta, int max_nA) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   uint8_t* box = smem;
@@ -109,6 +109,22 @@ __global__ void __launch_bounds__(128, 6)
       epoch++;
       if (!grid_barrier(bar, epoch * gridDim.x, status, timeout_ns)) return;
     }
+}
+
+// 128-thread CTAs (one or two link-cell slots per thread), and 256-thread
+// CTAs for tiles of up to 256 slots (6^3 with link cells of 3): one slot per
+// thread, so a tile's phases take half the sequential steps of two slots.
+template <int K, int NW, int PL, int SLOTS>
+__global__ void __launch_bounds__(128, 6)
+    k_bcc_batch(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
+                int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
+  batch_body<K, NW, PL, SLOTS>(Q, descs, items, n_items, n_sweeps, bar, status, timeout_ns, skip_cta, max_nA);
+}
+template <int K, int NW, int PL>
+__global__ void __launch_bounds__(256, 3)
+    k_bcc_batch256(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
+                   int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
+  batch_body<K, NW, PL, 1>(Q, descs, items, n_items, n_sweeps, bar, status, timeout_ns, skip_cta, max_nA);
 }
 
 }  // namespace bccfast
@@ -156,7 +172,13 @@ void rebuild_items(smcx_batch* b) {
   check_cuda(cudaStreamSynchronize(b->stream), "batch work list sync");
   b->n_items = (int)items.size();
   int threads, slots;
-  bcc_block_shape(nq, b->threads, &threads, &slots);
+  if (b->threads == 256) {
+    threads = 256;  // one slot per thread
+    slots = 1;
+    if (nq * nq * nq > 256) fail(SMCX_E_UNSUPPORTED, "256-thread CTAs take tiles of at most 256 link-cell slots");
+  } else {
+    bcc_block_shape(nq, b->threads, &threads, &slots);
+  }
   if (slots > 2) fail(SMCX_E_UNSUPPORTED, "batched tiles need at most 256 link-cell slots");
   b->threads = threads;
   b->slots = slots;
@@ -168,9 +190,12 @@ void rebuild_items(smcx_batch* b) {
 using KernelFn = void (*)(const bccfast::Planes, const bccfast::LatDesc*, const int2*, int, int, unsigned*, int*,
                           long long, int, int);
 
-KernelFn pick_kernel(int nw, int pl, int slots) {
+KernelFn pick_kernel(int nw, int pl, int slots, int threads) {
   using namespace bccfast;
-#define SMCX_PICK(NW_, PL_) return slots == 1 ? k_bcc_batch<4, NW_, PL_, 1> : k_bcc_batch<4, NW_, PL_, 2>
+#define SMCX_PICK(NW_, PL_)                                    \
+  return threads == 256 ? k_bcc_batch256<4, NW_, PL_>          \
+         : slots == 1   ? k_bcc_batch<4, NW_, PL_, 1> \
+                        : k_bcc_batch<4, NW_, PL_, 2>
   if (nw == 1 && pl == 2) SMCX_PICK(1, 2);
   if (nw == 1) SMCX_PICK(1, 3);
   if (pl == 2) SMCX_PICK(2, 2);
@@ -231,7 +256,7 @@ static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps,
   bccfast::Planes Q;
   const int PL = build_planes(b->lat[0], &Q, 2);
   const int nw = b->lat[0]->M <= 4 ? 1 : 2;
-  KernelFn fn = pick_kernel(nw, PL, b->slots);
+  KernelFn fn = pick_kernel(nw, PL, b->slots, b->threads);
   // shared memory for the largest table of this call, rounded up so that a
   // graph instantiated for it serves nearby temperature sets as well
   const int nA_cap = std::min(kNA, ((max_nA + 255) / 256) * 256);
@@ -632,6 +657,15 @@ int smcx_batch_info(const smcx_batch* b, int* grid, int* threads, int* used_grap
     if (grid) *grid = b->last_grid;
     if (threads) *threads = b->threads;
     if (used_graph) *used_graph = b->last_graph ? 1 : 0;
+  });
+}
+
+int smcx_batch_set_block(smcx_batch* b, int threads) {
+  return guarded_call([&] {
+    need_(b != nullptr, SMCX_E_INVALID_ARG, "NULL batch");
+    need_(threads == 0 || threads == 128 || threads == 256, SMCX_E_INVALID_ARG, "threads must be 0, 128 or 256");
+    b->threads = threads;
+    b->items_dirty = true;
   });
 }
 

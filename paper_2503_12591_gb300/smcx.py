@@ -70,6 +70,7 @@ _SIGS = {
     "smcx_batch_energy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_batch_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smcx_batch_set_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "smcx_batch_set_block": (C.c_int, [C.c_void_p, C.c_int]),
     "smcx_set_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_get_schedule": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_sweep": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64]),
@@ -440,6 +441,9 @@ class Batch:
         v = np.zeros(3, np.int32)
         _check(lib().smcx_batch_info(self._h, _p(v[0:]), _p(v[1:]), _p(v[2:])))
         return {"grid": int(v[0]), "threads": int(v[1]), "graph": bool(v[2])}
+
+    def set_block(self, threads):
+        _check(lib().smcx_batch_set_block(self._h, int(threads)))
 
     def set_fault(self, skip_cta, timeout_ms):
         _check(lib().smcx_batch_set_fault(self._h, int(skip_cta), int(timeout_ms)))

@@ -66,6 +66,33 @@ def test_batch_equals_plain_and_oracle(stream):
     b.close()
 
 
+@pytest.mark.parametrize("threads", [128, 256])
+def test_batch_block_sizes_equal_plain(stream, threads):
+    """Tiles of 16-18 cells with link cells of 3 have up to 216 link-cell
+    slots: two per thread on 128-thread CTAs, one on 256-thread CTAs.  Both
+    block sizes give every replica its own plain trajectory."""
+    dims = [(36, 34, 32), (18, 18, 18), (32, 36, 34)]
+    V = epi_gaussian(4, 4, 20.0, 3)
+    T = log_temperatures(len(dims), 500.0, 2500.0)
+    scheds = [_sched(d, L=3, target=18) for d in dims]
+    lats = [_make(d, r, V, stream, scheds[r]) for r, d in enumerate(dims)]
+    b = smcx.Batch(lats, stream)
+    b.set_block(threads)
+    b.sweep(T, 3, 13)
+    assert b.info()["threads"] == threads
+    for r, d in enumerate(dims):
+        plain = _make(d, r, V, stream, scheds[r])
+        plain.sweep(T[r], 3, 13)
+        assert (lats[r].get_config() == plain.get_config()).all(), f"replica {r} differs from its plain run"
+        assert lats[r].state()[1].tolist() == plain.state()[1].tolist()
+        plain.close()
+    with pytest.raises(smcx.SmcxError):
+        b.set_block(64)
+    b.close()
+    for l in lats:
+        l.close()
+
+
 def test_batch_autotune_then_oracle(stream):
     V = epi_gaussian(4, 4, 20.0, 2)
     dims = DIMS[:4]
