@@ -68,10 +68,10 @@ def parse():
     ap.add_argument("--no-fcc", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput", "anneal", "fcc", "paper"],
+                                                    "throughput", "anneal", "fcc", "paper", "paper_bcc"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
-                    help="profiling only: FCC edge of the fcc / qsro / clusters measurement other than 400")
+                    help="profiling only: lattice edge of the fcc / qsro / clusters / paper_bcc measurement")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -474,6 +474,34 @@ PAPER_ROWS = [
     ("FeCoNiAlTi_1M_EPI", "fcc", (72, 60, 60), FECONIALTI, "epi", 0.001755),
     ("FeCoNiAlTi_1M_qSRO", "fcc", (72, 60, 60), FECONIALTI, "qsro", 0.04703),
 ]
+
+
+def run_paper_bcc(stream, edge=0):
+    """The MoNbTaW_1B_EPI shape of the paper's Tab. models_summary (BCC, 4
+    equiatomic species, 2-shell EPI N(0,20 meV), packed 4-bit, 1000 K) at
+    edge^3 cells (795 by default), library schedule: sweeps timed with CUDA
+    events (the profiling entry of that row's kernel)."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+
+    n = edge or 795
+    lat = smcx.Lattice(smcx.BCC, (n, n, n), 4, [0.25] * 4, init_seed=11, storage=smcx.PACKED4, stream=stream)
+    lat.set_epi(epi_gaussian(2, 4, 20.0, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.sweep(1000.0, 1, SEED)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.sweep(1000.0, 5, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    L, nt = lat.schedule()
+    N = lat.N
+    lat.close()
+    return {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms, "schedule": {"L": L, "tiles": list(nt)},
+            "kernel": "k_bcc_tile_sweep<2,1,2,1,0>",
+            "workload": f"BCC {n}^3 x 2 = {N:,} sites, 4 species equiatomic, 2-shell EPI N(0,20 meV), packed 4-bit, "
+                        "1000 K"}
 
 
 def run_paper_rows(stream):
@@ -936,6 +964,7 @@ def main():
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
               "throughput": run_throughput256, "anneal": run_anneal,
               "fcc": lambda st: run_fcc(st, args.edge), "paper": run_paper_rows,
+              "paper_bcc": lambda st: run_paper_bcc(st, args.edge),
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:
