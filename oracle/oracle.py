@@ -68,6 +68,7 @@ def lib():
         L.orc_init_sample.argtypes = [i32] * 5 + [vp, u64, vp, i32, vp]
         L.orc_phase_of.argtypes = [i32] * 8 + [i64, vp]
         L.orc_phase_of.restype = i64
+        L.orc_specific_heat.argtypes = [vp, vp, i64, i64, dbl, vp]
         _lib = L
     return _lib
 
@@ -374,3 +375,16 @@ def init_sample(kind, dims, M, comp, seed, ids):
 
 def phase_direction(seed, sweep, replica, tile, ic, z1):
     return int(lib().orc_phase_direction(int(seed), int(sweep), int(replica), int(tile), int(ic), int(z1)))
+
+
+def specific_heat(E, n_sites, T, w=None):
+    """(mean E, Var E, C_V / (N k_B)) of energies E (int64, 0.01 meV) with
+    optional weights w (see orc_specific_heat)."""
+    Ev = np.ascontiguousarray(E, np.int64)
+    wv = None if w is None else np.ascontiguousarray(w, np.float64)
+    assert wv is None or wv.size == Ev.size
+    out = np.zeros(3, np.float64)
+    rc = lib().orc_specific_heat(_p(Ev), None if wv is None else _p(wv), Ev.size, int(n_sites), float(T), _p(out))
+    if rc:
+        raise ValueError("oracle specific heat rejected the request")
+    return float(out[0]), float(out[1]), float(out[2])

@@ -1125,3 +1125,34 @@ int orc_clusters_qsro(int kind, int nx, int ny, int nz, int M, int K, const int3
                       const int8_t* sigma, int64_t thr2, int64_t* labels, int64_t* n_clusters) {
   return clusters_impl(kind, nx, ny, nz, M, K, V, W, sigma, thr2, labels, n_clusters);
 }
+
+/* ------------------------------------------------------------------ */
+/* Specific heat from energy fluctuations                              */
+/* ------------------------------------------------------------------ */
+
+/* C_V / (N k_B) = Var(E) / (N (k_B T)^2) with E converted from 0.01 meV to
+ * meV and k_B in meV/K (Results, Fig. C_V; Method "MC simulation"). */
+int orc_specific_heat(const int64_t* E, const double* w, int64_t n, int64_t N, double T, double* out) {
+  if (n < 1 || N < 1 || !(T > 0.0)) return -1;
+  double wsum = 0.0, mean = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    const double wi = w ? w[i] : 1.0;
+    wsum += wi;
+    mean += wi * (double)E[i];
+  }
+  if (!(wsum > 0.0)) return -1;
+  mean /= wsum;
+  double var = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    const double wi = w ? w[i] : 1.0;
+    const double d = (double)E[i] - mean;
+    var += wi * d * d;
+  }
+  var /= wsum;
+  const double var_mev2 = var * 0.01 * 0.01;
+  const double kT = ORC_KB_MEV * T;
+  out[0] = mean;
+  out[1] = var;
+  out[2] = var_mev2 / ((double)N * kT * kT);
+  return 0;
+}

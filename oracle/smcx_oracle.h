@@ -175,6 +175,21 @@ int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t
                    int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
                    int ntx, int nty, int ntz, int64_t* stats);
 
+/* Specific heat from energy fluctuations (Results, Fig. C_V; Method "MC
+ * simulation"; Supplementary "Statistical mechanics" for the canonical
+ * average).  The canonical fluctuation formula
+ *   C_V / (N k_B) = (<E^2> - <E>^2) / (N (k_B T)^2),
+ * where <.> averages the n energies E[i] (0.01 meV units) with weights w[i]
+ * (w = NULL: weight 1 each, the time average over a recorded trace; else,
+ * e.g., Boltzmann weights of enumerated states; they need not sum to 1).
+ * Two passes in double: the weighted mean, then the weighted mean squared
+ * deviation from it.  out[0] = <E> (0.01 meV), out[1] = <E^2> - <E>^2
+ * ((0.01 meV)^2), out[2] = C_V / (N k_B) (per site, k_B units).
+ * Returns 0, or -1 for n < 1, N < 1, T <= 0 or a non-positive weight sum.
+ * Pinned: equals d<E>/dT / (N k_B) of an exactly enumerated canonical
+ * average (16-site box) and the two-level closed form. */
+int orc_specific_heat(const int64_t* E, const double* w, int64_t n, int64_t N, double T, double* out);
+
 #ifdef __cplusplus
 }
 #endif
