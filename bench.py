@@ -584,7 +584,8 @@ def run_anneal(stream):
                     "include the relaxation drift after each temperature step and are not physical",
             "workload": "BCC 320^3 = 65,536,000 sites packed 4-bit, 4 species, 4-shell EPI N(0,20 meV); "
                         "2000 -> 1000 K in 50 K steps, 20 discarded + 40 recorded sweeps per temperature; "
-                        "host wall time including the per-sweep exact energies (smcx_sweep_energies)"}
+                        "host wall time including the per-sweep exact energies and their FP64 moments on the device "
+                        "(smcx_sweep_cv)"}
 
 
 def run_clusters(stream, edge=0):

@@ -260,6 +260,24 @@ int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* th
  */
 int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E);
 
+/*
+ * Specific heat from energy fluctuations (Results, Fig. C_V; Method "MC
+ * simulation": C_V from the energies recorded over the sweeps at one
+ * temperature).  Runs n_sweeps (1..2^24) sweeps as smcx_sweep_energies,
+ * recording the exact energy after each one on the device, and reduces that
+ * trace on the device in FP64 (two passes: mean, then mean squared deviation)
+ * to the canonical fluctuation formula
+ *   moments[0] = <E>                  (0.01 meV),
+ *   moments[1] = <E^2> - <E>^2        ((0.01 meV)^2),
+ *   moments[2] = C_V / (N k_B) = (<E^2> - <E>^2) / (N (k_B T)^2)
+ * with E in meV and k_B = 8.617333262e-2 meV/K; <.> is the average over the
+ * n_sweeps recorded energies.  moments: host double[3], required.  E: host
+ * int64[n_sweeps] receiving the trace, or NULL.  Synchronous on return.
+ * Temporary device memory 8 (n_sweeps + 4) bytes.  Errors as
+ * smcx_sweep_energies; SMCX_E_INVALID_ARG for n_sweeps < 1 or NULL moments.
+ */
+int smcx_sweep_cv(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E, double* moments);
+
 /* Verification hook: run tile colours 0..n_colours-1 (0..8) of sweep number
  * `cumulative sweep index` without advancing the index, i.e. the first part
  * of the next smcx_sweep.  Tiles of one colour never interact, so after one
@@ -476,16 +494,21 @@ int smcx_fluct_gradient(const double* d_acc, int K, int M, double T, double* d_g
  *   kind, nx, ny, nz, M, storage  describe d_sites exactly as for
  *                                 smcx_lattice_create (canonical site order);
  *   K, V                          EPI table V[K][M][M] on the host (symmetric);
- *   d_sites                       device pointer to the species ids, read only;
+ *   d_sites                       device (or managed) pointer to the species
+ *                                 ids, read only; a host pointer is rejected;
  *   E                             host output, exact energy in 0.01 meV;
  *   stream                        cudaStream_t ordering the work (NULL = default).
- * The histogram, the EPI table and the result live in one fixed device array
- * of 16 KiB inside the library (held by every GPU that loads it until the
- * process exits): K*M*M must not exceed 1300, otherwise SMCX_E_INVALID_ARG.
- * The first call on a device looks up that array's address with the device
- * current; make that first call before any stream capture.  All calls share
- * the array: it is cleared at the start of each call, and calls whose GPU work
- * overlaps (several streams or host threads) race and return wrong energies.
+ * The histogram, the EPI table, the result and a bad-id flag live in one fixed
+ * device array of 16 KiB inside the library (held by every GPU that loads it
+ * until the process exits): K*M*M must not exceed 1300, otherwise
+ * SMCX_E_INVALID_ARG.  Species ids are checked as they are read: an id outside
+ * 0..M-1 is not counted and the call returns SMCX_E_INVALID_ARG.  The first
+ * call on a device looks up that array's address with the device current;
+ * make that first call before any stream capture.  The address is kept for the
+ * life of the process and does not survive cudaDeviceReset: do not call this
+ * entry point on a device after resetting it.  All calls share the array: it
+ * is cleared at the start of each call, and calls whose GPU work overlaps
+ * (several streams or host threads) race and return wrong energies.
  * Synchronises `stream` before returning.
  */
 int smcx_energy_noalloc(int kind, int nx, int ny, int nz, int M, int storage, int K, const int32_t* V,

@@ -3,20 +3,15 @@
 The paper anneals from 2000 K downwards in 50 K steps, discards the first
 sweeps at each temperature and records the following ones to compute C_V
 (Method "MC simulation"; Results "Energy model", Fig. CV).  The specific heat
-is the textbook canonical fluctuation formula C_V = (<E^2> - <E>^2) / (k_B T^2).
+is the canonical fluctuation formula C_V = (<E^2> - <E>^2) / (k_B T^2).
 
-The energy after every sweep comes from smcx_sweep_energies: the library
-accumulates the exact sum of the accepted energy changes, so E(t) = E(0) +
-(dsum(t) - dsum(0)), recorded on the device after each sweep and read once.
-Every number here is computed by the CUDA library; this module only
-schedules calls and sums the int64 energies it returns (FP64 moments).
+This module only schedules library calls.  smcx_sweep_cv sweeps, records the
+exact energy after every sweep on the device (E(0) plus the accepted energy
+changes) and reduces that trace on the device in FP64 to <E>, Var(E) and
+C_V / (N k_B); the acceptance rate comes from the library's counters.
 """
 from dataclasses import dataclass, field
 from typing import List
-
-import numpy as np
-
-KB_MEV = 8.617333262e-2  # meV / K
 
 
 @dataclass
@@ -31,17 +26,6 @@ class AnnealStep:
     energies: List[int] = field(default_factory=list)
 
 
-def energy_trace(lat, T: float, n: int, seed: int):
-    """Sweep n times at T; return the exact energy after each sweep."""
-    return [int(e) for e in lat.sweep_energies(T, n, seed)]
-
-
-def specific_heat(energies, T: float, n_sites: int) -> float:
-    """C_V / (N k_B) = (<E^2> - <E>^2) / (N (k_B T)^2), E in 0.01 meV."""
-    e = np.asarray(energies, np.float64) * 0.01  # meV
-    return float(e.var() / (n_sites * (KB_MEV * T) ** 2))
-
-
 def anneal(lat, temperatures, discard: int, record: int, seed: int, keep_energies=False):
     """Run the annealing schedule; return one AnnealStep per temperature."""
     steps = []
@@ -49,15 +33,13 @@ def anneal(lat, temperatures, discard: int, record: int, seed: int, keep_energie
         st0 = lat.state()[1].copy()
         if discard:
             lat.sweep(T, discard, seed)
-        E = energy_trace(lat, T, record, seed)
+        E, mean, var, cv = lat.sweep_cv(T, record, seed, want_trace=keep_energies)
         st1 = lat.state()[1]
         trials = max(1, int(st1[0] - st0[0]))
-        e = np.asarray(E, np.float64)
         steps.append(AnnealStep(T=float(T), sweeps_discarded=discard, sweeps_recorded=record,
-                                mean_E=float(e.mean()), var_E=float(e.var()),
-                                cv_per_site=specific_heat(E, T, lat.N),
+                                mean_E=mean, var_E=var, cv_per_site=cv,
                                 accept_rate=float(st1[1] - st0[1]) / trials,
-                                energies=list(E) if keep_energies else []))
+                                energies=[int(e) for e in E] if keep_energies else []))
     return steps
 
 

@@ -456,42 +456,66 @@ int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* th
   });
 }
 
-int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E) {
-  return guarded([&] {
-    need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
-    need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi before smcx_sweep_energies");
-    need(h->sched.L != 0, SMCX_E_SCHEDULE, "no checkerboard schedule fits this lattice");
-    need(T > 0.0 && isfinite(T), SMCX_E_INVALID_ARG, "temperature must be finite and > 0");
-    need(n_sweeps >= 0 && n_sweeps <= (1 << 24), SMCX_E_INVALID_ARG, "n_sweeps must be 0..2^24");
-    need(n_sweeps == 0 || E != nullptr, SMCX_E_INVALID_ARG, "NULL energy buffer");
-    need(h->sweep_cum + (uint64_t)n_sweeps < (1ull << 63), SMCX_E_INVALID_ARG, "sweep counter overflow");
-    if (n_sweeps == 0) return;
-    // start energy into d_energy, accepted-dE sum at the start beside it
-    if (!energy_bcc_direct(h)) {
-      pair_counts_device(h);
-      energy_device(h);
+// n_sweeps sweeps at T with the exact energy after each one recorded on the
+// device; then optionally the trace (E, host) and its FP64 moments and
+// specific heat (moments, host [3]).
+static void sweep_recorded(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E,
+                           double* moments, const char* who) {
+  need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
+  need(h->have_epi, SMCX_E_NO_EPI, (std::string("call smcx_set_epi before ") + who).c_str());
+  need(h->sched.L != 0, SMCX_E_SCHEDULE, "no checkerboard schedule fits this lattice");
+  need(T > 0.0 && isfinite(T), SMCX_E_INVALID_ARG, "temperature must be finite and > 0");
+  need(n_sweeps >= 0 && n_sweeps <= (1 << 24), SMCX_E_INVALID_ARG, "n_sweeps must be 0..2^24");
+  need(n_sweeps == 0 || E != nullptr || moments != nullptr, SMCX_E_INVALID_ARG, "NULL output buffer");
+  need(h->sweep_cum + (uint64_t)n_sweeps < (1ull << 63), SMCX_E_INVALID_ARG, "sweep counter overflow");
+  if (n_sweeps == 0) return;
+  // start energy into d_energy, accepted-dE sum at the start beside it
+  if (!energy_bcc_direct(h)) {
+    pair_counts_device(h);
+    energy_device(h);
+  }
+  if (!h->Wq.empty()) qsro_energy_add(h);
+  // d_buf: dE-sum snapshot, the n_sweeps energies, then 3 doubles of moments
+  long long* d_buf = nullptr;
+  check_cuda(cudaMalloc(&d_buf, (size_t)(n_sweeps + 1 + 3) * sizeof(long long)), "energy trace");
+  try {
+    check_cuda(cudaMemcpyAsync(d_buf, h->d_stats + 3, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream),
+               "dE sum snapshot");
+    upload_thresholds(h, T);
+    for (int64_t i = 0; i < n_sweeps; i++) {
+      sweep_device(h, h->thr_nA, seed, 1);
+      h->sweep_cum += 1;
+      record_energy(h, d_buf, d_buf + 1 + i);
     }
-    if (!h->Wq.empty()) qsro_energy_add(h);
-    long long* d_buf = nullptr;
-    check_cuda(cudaMalloc(&d_buf, (size_t)(n_sweeps + 1) * sizeof(long long)), "energy trace");
-    try {
-      check_cuda(cudaMemcpyAsync(d_buf, h->d_stats + 3, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream),
-                 "dE sum snapshot");
-      upload_thresholds(h, T);
-      for (int64_t i = 0; i < n_sweeps; i++) {
-        sweep_device(h, h->thr_nA, seed, 1);
-        h->sweep_cum += 1;
-        record_energy(h, d_buf, d_buf + 1 + i);
-      }
+    double* d_mom = reinterpret_cast<double*>(d_buf + 1 + n_sweeps);
+    if (moments) energy_moments(h, d_buf + 1, n_sweeps, T, d_mom);
+    if (E)
       check_cuda(cudaMemcpyAsync(E, d_buf + 1, (size_t)n_sweeps * sizeof(long long), cudaMemcpyDeviceToHost,
                                  h->stream),
                  "energy trace download");
-      check_cuda(cudaStreamSynchronize(h->stream), "energy trace sync");
-    } catch (...) {
-      cudaFree(d_buf);
-      throw;
-    }
+    if (moments)
+      check_cuda(cudaMemcpyAsync(moments, d_mom, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "moments download");
+    check_cuda(cudaStreamSynchronize(h->stream), "energy trace sync");
+  } catch (...) {
     cudaFree(d_buf);
+    throw;
+  }
+  cudaFree(d_buf);
+}
+
+int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E) {
+  return guarded([&] {
+    need(n_sweeps == 0 || E != nullptr, SMCX_E_INVALID_ARG, "NULL energy buffer");
+    sweep_recorded(h, T, n_sweeps, seed, E, nullptr, "smcx_sweep_energies");
+  });
+}
+
+int smcx_sweep_cv(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E, double* moments) {
+  return guarded([&] {
+    need(n_sweeps >= 1, SMCX_E_INVALID_ARG, "the specific heat needs n_sweeps >= 1");
+    need(moments != nullptr, SMCX_E_INVALID_ARG, "NULL moments buffer");
+    sweep_recorded(h, T, n_sweeps, seed, E, moments, "smcx_sweep_cv");
   });
 }
 

@@ -284,6 +284,53 @@ void record_energy(smcx_lattice* hd, const long long* d_dsum0, long long* d_out)
   check_cuda(cudaGetLastError(), "energy record launch");
 }
 
+// FP64 moments of a recorded energy trace and the specific heat from its
+// fluctuation (Results, Fig. C_V; Method "MC simulation"):
+// C_V / (N k_B) = Var(E) / (N (k_B T)^2), E converted from 0.01 meV to meV.
+// One CTA, two passes over the trace (mean, then mean squared deviation),
+// each a strided per-thread sum and a block reduction.
+__device__ double block_sum(double v, double* part) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(512) k_energy_moments(const long long* E, long long n, long long N, double T,
+                                                        double* out) {
+  __shared__ double part[16];
+  __shared__ double s_mean;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += (double)E[i];
+  s = block_sum(s, part);
+  if (threadIdx.x == 0) s_mean = s / (double)n;
+  __syncthreads();
+  const double mean = s_mean;
+  double q = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = (double)E[i] - mean;
+    q += d * d;
+  }
+  q = block_sum(q, part);
+  if (threadIdx.x == 0) {
+    const double var = q / (double)n;
+    const double kT = kBoltzmannMeV * T;
+    out[0] = mean;
+    out[1] = var;
+    out[2] = var * 1e-4 / ((double)N * kT * kT);
+  }
+}
+
+void energy_moments(smcx_lattice* hd, const long long* d_E, long long n, double T, double* d_out) {
+  k_energy_moments<<<1, 512, 0, hd->stream>>>(d_E, n, hd->N, T, d_out);
+  check_cuda(cudaGetLastError(), "energy moments launch");
+}
+
 void validate_store_at(smcx_lattice* hd, const uint8_t* d_store) {
   k_validate_store<<<1024, 256, 0, hd->stream>>>(d_store, hd->N, hd->storage, hd->M, hd->d_flag);
   check_cuda(cudaGetLastError(), "validate launch");

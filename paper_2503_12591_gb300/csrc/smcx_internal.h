@@ -140,6 +140,7 @@ void validate_int8(smcx_lattice* h, const int8_t* d_ids, int64_t count);  // set
 void validate_store(smcx_lattice* h);  // every stored id < M, else sets d_flag
 void validate_store_at(smcx_lattice* h, const uint8_t* d_store);  // same for a buffer in the store layout
 void record_energy(smcx_lattice* h, const long long* d_dsum0, long long* d_out);  // d_energy + stats[3] - dsum0
+void energy_moments(smcx_lattice* h, const long long* d_E, long long n, double T, double* d_out);  // mean, var, C_V/(N k_B)
 void local_energy_device(smcx_lattice* h, int32_t* d_e2);
 void sweep_qsro_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours);
 bool fcc_fast_usable(const smcx_lattice* h);

@@ -51,6 +51,7 @@ _SIGS = {
     "smcx_get_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_set_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_sweep_energies": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
+    "smcx_sweep_cv": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "smcx_probe_lds_rate": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
@@ -292,6 +293,15 @@ class Lattice:
         E = np.zeros(max(1, int(n_sweeps)), np.int64)
         _check(lib().smcx_sweep_energies(self._h, float(T), int(n_sweeps), int(seed), _p(E)))
         return E[:int(n_sweeps)]
+
+    def sweep_cv(self, T, n_sweeps, seed, want_trace=True):
+        """n_sweeps sweeps; (trace or None, mean E, Var E, C_V / (N k_B)),
+        the moments reduced on the device (smcx_sweep_cv)."""
+        m = np.zeros(3, np.float64)
+        E = np.zeros(max(1, int(n_sweeps)), np.int64) if want_trace else None
+        _check(lib().smcx_sweep_cv(self._h, float(T), int(n_sweeps), int(seed), None if E is None else _p(E),
+                                   _p(m)))
+        return (None if E is None else E[:int(n_sweeps)]), float(m[0]), float(m[1]), float(m[2])
 
     def set_kernel(self, which):
         _check(lib().smcx_set_kernel(self._h, int(which)))
