@@ -5,6 +5,8 @@ C functions; every computation happens in the C file, whose header cites the
 paper's passages each function follows.
 """
 import ctypes as C
+import os
+
 import numpy as np
 
 from . import build as _build
@@ -21,7 +23,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # SMCX_ORACLE_SANITIZE=1: the AddressSanitizer / UBSan build (the
+        # process must preload libasan; see tests/test_oracle_sanitize.py)
+        path = _build.build(sanitize=os.environ.get("SMCX_ORACLE_SANITIZE") == "1")
         L = C.CDLL(path)
         i32, i64, u64, dbl, vp = C.c_int, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
         L.orc_sites_per_cell.argtypes = [i32]
@@ -69,6 +73,10 @@ def lib():
         L.orc_phase_of.argtypes = [i32] * 8 + [i64, vp]
         L.orc_phase_of.restype = i64
         L.orc_specific_heat.argtypes = [vp, vp, i64, i64, dbl, vp]
+        L.orc_block_direction.argtypes = [u64, u64, i32, i32, i64, i32, i32]
+        L.orc_tile_pass_proposal.argtypes = [i32] * 6 + [vp, vp, dbl, u64, u64, i32] + [i32] * 7 + [vp, i32]
+        L.orc_sweep_parallel_proposal.argtypes = ([i32] * 6 + [vp, vp, dbl, i64, u64, u64, i32, i32, i32, i32, i32,
+                                                               vp, i32, vp, i32])
         _lib = L
     return _lib
 
@@ -185,7 +193,8 @@ def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
           L=0, nt=(1, 1, 1), proposal=0):
     """Run n_sweeps in place on sigma (int8, contiguous); returns stats
     (attempts, accepts, same-species proposals, sum of accepted dE).
-    proposal: 0 = direction per trial, 1 = shared per (sweep, tile, phase)."""
+    proposal: 0 = direction per trial, 1 = shared per (sweep, tile, phase),
+    2 = shared per (sweep, tile colour, block of two tiles, phase)."""
     assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
     Vv = np.ascontiguousarray(V, np.int32)
     st = np.zeros(4, np.int64)
@@ -198,16 +207,16 @@ def sweep(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
 
 
 def sweep_parallel(kind, dims, M, K, V, sigma, T, n_sweeps, seed, sweep0=0, replica=0,
-                   L=0, nt=(1, 1, 1), threads=0):
+                   L=0, nt=(1, 1, 1), threads=0, proposal=0):
     """oracle sweep with every phase split across OpenMP threads (identical
     result to sweep()); returns (stats, threads used)."""
     assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
     Vv = np.ascontiguousarray(V, np.int32)
     st = np.zeros(4, np.int64)
     used = np.zeros(1, np.int32)
-    rc = lib().orc_sweep_parallel(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
-                                  int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
-                                  _p(st), int(threads), _p(used))
+    rc = lib().orc_sweep_parallel_proposal(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(n_sweeps),
+                                           int(seed), int(sweep0), int(replica), int(L), *[int(t) for t in nt],
+                                           _p(st), int(threads), _p(used), int(proposal))
     if rc:
         raise ValueError(f"oracle sweep rejected the request ({rc})")
     return st, int(used[0])
@@ -352,13 +361,14 @@ def phase_of(kind, dims, L, nt, s):
     return int(ph), tuple(int(x) for x in t)
 
 
-def tile_pass(kind, dims, M, K, V, sigma, T, seed, sweep, replica, L, nt, tile):
+def tile_pass(kind, dims, M, K, V, sigma, T, seed, sweep, replica, L, nt, tile, proposal=0):
     """Run every phase of one tile in place (see orc_tile_pass)."""
     assert sigma.dtype == np.int8 and sigma.flags.c_contiguous
     Vv = np.ascontiguousarray(V, np.int32)
     st = np.zeros(4, np.int64)
-    rc = lib().orc_tile_pass(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(seed), int(sweep),
-                             int(replica), int(L), *[int(t) for t in nt], *[int(t) for t in tile], _p(st))
+    rc = lib().orc_tile_pass_proposal(kind, *dims, M, K, _p(Vv), _p(sigma), float(T), int(seed), int(sweep),
+                                      int(replica), int(L), *[int(t) for t in nt], *[int(t) for t in tile], _p(st),
+                                      int(proposal))
     if rc:
         raise ValueError(f"oracle tile pass rejected the request ({rc})")
     return st
@@ -388,3 +398,8 @@ def specific_heat(E, n_sites, T, w=None):
     if rc:
         raise ValueError("oracle specific heat rejected the request")
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def block_direction(seed, sweep, replica, tc, block, ic, z1):
+    return int(lib().orc_block_direction(int(seed), int(sweep), int(replica), int(tc), int(block), int(ic),
+                                         int(z1)))

@@ -668,19 +668,61 @@ int orc_phase_direction(uint64_t seed, uint64_t sweep, int replica, int64_t tile
   return (int)(((uint64_t)((ic & 1) ? o[2] : o[0]) * (uint64_t)z1) >> 32);
 }
 
+/* Block-shared proposals (mode 2): one shell-1 direction per (sweep, tile
+ * colour tc, block, intra colour ic), where a block is a pair of tiles of one
+ * colour: the tiles of colour tc are numbered j = (jz * ncy + jy) * ncx + jx
+ * with j_a = tile index >> 1 and nc_a the colour's tile count on axis a, and
+ * block = j >> 1 (the last block of an odd count holds one tile).  Philox
+ * counter (block | tc << 28, (ic >> 1) | replica << 16, sweep lo, sweep hi |
+ * 2^29), key = seed; word 0 for even ic, word 2 for odd ic.  As in mode 1,
+ * every trial is a symmetric proposal along a state-independent vector. */
+int orc_block_direction(uint64_t seed, uint64_t sweep, int replica, int tc, int64_t block, int ic, int z1) {
+  uint32_t ctr[4] = {(uint32_t)block | ((uint32_t)tc << 28), ((uint32_t)ic >> 1) | ((uint32_t)replica << 16),
+                     (uint32_t)sweep, (uint32_t)(sweep >> 32) | 0x20000000u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  return (int)(((uint64_t)((ic & 1) ? o[2] : o[0]) * (uint64_t)z1) >> 32);
+}
+
+/* block index (mode 2) of tile (ix, iy, iz) among the tiles of its colour */
+static int64_t tile_block(int ntx, int nty, int ix, int iy, int iz) {
+  const int ncx = (ntx + 1 - (ix & 1)) / 2, ncy = (nty + 1 - (iy & 1)) / 2;
+  const int64_t j = ((int64_t)(iz >> 1) * ncy + (iy >> 1)) * ncx + (ix >> 1);
+  return j >> 1;
+}
+
+/* forced direction of a phase of tile (ix, iy, iz), or -1 (mode 0) */
+static int phase_dir(int proposal, uint64_t seed, uint64_t sweep, int replica, int ntx, int nty, int ix, int iy,
+                     int iz, int ic, int z1) {
+  const int tc = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
+  if (proposal == 1) return orc_phase_direction(seed, sweep, replica, ((int64_t)iz * nty + iy) * ntx + ix, ic, z1);
+  if (proposal == 2) return orc_block_direction(seed, sweep, replica, tc, tile_block(ntx, nty, ix, iy, iz), ic, z1);
+  return -1;
+}
+
 /* All intra-colour phases of ONE tile (tile indices tx, ty, tz) of sweep
  * `sweep`: the part of the sweep loop below that belongs to this tile.  Tiles
  * of one colour never interact, so on that tile (and its partner ring) the
  * result equals the whole colour pass. */
 static int tile_pass_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
                           int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx,
-                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats);
+                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats, int proposal);
 
 int orc_tile_pass(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
                   int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica,
                   int L, int ntx, int nty, int ntz, int tx, int ty, int tz, int64_t* stats) {
   return tile_pass_impl(kind, nx, ny, nz, M, K, V, NULL, sigma, T, seed, sweep, replica, L, ntx, nty, ntz, tx, ty,
-                        tz, stats);
+                        tz, stats, 0);
+}
+
+/* orc_tile_pass with proposal mode 0, 1 or 2. */
+int orc_tile_pass_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, int8_t* sigma,
+                           double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx, int nty, int ntz,
+                           int tx, int ty, int tz, int64_t* stats, int proposal) {
+  if (proposal < 0 || proposal > 2) return -2;
+  return tile_pass_impl(kind, nx, ny, nz, M, K, V, NULL, sigma, T, seed, sweep, replica, L, ntx, nty, ntz, tx, ty,
+                        tz, stats, proposal);
 }
 
 /* orc_tile_pass for the qSRO model (W [K][M]). */
@@ -688,12 +730,12 @@ int orc_tile_pass_qsro(int kind, int nx, int ny, int nz, int M, int K, const int
                        int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx, int nty,
                        int ntz, int tx, int ty, int tz, int64_t* stats) {
   return tile_pass_impl(kind, nx, ny, nz, M, K, V, W, sigma, T, seed, sweep, replica, L, ntx, nty, ntz, tx, ty, tz,
-                        stats);
+                        stats, 0);
 }
 
 static int tile_pass_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
                           int8_t* sigma, double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx,
-                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats) {
+                          int nty, int ntz, int tx, int ty, int tz, int64_t* stats, int proposal) {
   shells_t S;
   int m = orc_sites_per_cell(kind);
   if (m == 0 || load_shells(kind, K, &S)) return -1;
@@ -733,9 +775,10 @@ static int tile_pass_impl(int kind, int nx, int ny, int nz, int M, int K, const 
   for (int ic = 0; ic < L * L * L * m; ic++) {
     int b = ic % m;
     int cx = (ic / m) % L, cy = (ic / m / L) % L, cz = ic / m / L / L;
+    const int fd = phase_dir(proposal, seed, sweep, replica, ntx, nty, tx, ty, tz, ic, S.z[0]);
     for (int z = z0 + cz; z < z0 + sz; z += L)
       for (int y = y0 + cy; y < y0 + sy; y += L)
-        for (int x = x0 + cx; x < x0 + sx; x += L) attempt(&c, (((int64_t)z * ny + y) * nx + x) * m + b);
+        for (int x = x0 + cx; x < x0 + sx; x += L) attempt_dir(&c, (((int64_t)z * ny + y) * nx + x) * m + b, fd);
   }
   free(A);
   free(B);
@@ -799,7 +842,7 @@ int orc_sweep_proposal(int kind, int nx, int ny, int nz, int M, int K, const int
                        int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed,
                        uint64_t sweep0, int replica, int L, int ntx, int nty, int ntz,
                        int64_t* stats, int proposal) {
-  if (proposal != 0 && (proposal != 1 || L == 0)) return -2;
+  if (proposal != 0 && ((proposal != 1 && proposal != 2) || L == 0)) return -2;
   return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
                     stats, proposal, 1, NULL);
 }
@@ -825,6 +868,24 @@ int orc_sweep_parallel(int kind, int nx, int ny, int nz, int M, int K, const int
                     stats, 0, nt, NULL);
 }
 
+/* orc_sweep_parallel with proposal mode 0, 1 or 2 (identical to the serial
+ * orc_sweep_proposal). */
+int orc_sweep_parallel_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, int8_t* sigma,
+                                double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
+                                int ntx, int nty, int ntz, int64_t* stats, int n_threads, int* used, int proposal) {
+#ifdef _OPENMP
+  int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+  int nt = 1;
+  (void)n_threads;
+#endif
+  if (proposal < 0 || proposal > 2 || (proposal != 0 && L == 0)) return -2;
+  if (L == 0) nt = 1;
+  if (used) *used = nt;
+  return sweep_impl(kind, nx, ny, nz, M, K, V, sigma, T, n_sweeps, seed, sweep0, replica, L, ntx, nty, ntz,
+                    stats, proposal, nt, NULL);
+}
+
 /* Sweep of the qSRO model (W [K][M], see qsro_site); the schedule is checked
  * against the qSRO read reach. */
 int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, const int32_t* W,
@@ -838,10 +899,11 @@ int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t
  * in the serial loop's order and split across threads; every thread keeps its
  * own statistics, summed at the end (integer sums: order-free). */
 static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty, int ntz, uint64_t sweep0,
-                                  int64_t n_sweeps, int n_threads) {
+                                  int64_t n_sweeps, int n_threads, int proposal) {
   const int m = c0->m, nx = c0->nx, ny = c0->ny, nz = c0->nz;
   const int64_t N = (int64_t)nx * ny * nz * m;
   int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  int8_t* fdir = (int8_t*)malloc((size_t)(N > 0 ? N : 1));
   int64_t tot[4] = {0, 0, 0, 0};
   int nA_ic = L * L * L * m;
   for (int64_t n = 0; n < n_sweeps; n++) {
@@ -859,9 +921,13 @@ static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty
               tile_bounds(nx, ntx, ix, &x0, &sx);
               tile_bounds(ny, nty, iy, &y0, &sy);
               tile_bounds(nz, ntz, iz, &z0, &sz);
+              const int fd = phase_dir(proposal, c0->seed, sw, c0->replica, ntx, nty, ix, iy, iz, ic, c0->S->z[0]);
               for (int z = z0 + cz; z < z0 + sz; z += L)
                 for (int y = y0 + cy; y < y0 + sy; y += L)
-                  for (int x = x0 + cx; x < x0 + sx; x += L) list[cnt++] = (((int64_t)z * ny + y) * nx + x) * m + b;
+                  for (int x = x0 + cx; x < x0 + sx; x += L) {
+                    fdir[cnt] = (int8_t)fd;
+                    list[cnt++] = (((int64_t)z * ny + y) * nx + x) * m + b;
+                  }
             }
         int64_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;
 #ifdef _OPENMP
@@ -875,7 +941,7 @@ static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty
 #ifdef _OPENMP
 #pragma omp for schedule(static)
 #endif
-          for (int64_t i = 0; i < cnt; i++) attempt_dir(&c, list[i], -1);
+          for (int64_t i = 0; i < cnt; i++) attempt_dir(&c, list[i], fdir[i]);
           t0 += st[0];
           t1 += st[1];
           t2 += st[2];
@@ -889,6 +955,7 @@ static void sweep_phases_parallel(const attempt_ctx* c0, int L, int ntx, int nty
   }
   for (int i = 0; i < 4; i++) c0->stats[i] += tot[i];
   free(list);
+  free(fdir);
 }
 
 static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V,
@@ -927,7 +994,7 @@ static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int3
   stats[0] = stats[1] = stats[2] = stats[3] = 0;
   int64_t N = (int64_t)nx * ny * nz * m;
   if (n_threads > 1) {
-    sweep_phases_parallel(&c, L, ntx, nty, ntz, sweep0, n_sweeps, n_threads);
+    sweep_phases_parallel(&c, L, ntx, nty, ntz, sweep0, n_sweeps, n_threads, proposal);
     free(A);
     free(B);
     return 0;
@@ -951,9 +1018,7 @@ static int sweep_impl(int kind, int nx, int ny, int nz, int M, int K, const int3
               tile_bounds(nx, ntx, ix, &x0, &sx);
               tile_bounds(ny, nty, iy, &y0, &sy);
               tile_bounds(nz, ntz, iz, &z0, &sz);
-              int fd = -1;
-              if (proposal == 1)
-                fd = orc_phase_direction(seed, c.sweep, replica, ((int64_t)iz * nty + iy) * ntx + ix, ic, S.z[0]);
+              const int fd = phase_dir(proposal, seed, c.sweep, replica, ntx, nty, ix, iy, iz, ic, S.z[0]);
               for (int z = z0 + cz; z < z0 + sz; z += L)
                 for (int y = y0 + cy; y < y0 + sy; y += L)
                   for (int x = x0 + cx; x < x0 + sx; x += L)

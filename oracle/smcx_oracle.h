@@ -175,6 +175,17 @@ int orc_sweep_qsro(int kind, int nx, int ny, int nz, int M, int K, const int32_t
                    int8_t* sigma, double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
                    int ntx, int nty, int ntz, int64_t* stats);
 
+/* Block-shared proposals (mode 2): the shell-1 direction shared by the tiles
+ * of one block (a pair of consecutive tiles of colour tc) in phase ic. */
+int orc_block_direction(uint64_t seed, uint64_t sweep, int replica, int tc, int64_t block, int ic, int z1);
+/* orc_tile_pass / orc_sweep_parallel with a proposal mode (0, 1, 2). */
+int orc_tile_pass_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, int8_t* sigma,
+                           double T, uint64_t seed, uint64_t sweep, int replica, int L, int ntx, int nty, int ntz,
+                           int tx, int ty, int tz, int64_t* stats, int proposal);
+int orc_sweep_parallel_proposal(int kind, int nx, int ny, int nz, int M, int K, const int32_t* V, int8_t* sigma,
+                                double T, int64_t n_sweeps, uint64_t seed, uint64_t sweep0, int replica, int L,
+                                int ntx, int nty, int ntz, int64_t* stats, int n_threads, int* used, int proposal);
+
 /* Specific heat from energy fluctuations (Results, Fig. C_V; Method "MC
  * simulation"; Supplementary "Statistical mechanics" for the canonical
  * average).  The canonical fluctuation formula

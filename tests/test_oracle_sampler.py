@@ -224,3 +224,62 @@ def test_shared_direction_differs_and_is_uniform():
     assert (a != b).any()
     assert (np.bincount(b, minlength=M) == np.bincount(a, minlength=M)).all()
     assert st[0] == 2 * b.size
+
+
+def test_block_direction_enumeration_chi2():
+    """Block-shared proposals (one direction per tile colour, block of two
+    tiles and phase) sample the canonical distribution: nearest-neighbour EPI
+    on the 16-site box, link-cell schedule L = 2, exact enumeration chi^2."""
+    dims, K = (2, 2, 2), 1
+    V = epi_gaussian(K, 2, 20.0, 33)
+    T = 1500.0
+    E = []
+    for ones in itertools.combinations(range(16), 8):
+        s = np.zeros(16, np.int8)
+        s[list(ones)] = 1
+        E.append(O.energy(O.BCC, dims, 2, K, V, s))
+    E = np.array(E)
+    lev, inv = np.unique(E, return_inverse=True)
+    p = np.bincount(inv) * np.exp(-(lev - lev.min()) * 0.01 / (KB * T))
+    p /= p.sum()
+    sig = O.init_config(O.BCC, dims, 2, [0.5, 0.5], 5)
+    idx = {int(e): i for i, e in enumerate(lev)}
+    hist = np.zeros(len(lev))
+    n, thin = 5000, 4
+    for i in range(n):
+        O.sweep(O.BCC, dims, 2, K, V, sig, T, thin, 13, sweep0=thin * i, L=2, proposal=2)
+        hist[idx[O.energy(O.BCC, dims, 2, K, V, sig)]] += 1
+    exp = p * n
+    keep = exp >= 5
+    obs = np.concatenate([hist[keep], [hist[~keep].sum()]])
+    ex = np.concatenate([exp[keep], [exp[~keep].sum()]])
+    if ex[-1] < 5:
+        obs, ex = obs[:-1], ex[:-1]
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    assert stats.chi2.sf(chi2, len(ex) - 1) > 1e-3
+
+
+def test_block_direction_shared_by_pairs_and_uniform():
+    """Mode 2 directions are uniform over the 8 shell-1 directions; on a
+    lattice with two blocks per colour the trajectory differs from mode 1's,
+    conserves the composition, attempts every site once per sweep, and the
+    OpenMP oracle follows it exactly."""
+    z1 = 8
+    counts = np.zeros(z1, np.int64)
+    for blk in range(40):
+        for tc in range(8):
+            for ic in range(54):
+                counts[O.block_direction(5, 3, 0, tc, blk, ic, z1)] += 1
+    exp = counts.sum() / z1
+    assert ((counts - exp) ** 2 / exp).sum() < 30.0
+    dims, K, M = (12, 12, 12), 4, 4
+    V = epi_gaussian(K, M, 20.0, 3)
+    a = O.init_config(O.BCC, dims, M, [0.25] * 4, 2)
+    b, c = a.copy(), a.copy()
+    O.sweep(O.BCC, dims, M, K, V, a, 1000.0, 2, 1, L=3, nt=(4, 2, 2), proposal=1)
+    st = O.sweep(O.BCC, dims, M, K, V, b, 1000.0, 2, 1, L=3, nt=(4, 2, 2), proposal=2)
+    O.sweep_parallel(O.BCC, dims, M, K, V, c, 1000.0, 2, 1, L=3, nt=(4, 2, 2), threads=4, proposal=2)
+    assert (a != b).any()
+    assert (b == c).all()  # the OpenMP oracle follows the same trajectory
+    assert (np.bincount(b, minlength=M) == np.bincount(a, minlength=M)).all()
+    assert st[0] == 2 * b.size
