@@ -213,10 +213,20 @@ int smcx_set_replica(smcx_lattice* h, int replica);
  * + tx (0 for the link-cell schedule); acceptance uniforms stay per trial.  Each trial is still a symmetric proposal, so every
  * phase keeps detailed balance and the canonical distribution is unchanged;
  * trials of a phase move along the same vector, which lets the BCC kernel
- * fetch the two environments as one compile-time union.  Batched sweeps use
- * SMCX_PROPOSAL_SITE. */
+ * fetch the two environments as one compile-time union.
+ * SMCX_PROPOSAL_BLOCK: one direction per (sweep, tile colour tc, block, intra
+ * colour ic), where a block is a pair of consecutive tiles of colour tc (the
+ * colour's tiles numbered j = (jz * ncy + jy) * ncx + jx, j_a = tile index >>
+ * 1, nc_a = the colour's tile count on axis a; block = j >> 1): Philox counter
+ * (block | tc << 28, (ic >> 1) | replica << 16, sweep lo, sweep hi | 2^29),
+ * key = seed, word 0 for even ic and word 2 for odd ic.  The proposals are
+ * keyed by (seed, sweep, colour, block), and the BCC kernel sweeps the two
+ * tiles of a block in one CTA with the union of the environments read once
+ * for both.  FCC lattices run the other modes on the generic tile kernel;
+ * batched and qSRO sweeps run SMCX_PROPOSAL_SITE only. */
 #define SMCX_PROPOSAL_SITE 0
 #define SMCX_PROPOSAL_TILE 1
+#define SMCX_PROPOSAL_BLOCK 2
 int smcx_set_proposal(smcx_lattice* h, int mode);
 
 /* Threads per CTA of the BCC shared-memory kernel (0 = one thread per
@@ -459,7 +469,9 @@ int smcx_batch_set_fault(smcx_batch* b, int skip_cta, int timeout_ms);
  * by back-propagation (Results "Energy model").
  *   smcx_pair_counts_batch  C[B][K][M][M] (int64) of B configurations of one
  *                           geometry (int8 ids [B][N], canonical order; N up
- *                           to ~200k sites).
+ *                           to ~200k sites).  A configuration holding an id
+ *                           outside 0..M-1 is not counted: all its K*M*M
+ *                           counts are set to -1.
  *   smcx_epi_energy_batch   E[b] = 1/2 sum_i V[i] C[b][i] (float V, FP64 sum,
  *                           float E), KMM = K*M*M.
  *   smcx_epi_grad_batch     grad[i] = 1/2 sum_b g[b] C[b][i] (float).
@@ -521,6 +533,21 @@ int smcx_energy_noalloc(int kind, int nx, int ny, int nz, int M, int storage, in
  * enqueued on `stream` and waited for) and returns lane-loads per second.
  */
 int smcx_probe_lds_rate(double* lane_loads_per_s, void* stream);
+
+/*
+ * Bounds-check status of the debug build (entry point outside the paper).
+ * The library built with SMCX_DEBUG=1 (paper_2503_12591_gb300/_build/
+ * libsmcx_debug.so) checks the index of its shared-memory box accesses,
+ * tile staging and write-back, and pair-count bins against their extents;
+ * an out-of-range index skips that access and records a tag (the access
+ * kind, SMCX_DEBUG_* in smcx_device.cuh order: 1 BCC box, 2 BCC staging,
+ * 3 BCC write-back, 4 BCC phase directions, 5 generic tile box, 6 FCC box,
+ * 7 pair-count bin, 8 lattice store) and the index.  Nothing traps.  This call
+ * synchronises the device, writes info[0] = the first tag recorded since the
+ * last call (0: none), info[1] = its index, and clears the record.
+ * SMCX_E_UNSUPPORTED in the normal build.
+ */
+int smcx_debug_status(uint64_t* info);
 
 #ifdef __cplusplus
 }

@@ -96,7 +96,25 @@ void upload_thresholds(smcx_lattice* h, double T) {
 
 }  // namespace
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace smcx {
+
+// Debug build: host readers of the per-translation-unit status words (see
+// smcx_device.cuh); registered by static initialisers when the library loads.
+namespace dbg {
+static std::vector<int (*)(unsigned long long*)>& readers() {
+  static std::vector<int (*)(unsigned long long*)> r;
+  return r;
+}
+int register_reader(int (*reader)(unsigned long long*)) {
+  readers().push_back(reader);
+  return (int)readers().size();
+}
+}  // namespace dbg
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 void upload_thresholds_for(smcx_lattice* h, double T) { upload_thresholds(h, T); }
 }  // namespace smcx
 
@@ -324,7 +342,8 @@ int smcx_set_replica(smcx_lattice* h, int replica) {
 int smcx_set_proposal(smcx_lattice* h, int mode) {
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
-    need(mode == SMCX_PROPOSAL_SITE || mode == SMCX_PROPOSAL_TILE, SMCX_E_INVALID_ARG, "unknown proposal mode");
+    need(mode == SMCX_PROPOSAL_SITE || mode == SMCX_PROPOSAL_TILE || mode == SMCX_PROPOSAL_BLOCK,
+         SMCX_E_INVALID_ARG, "unknown proposal mode");
     h->proposal = mode;
   });
 }
@@ -353,6 +372,7 @@ int smcx_get_schedule(const smcx_lattice* h, smcx_sched* out) {
 }
 
 int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed) {
+  NvtxRange nvtx_range("smcx_sweep");
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi before smcx_sweep");
@@ -372,6 +392,7 @@ int smcx_sweep(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed) {
 // kernel, block size, on a snapshot of the configuration; restores the
 // configuration, statistics and sweep counter and installs the fastest.
 int smcx_autotune(smcx_lattice* h, double T, int trial, smcx_sched* out, int* threads) {
+  NvtxRange nvtx_range("smcx_autotune");
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
@@ -505,6 +526,7 @@ static void sweep_recorded(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t
 }
 
 int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E) {
+  NvtxRange nvtx_range("smcx_sweep_energies");
   return guarded([&] {
     need(n_sweeps == 0 || E != nullptr, SMCX_E_INVALID_ARG, "NULL energy buffer");
     sweep_recorded(h, T, n_sweeps, seed, E, nullptr, "smcx_sweep_energies");
@@ -512,6 +534,7 @@ int smcx_sweep_energies(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t se
 }
 
 int smcx_sweep_cv(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, int64_t* E, double* moments) {
+  NvtxRange nvtx_range("smcx_sweep_cv");
   return guarded([&] {
     need(n_sweeps >= 1, SMCX_E_INVALID_ARG, "the specific heat needs n_sweeps >= 1");
     need(moments != nullptr, SMCX_E_INVALID_ARG, "NULL moments buffer");
@@ -520,6 +543,7 @@ int smcx_sweep_cv(smcx_lattice* h, double T, int64_t n_sweeps, uint64_t seed, in
 }
 
 int smcx_sweep_partial(smcx_lattice* h, double T, uint64_t seed, int n_colours) {
+  NvtxRange nvtx_range("smcx_sweep_partial");
   return guarded([&] {
     need(h != nullptr, SMCX_E_INVALID_ARG, "NULL handle");
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi before smcx_sweep_partial");
@@ -544,6 +568,7 @@ int smcx_pair_counts(smcx_lattice* h, int64_t* C) {
 }
 
 int smcx_energy(smcx_lattice* h, int64_t* E) {
+  NvtxRange nvtx_range("smcx_energy");
   return guarded([&] {
     need(h && E, SMCX_E_INVALID_ARG, "NULL argument");
     need(h->have_epi, SMCX_E_NO_EPI, "call smcx_set_epi first");
@@ -701,3 +726,24 @@ int smcx_lattice_info(const smcx_lattice* h, int* kind, int* dims, int* M, int* 
 }
 
 }  // extern "C"
+
+int smcx_debug_status(uint64_t* info) {
+  return guarded([&] {
+    need(info != nullptr, SMCX_E_INVALID_ARG, "NULL argument");
+#ifdef SMCX_DEBUG
+    check_cuda(cudaDeviceSynchronize(), "debug status sync");
+    info[0] = 0;
+    info[1] = 0;
+    for (auto rd : dbg::readers()) {
+      unsigned long long w[2] = {0ull, 0ull};
+      if (rd(w) != 0) fail(SMCX_E_CUDA, "debug status read failed");
+      if (info[0] == 0 && w[0] != 0) {
+        info[0] = w[0];
+        info[1] = w[1];
+      }
+    }
+#else
+    fail(SMCX_E_UNSUPPORTED, "not a debug build (build with SMCX_DEBUG=1)");
+#endif
+  });
+}

@@ -39,7 +39,11 @@ __global__ void __launch_bounds__(256) k_pair_counts(const SweepParams P, unsign
           const long long t =
               (((long long)wrap_add(z, d[2], nz) * ny + wrap_add(y, d[1], ny)) * nx + wrap_add(x, d[0], nx)) * m +
               d[3];
-          atomicAdd(&hist[(k * M + p) * M + load_site(P.sites, t, P.storage)], 1u);
+          const int bin = (k * M + p) * M + load_site(P.sites, t, P.storage);
+#ifdef SMCX_DEBUG
+          if (!dbg::in_bounds(bin, KMM, kDbgPairHist)) continue;
+#endif
+          atomicAdd(&hist[bin], 1u);
         }
       }
     }

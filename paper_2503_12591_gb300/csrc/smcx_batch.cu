@@ -610,6 +610,7 @@ int smcx_batch_destroy(smcx_batch* b) {
 }
 
 int smcx_batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed) {
+  NvtxRange nvtx_range("smcx_batch_sweep");
   return guarded_call([&] {
     need_(b && T, SMCX_E_INVALID_ARG, "NULL argument");
     need_(n_sweeps >= 0, SMCX_E_INVALID_ARG, "negative sweep count");
@@ -618,6 +619,7 @@ int smcx_batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t 
 }
 
 int smcx_batch_autotune(smcx_batch* b, const double* T, int trial_sweeps, int* threads) {
+  NvtxRange nvtx_range("smcx_batch_autotune");
   return guarded_call([&] {
     need_(b && T, SMCX_E_INVALID_ARG, "NULL argument");
     need_(trial_sweeps >= 1, SMCX_E_INVALID_ARG, "trial_sweeps must be >= 1");
@@ -637,6 +639,7 @@ int smcx_batch_energy(smcx_batch* b, int64_t* E) {
 
 int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, int64_t n_rounds,
                         int64_t sweeps_per_round, uint64_t seed, uint64_t* round_ctr, int64_t* accepts) {
+  NvtxRange nvtx_range("smcx_batch_exchange");
   return guarded_call([&] {
     need_(b && T_slot && slot_rep && round_ctr, SMCX_E_INVALID_ARG, "NULL argument");
     need_(n_rounds >= 0 && sweeps_per_round >= 0, SMCX_E_INVALID_ARG, "negative round or sweep count");
@@ -645,6 +648,7 @@ int smcx_batch_exchange(smcx_batch* b, const double* T_slot, int32_t* slot_rep, 
 }
 
 int smcx_batch_fluct_accumulate(smcx_batch* b, int shell, double* d_acc) {
+  NvtxRange nvtx_range("smcx_batch_fluct_accumulate");
   return guarded_call([&] {
     need_(b && d_acc, SMCX_E_INVALID_ARG, "NULL argument");
     batch_fluct_accumulate(b, shell, d_acc);

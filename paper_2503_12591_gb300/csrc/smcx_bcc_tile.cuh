@@ -89,7 +89,7 @@ struct LatDesc {
   uint32_t seed_lo, seed_hi;
   unsigned long long sweep;     // cumulative index of the first sweep of the call
   int M;                        // species count (pair counting)
-  int proposal;                 // 0: direction per trial; 1: per (sweep, tile, intra colour)
+  int proposal;                 // 0: direction per trial; 1: per (sweep, tile, intra colour); 2: per block
 };
 
 // 50 BCC neighbour vectors (half units) of shells 1..4 with their shell.
@@ -146,7 +146,7 @@ __device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[
   for (int j = 0; j < T.n; j++) {
     const int k = T.v[j].k;
     if (k >= K) continue;
-    const uint32_t v = box[c + nb_offset(B, T.v[j].x, T.v[j].y, T.v[j].z)];
+    const uint32_t v = ld_chk(box, c + nb_offset(B, T.v[j].x, T.v[j].y, T.v[j].z), 2 * SUB, kDbgBccBox);
     if (NW == 1) {
       const uint32_t one = 1u << v;
       if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   // shell-1 vector (+-1,+-1,+-1): bit 2 -> x, bit 1 -> y, bit 0 -> z
   const int dx = ((dir >> 2) & 1) - 1 + B, dy = ((dir >> 1) & 1) - 1 + B, dz = (dir & 1) - 1 + B;
   const int sp = s + (1 - 2 * B) * SUB + dz * PP + dy * PX + dx;
-  const uint32_t a8 = box[s], b8 = box[sp];
+  const uint32_t a8 = ld_chk(box, s, 2 * SUB, kDbgBccBox), b8 = ld_chk(box, sp, 2 * SUB, kDbgBccBox);
   if (a8 == b8) {
     same++;
     return;
@@ -233,8 +233,8 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
   }
   const int dE = Gb - Ga;
   if (metropolis_accept(dE, ru, sA, nA, sB)) {
-    box[s] = (uint8_t)b8;
-    box[sp] = (uint8_t)a8;
+    st_chk(box, s, 2 * SUB, kDbgBccBox, (uint8_t)b8);
+    st_chk(box, sp, 2 * SUB, kDbgBccBox, (uint8_t)a8);
     acc++;
     dsum += dE;
   }
@@ -329,8 +329,8 @@ __device__ __forceinline__ void finish_trial(uint8_t* box, int s, int sp, uint32
   }
   const int dE = Gb - Ga;
   if (metropolis_accept(dE, ru, sA, nA, sB)) {
-    box[s] = (uint8_t)b8;
-    box[sp] = (uint8_t)a8;
+    st_chk(box, s, 2 * SUB, kDbgBccBox, (uint8_t)b8);
+    st_chk(box, sp, 2 * SUB, kDbgBccBox, (uint8_t)a8);
     acc++;
     dsum += dE;
   }
@@ -370,11 +370,15 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
   if (PROP == 1) {
+    // per (sweep, tile, phase) (mode 1) or per (sweep, colour, block of two
+    // tiles, phase) (mode 2)
     const unsigned tile = (unsigned)((ti[2] * D.nt[1] + ti[1]) * D.nt[0] + ti[0]);
     for (int pr = tid; pr < D.L * D.L * D.L; pr += nth) {
-      const uint4 r = phase_direction_block(D.seed_lo, D.seed_hi, sweep, D.replica, tile, pr);
-      s_dir[2 * pr] = (uint8_t)(r.x >> 29);
-      s_dir[2 * pr + 1] = (uint8_t)(r.z >> 29);
+      const uint4 r = D.proposal == 2 ? block_direction_block(D.seed_lo, D.seed_hi, sweep, D.replica, tc,
+                                                              (unsigned)jt >> 1, pr)
+                                      : phase_direction_block(D.seed_lo, D.seed_hi, sweep, D.replica, tile, pr);
+      st_chk(s_dir, 2 * pr, 512, kDbgBccDir, (uint8_t)(r.x >> 29));
+      st_chk(s_dir, 2 * pr + 1, 512, kDbgBccDir, (uint8_t)(r.z >> 29));
     }
   }
 
@@ -388,6 +392,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   constexpr int U = 8;
   const int rows = ey * ez;
   const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
+  const long long ncell = (long long)nx * ny * nz;
   for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
     uint32_t v[U];
 #pragma unroll
@@ -398,8 +403,9 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
         const int ys = row % ey, zs = row / ey;
         const long long cell =
             ((long long)wrap_add(t0[2] - h, zs, nz) * ny + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
-        v[u] = D.storage == SMCX_INT8 ? (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell))
-                                      : (uint32_t)D.sites[cell];
+        v[u] = D.storage == SMCX_INT8
+                   ? (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(D.sites), cell, ncell, kDbgSite)
+                   : (uint32_t)ld_chk(D.sites, cell, ncell, kDbgSite);
       }
     }
 #pragma unroll
@@ -410,8 +416,8 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
         const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
         const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
         const int bi = zs * PP + ys * PX + lane;
-        box[bi] = (uint8_t)(s0 << 3);
-        box[SUB + bi] = (uint8_t)(s1 << 3);
+        st_chk(box, bi, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
+        st_chk(box, SUB + bi, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
       }
     }
   }
@@ -451,8 +457,8 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
             keep_u[j] = rw.w;
             const int s = (zr + h) * PP + (yr + h) * PX + (xr + h);
             if (PROP == 1)
-              trial_shared_dir<0, K, NW, PL>(box, s, s_dir[((cz * L + cy) * L + cx) * 2], rw.y, Q, D.nA, sA, sB, acc,
-                                             same, dsum);
+              trial_shared_dir<0, K, NW, PL>(box, s, ld_chk(s_dir, ((cz * L + cy) * L + cx) * 2, 512, kDbgBccDir),
+                                             rw.y, Q, D.nA, sA, sB, acc, same, dsum);
             else
               trial<0, K, NW, PL>(box, s, rw.x, rw.y, Q, D.nA, sA, sB, acc, same, dsum);
           }
@@ -464,8 +470,9 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
           if (slot[j] && xr < ts[0] && yr < ts[1] && zr < ts[2]) {
             const int s = (zr + h) * PP + (yr + h) * PX + (xr + h);
             if (PROP == 1)
-              trial_shared_dir<1, K, NW, PL>(box, SUB + s, s_dir[((cz * L + cy) * L + cx) * 2 + 1], keep_u[j], Q,
-                                             D.nA, sA, sB, acc, same, dsum);
+              trial_shared_dir<1, K, NW, PL>(box, SUB + s,
+                                             ld_chk(s_dir, ((cz * L + cy) * L + cx) * 2 + 1, 512, kDbgBccDir),
+                                             keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
             else
               trial<1, K, NW, PL>(box, SUB + s, keep_d[j], keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
           }
@@ -483,12 +490,13 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
       const int gx = wrap_add(t0[0] - 1, xw, nx);
       const long long cell = rbase + gx;
       const int bi = (zw + h - 1) * PP + (yw + h - 1) * PX + (xw + h - 1);
-      const uint32_t s0 = box[bi] >> 3, s1 = box[SUB + bi] >> 3;
+      const uint32_t s0 = ld_chk(box, bi, 2 * SUB, kDbgBccWrite) >> 3;
+      const uint32_t s1 = ld_chk(box, SUB + bi, 2 * SUB, kDbgBccWrite) >> 3;
       if (D.storage == SMCX_INT8) {
-        D.sites[2 * cell] = (uint8_t)s0;
-        D.sites[2 * cell + 1] = (uint8_t)s1;
+        st_chk(D.sites, 2 * cell, 2 * ncell, kDbgSite, (uint8_t)s0);
+        st_chk(D.sites, 2 * cell + 1, 2 * ncell, kDbgSite, (uint8_t)s1);
       } else {
-        D.sites[cell] = (uint8_t)(s0 | (s1 << 4));
+        st_chk(D.sites, cell, ncell, kDbgSite, (uint8_t)(s0 | (s1 << 4)));
       }
     }
   }

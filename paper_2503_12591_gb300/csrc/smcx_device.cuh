@@ -7,6 +7,59 @@
 
 namespace smcx {
 
+// ---- SMCX_DEBUG: in-kernel bounds checks --------------------------------
+// Built with -DSMCX_DEBUG (the library's debug build, libsmcx_debug.so), the
+// checked accesses below test their index against the buffer's extent; an
+// index outside it skips the access (a load returns 0) and records a tag and
+// the index in this translation unit's device status words, which
+// smcx_debug_status reads and clears.  Nothing traps or returns early, so
+// every barrier of the kernel is still reached.  In the normal build the
+// helpers are the plain access.
+enum DebugTag : unsigned {
+  kDbgBccBox = 1,      // BCC tile pass: trial loads and stores in the box
+  kDbgBccStage = 2,    // BCC tile pass: staging stores
+  kDbgBccWrite = 3,    // BCC tile pass: write-back loads from the box
+  kDbgBccDir = 4,      // BCC tile pass: phase-direction table
+  kDbgTileBox = 5,     // generic tile sweep: box accesses
+  kDbgFccBox = 6,      // FCC tile pass: box accesses
+  kDbgPairHist = 7,    // pair counts: histogram bin
+  kDbgSite = 8,        // global-memory kernels: site index
+  kDbgQsroBox = 9,     // qSRO tile passes: box accesses
+};
+#ifdef SMCX_DEBUG
+namespace dbg {
+static __device__ unsigned long long g_status[2];  // tag of the first failure, its index
+__device__ __forceinline__ bool in_bounds(long long i, long long n, unsigned tag) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(&g_status[0], 0ull, (unsigned long long)tag) == 0ull) g_status[1] = (unsigned long long)i;
+  return false;
+}
+// Host reader of this translation unit's status words (registered below).
+static int read_and_clear(unsigned long long* out) {
+  const unsigned long long zero[2] = {0ull, 0ull};
+  if (cudaMemcpyFromSymbol(out, g_status, sizeof(zero)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_status, zero, sizeof(zero)) != cudaSuccess) return -1;
+  return 0;
+}
+int register_reader(int (*reader)(unsigned long long*));  // smcx_api.cu
+static const int g_registered = register_reader(&read_and_clear);
+}  // namespace dbg
+#endif
+template <class T, class I>
+__device__ __forceinline__ T ld_chk(const T* p, I i, I n, unsigned tag) {
+#ifdef SMCX_DEBUG
+  if (!dbg::in_bounds((long long)i, (long long)n, tag)) return T(0);
+#endif
+  return p[i];
+}
+template <class T, class I>
+__device__ __forceinline__ void st_chk(T* p, I i, I n, unsigned tag, T v) {
+#ifdef SMCX_DEBUG
+  if (!dbg::in_bounds((long long)i, (long long)n, tag)) return;
+#endif
+  p[i] = v;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32 -> 64-bit multiplies with a word permutation and key xor; the key is
 // bumped by the Weyl constants between rounds.
@@ -54,6 +107,23 @@ __device__ __forceinline__ uint4 phase_direction_block(uint32_t seed_lo, uint32_
 __device__ __forceinline__ int phase_direction(uint32_t seed_lo, uint32_t seed_hi, unsigned long long sweep, int rep,
                                                unsigned tile, int ic, int z1) {
   const uint4 r = phase_direction_block(seed_lo, seed_hi, sweep, rep, tile, ic >> 1);
+  return (int)__umulhi((ic & 1) ? r.z : r.x, (uint32_t)z1);
+}
+
+// Block-shared proposals: the shell-1 direction of phase ic shared by the
+// tiles of one block (a pair of consecutive tiles of colour tc, numbered in
+// launch order (jz, jy, jx) within the colour): Philox counter (block | tc <<
+// 28, (ic >> 1) | replica << 16, sweep lo, sweep hi | 2^29), key = seed;
+// word 0 (even ic) or word 2 (odd ic); floor(word * z1 / 2^32).
+__device__ __forceinline__ uint4 block_direction_block(uint32_t seed_lo, uint32_t seed_hi, unsigned long long sweep,
+                                                       int rep, int tc, unsigned block, int ic_pair) {
+  return philox4x32_10(make_uint4(block | ((uint32_t)tc << 28), (uint32_t)ic_pair | ((uint32_t)rep << 16),
+                                  (uint32_t)sweep, (uint32_t)(sweep >> 32) | 0x20000000u),
+                       make_uint2(seed_lo, seed_hi));
+}
+__device__ __forceinline__ int block_direction(uint32_t seed_lo, uint32_t seed_hi, unsigned long long sweep, int rep,
+                                               int tc, unsigned block, int ic, int z1) {
+  const uint4 r = block_direction_block(seed_lo, seed_hi, sweep, rep, tc, block, ic >> 1);
   return (int)__umulhi((ic & 1) ? r.z : r.x, (uint32_t)z1);
 }
 

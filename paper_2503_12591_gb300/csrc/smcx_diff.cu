@@ -31,9 +31,16 @@ __global__ void __launch_bounds__(256) k_pair_counts_batch(const int8_t* __restr
   for (long long b = blockIdx.x; b < B; b += gridDim.x) {
     for (int i = threadIdx.x; i < KMM; i += blockDim.x) hist[i] = 0;
     const int8_t* c = cfg + b * N;
-    for (long long i = threadIdx.x; i < N; i += blockDim.x) s[i] = c[i];
-    __syncthreads();
-    for (long long cell = threadIdx.x; cell < (long long)nx * ny * nz; cell += blockDim.x) {
+    int bad = 0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+      const int8_t v = c[i];
+      s[i] = v;
+      bad |= (v < 0 || v >= M);
+    }
+    // a configuration holding an id outside 0..M-1 is not counted (its bins
+    // would lie outside the histogram); all its counts are set to -1
+    bad = __syncthreads_or(bad);
+    for (long long cell = threadIdx.x; !bad && cell < (long long)nx * ny * nz; cell += blockDim.x) {
       const int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((long long)nx * ny));
 #pragma unroll
       for (int bsub = 0; bsub < m; bsub++) {
@@ -53,7 +60,7 @@ __global__ void __launch_bounds__(256) k_pair_counts_batch(const int8_t* __restr
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < KMM; i += blockDim.x) out[b * KMM + i] = (long long)hist[i];
+    for (int i = threadIdx.x; i < KMM; i += blockDim.x) out[b * KMM + i] = bad ? -1ll : (long long)hist[i];
     __syncthreads();
   }
 }

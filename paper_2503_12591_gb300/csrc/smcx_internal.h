@@ -26,6 +26,19 @@ constexpr int kMaxSweepM = 8;     // species supported by the sweep kernels
 constexpr double kBoltzmannMeV = 8.617333262e-2;  // k_B in meV/K (exact SI)
 
 // ---------------------------------------------------------------------------
+// NVTX: every sweep-type entry point opens a range named after itself for the
+// whole call (argument checks included), so that a profiler or an NVTX
+// injection library sees where each call's GPU work was enqueued.  Header-only
+// NVTX v3: without an attached tool every push and pop is a no-op.
+// ---------------------------------------------------------------------------
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// ---------------------------------------------------------------------------
 // Status plumbing: every C entry point catches and converts to an SMCX_E_*.
 // ---------------------------------------------------------------------------
 struct SmcxException {

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
   int* s_poff = s_off + m * NV;
   int* s_psub = s_poff + m * Z1;
   int8_t* box = reinterpret_cast<int8_t*>(s_psub + m * Z1);
+  [[maybe_unused]] const int nbox = P.BX * P.BY * P.BZ * m;  // box bytes (bounds checks of the debug build)
 
   // tile of this CTA: tile colour bits give the parity on each axis
   int bid = blockIdx.x;
@@ -121,10 +122,13 @@ __global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
       const int dir = P.proposal == 1
                           ? phase_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica,
                                             (unsigned)((ti[2] * P.nt[1] + ti[1]) * P.nt[0] + ti[0]), ic, Z1)
+                      : P.proposal == 2
+                          ? block_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica, P.tc, (unsigned)blockIdx.x >> 1,
+                                            ic, Z1)
                           : (int)__umulhi(rd, (uint32_t)Z1);
       const int sp = s + s_poff[b * Z1 + dir];
       const int bp = s_psub[b * Z1 + dir];
-      const int sa = box[s], sb = box[sp];
+      const int sa = ld_chk(box, s, nbox, kDbgTileBox), sb = ld_chk(box, sp, nbox, kDbgTileBox);
       if (sa == sb) {
         same++;
         continue;
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
         for (int k = 0; k < K; k++) {
 #pragma unroll
           for (int q = 0; q < shell_size(KIND, k); q++, j++) {
-            const uint32_t c = (uint32_t)box[s + s_off[b * NV + j]];
+            const uint32_t c = (uint32_t)ld_chk(box, s + s_off[b * NV + j], nbox, kDbgTileBox);
             const uint32_t one = 1u << (8 * (c & 3));
             if (NW == 1 || c < 4) hc[k][0] += one;
             else hc[k][NW - 1] += one;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
         for (int k = 0; k < K; k++) {
 #pragma unroll
           for (int q = 0; q < shell_size(KIND, k); q++, j++) {
-            const uint32_t c = (uint32_t)box[sp + s_off[bp * NV + j]];
+            const uint32_t c = (uint32_t)ld_chk(box, sp + s_off[bp * NV + j], nbox, kDbgTileBox);
             const uint32_t one = 1u << (8 * (c & 3));
             if (NW == 1 || c < 4) hc[k][0] -= one;
             else hc[k][NW - 1] -= one;
@@ -168,8 +172,8 @@ __global__ void __launch_bounds__(512) k_tile_sweep(const SweepParams P) {
         for (int c = 0; c < 4 * NW; c++)
           if (c < M) dE += ((int)((hc[k][c >> 2] >> (8 * (c & 3))) & 0xFFu) - 0x80) * W[k * M + c];
       if (metropolis_accept(dE, ru, s_A, P.nA, s_B)) {
-        box[s] = (int8_t)sb;
-        box[sp] = (int8_t)sa;
+        st_chk(box, s, nbox, kDbgTileBox, (int8_t)sb);
+        st_chk(box, sp, nbox, kDbgTileBox, (int8_t)sa);
         acc++;
         dsum += dE;
       }
@@ -232,8 +236,9 @@ __global__ void __launch_bounds__(256) k_linkcell_sweep(const SweepParams P) {
     const uint4 rw = attempt_block(gid, P.sweep, P.replica, P.seed_lo, P.seed_hi);
     const uint32_t rd = (gid & 1) ? rw.z : rw.x;
     const uint32_t ru = (gid & 1) ? rw.w : rw.y;
-    const int dir = P.proposal == 1 ? phase_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica, 0u, P.ic, Z1)
-                                    : (int)__umulhi(rd, (uint32_t)Z1);
+    const int dir = P.proposal == 1   ? phase_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica, 0u, P.ic, Z1)
+                    : P.proposal == 2 ? block_direction(P.seed_lo, P.seed_hi, P.sweep, P.replica, 0, 0u, P.ic, Z1)
+                                      : (int)__umulhi(rd, (uint32_t)Z1);
     const signed char* pd = P.gp[b][dir];
     const int px = wrap_add(x, pd[0], nx), py = wrap_add(y, pd[1], ny), pz = wrap_add(z, pd[2], nz);
     const int pb = pd[3];

@@ -29,7 +29,7 @@ int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes) {
 bool bcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;
   if (hd->kind != kBCC || hd->M > kMaxSweepM || !hd->have_epi) return false;
-  if (hd->proposal == 1) {
+  if (hd->proposal != 0) {
     // one compiled variant: 4 shells, M <= 4, |V| < 2^15, one slot per thread
     if (hd->shells.K != 4 || hd->M > 4) return false;
     for (int32_t v : hd->V)
@@ -45,7 +45,7 @@ bool bcc_fast_usable(const smcx_lattice* hd) {
     if (tmax + 4 > bccfast::BOX) return false;
     nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
   }
-  if (hd->proposal == 1 && nq * nq * nq > 128) return false;  // one slot per thread
+  if (hd->proposal != 0 && nq * nq * nq > 128) return false;  // one slot per thread
   // four slots per thread are compiled for 4 shells, M <= 4, two planes only
   if (nq * nq * nq > 256) {
     if (hd->shells.K != 4 || hd->M > 4) return false;
@@ -82,7 +82,7 @@ void sweep_bcc_dir(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes&
 static void dispatch(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int nw, int pl,
                      int threads, int slots, int64_t n, int nc) {
   const int K = hd->shells.K;
-  if (D.proposal == 1) return sweep_bcc_dir(hd, D, Q, threads, n, nc);
+  if (D.proposal != 0) return sweep_bcc_dir(hd, D, Q, threads, n, nc);
   if (K == 4) {
     if (nw == 1 && pl == 2) {
       if (slots == 1) return launch_bcc<4, 1, 2, 1>(hd, D, Q, threads, n, nc);

@@ -18,7 +18,7 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
                                  long long& dsum) {
   constexpr UTable T = make_union7<K>();
   const int sp = s + c_union.poff[B][dir];
-  const uint32_t a8 = box[s], b8 = box[sp];
+  const uint32_t a8 = ld_chk(box, s, 2 * SUB, kDbgBccBox), b8 = ld_chk(box, sp, 2 * SUB, kDbgBccBox);
   if (a8 == b8) {
     same++;
     return;
@@ -29,7 +29,7 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
   const int* off = c_union.off[B][dir];
 #pragma unroll
   for (int j = 0; j < T.n; j++) {
-    const uint32_t v = box[s + off[j]];
+    const uint32_t v = ld_chk(box, s + off[j], 2 * SUB, kDbgBccBox);
     uint32_t one;
     asm("shl.b32 %0, 1, %1;" : "=r"(one) : "r"(v));
     if (T.e[j].k1 >= 0) h[T.e[j].k1][0] += one;

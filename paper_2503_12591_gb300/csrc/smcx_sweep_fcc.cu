@@ -82,7 +82,7 @@ __device__ __forceinline__ void gather(const uint8_t* box, int c, uint32_t (&h)[
   for (int j = 0; j < T.n; j++) {
     const int k = T.v[j].k;
     if (k >= K) continue;
-    const uint32_t v = box[c + hoff(T.v[j].x, T.v[j].y, T.v[j].z)];
+    const uint32_t v = ld_chk(box, c + hoff(T.v[j].x, T.v[j].y, T.v[j].z), BOX_BYTES, kDbgFccBox);
     if (NW <= 1) {
       const uint32_t one = 1u << v;
       if (SIGN > 0) h[k][0] += one; else h[k][0] -= one;
@@ -136,8 +136,8 @@ __device__ __forceinline__ void finish_rows(uint8_t* box, int s, int sp, uint32_
   }
   const int dE = (gb0 + (gb1 << 8) + (gb2 << 16)) - (ga0 + (ga1 << 8) + (ga2 << 16));
   if (metropolis_accept(dE, ru, sA, nA, sB)) {
-    box[s] = (uint8_t)b8;
-    box[sp] = (uint8_t)a8;
+    st_chk(box, s, BOX_BYTES, kDbgFccBox, (uint8_t)b8);
+    st_chk(box, sp, BOX_BYTES, kDbgFccBox, (uint8_t)a8);
     acc++;
     dsum += dE;
   }
@@ -173,8 +173,8 @@ __device__ __forceinline__ void finish_six(uint8_t* box, int s, int sp, uint32_t
     for (int c = 0; c < 5; c++) e += (uint32_t)row[k * 5 + c] * ((h[k][0] >> (6 * c)) & 63u);
   const int dE = (int)e;
   if (metropolis_accept(dE, ru, sA, nA, sB)) {
-    box[s] = (uint8_t)b6;
-    box[sp] = (uint8_t)a6;
+    st_chk(box, s, BOX_BYTES, kDbgFccBox, (uint8_t)b6);
+    st_chk(box, sp, BOX_BYTES, kDbgFccBox, (uint8_t)a6);
     acc++;
     dsum += dE;
   }
@@ -186,7 +186,7 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
                                       const uint32_t* sB, unsigned& acc, unsigned& same, long long& dsum) {
   const int dir = (int)__umulhi(rd, 12u);
   const int sp = s + s_poff[dir];
-  const uint32_t a8 = box[s], b8 = box[sp];
+  const uint32_t a8 = ld_chk(box, s, BOX_BYTES, kDbgFccBox), b8 = ld_chk(box, sp, BOX_BYTES, kDbgFccBox);
   if (a8 == b8) {
     same++;
     return;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
 #pragma unroll
           for (int b = 0; b < 4; b++) {
             const uint32_t sp = D.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
-            box[base + boff(b)] = (uint8_t)(NW == 0 ? sp * 6 : sp << 3);
+            st_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox, (uint8_t)(NW == 0 ? sp * 6 : sp << 3));
           }
         }
       }
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
       uint32_t s4[4];
 #pragma unroll
       for (int b = 0; b < 4; b++) {
-        const uint32_t v = box[base + boff(b)];
+        const uint32_t v = ld_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox);
         s4[b] = NW == 0 ? (uint32_t)species6(v) : v >> 3;
       }
       if (D.storage == SMCX_INT8) {

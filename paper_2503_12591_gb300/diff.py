@@ -20,7 +20,8 @@ def _stream():
 
 
 def pair_counts(configs: torch.Tensor, kind: int, dims, M: int, K: int) -> torch.Tensor:
-    """Ordered pair counts int64 [B, K, M, M] of int8 configurations [B, N]."""
+    """Ordered pair counts int64 [B, K, M, M] of int8 configurations [B, N]
+    (a configuration holding an id outside 0..M-1 comes back as all -1)."""
     assert configs.is_cuda and configs.dtype == torch.int8 and configs.is_contiguous()
     B = configs.shape[0]
     out = torch.empty((B, K, M, M), dtype=torch.int64, device=configs.device)

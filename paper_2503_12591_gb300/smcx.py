@@ -10,12 +10,14 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libsmcx.so")
+# SMCX_DEBUG=1 loads the debug build (in-kernel bounds checks, see
+# smcx_debug_status); otherwise the normal library.
+LIB_PATH = os.path.join(HERE, "_build", "libsmcx_debug.so" if os.environ.get("SMCX_DEBUG") == "1" else "libsmcx.so")
 
 BCC, FCC = 0, 1
 INT8, PACKED4 = 0, 1
 KERNEL_AUTO, KERNEL_GENERIC = 0, 1
-PROPOSAL_SITE, PROPOSAL_TILE = 0, 1
+PROPOSAL_SITE, PROPOSAL_TILE, PROPOSAL_BLOCK = 0, 1, 2
 NA_MAX, NB = 4096, 1024
 
 OK = 0
@@ -52,6 +54,7 @@ _SIGS = {
     "smcx_set_config_store": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "smcx_sweep_energies": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "smcx_sweep_cv": (C.c_int, [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "smcx_debug_status": (C.c_int, [C.c_void_p]),
     "smcx_probe_lds_rate": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smcx_lattice_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                       C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]),
@@ -114,6 +117,15 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def debug_status():
+    """(tag, index) of the first out-of-bounds access the debug build recorded
+    since the last call, (0, 0) if none; SmcxError(E_UNSUPPORTED) in the
+    normal build."""
+    info = np.zeros(2, np.uint64)
+    _check(lib().smcx_debug_status(_p(info)))
+    return int(info[0]), int(info[1])
 
 
 def probe_lds_rate(stream=None):

@@ -41,6 +41,14 @@ def test_pair_counts_batch(dev, kind, dims, M, K):
     C = diff.pair_counts(torch.from_numpy(cfg).to(dev), kind, dims, M, K).cpu().numpy()
     for b in range(7):
         assert (C[b] == O.pair_counts(kind, dims, M, K, cfg[b])).all()
+    # ids outside 0..M-1 (too large, negative) are refused per configuration
+    bad = cfg.copy()
+    bad[2, 3] = M
+    bad[5, N - 1] = -1
+    C = diff.pair_counts(torch.from_numpy(bad).to(dev), kind, dims, M, K).cpu().numpy()
+    assert (C[2] == -1).all() and (C[5] == -1).all()
+    for b in (0, 1, 3, 4, 6):
+        assert (C[b] == O.pair_counts(kind, dims, M, K, cfg[b])).all()
 
 
 def test_epi_energy_autograd(dev):

@@ -239,6 +239,7 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     assert lat.state()[1].tolist() == rst.tolist()
 
 
+@pytest.mark.parametrize("mode", [smcx.PROPOSAL_TILE, smcx.PROPOSAL_BLOCK], ids=["tile", "block"])
 @pytest.mark.parametrize("kernel", [smcx.KERNEL_AUTO, smcx.KERNEL_GENERIC], ids=["auto", "generic"])
 @pytest.mark.parametrize("case", [
     (smcx.BCC, 4, (20, 20, 20), 4, [0.25] * 4, smcx.PACKED4, (4, (2, 2, 2)), 1200.0, 4),
@@ -246,19 +247,23 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     (smcx.BCC, 4, (18, 16, 20), 3, [0.5, 0.3, 0.2], smcx.PACKED4, (3, (2, 2, 2)), 2000.0, 3),  # L=3: generic
     (smcx.BCC, 2, (12, 12, 12), 4, [0.25] * 4, smcx.INT8, (3, (1, 1, 1)), 1000.0, 3),     # link-cell
     (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 3),
-], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc"])
-def test_shared_direction_proposals(stream, case, kernel):
-    """SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra colour)."""
+    (smcx.BCC, 4, (36, 24, 20), 4, [0.25] * 4, smcx.PACKED4, (4, (6, 4, 2)), 1200.0, 3),  # 3 blocks per colour
+    (smcx.BCC, 4, (29, 18, 18), 4, [0.25] * 4, smcx.INT8, (3, (6, 2, 2)), 900.0, 3),      # odd: last block 1 tile
+], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc", "bcc_blocks", "bcc_odd_blocks"])
+def test_shared_direction_proposals(stream, case, kernel, mode):
+    """SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra colour);
+    SMCX_PROPOSAL_BLOCK: one per (sweep, tile colour, block of two tiles,
+    intra colour)."""
     kind, K, dims, M, comp, storage, sched, T, n = case
     V = epi_gaussian(K, M, 20.0, 12)
     lat = smcx.Lattice(kind, dims, M, comp, init_seed=5, storage=storage, sched=sched, stream=stream)
     lat.set_kernel(kernel)
-    lat.set_proposal(smcx.PROPOSAL_TILE)
+    lat.set_proposal(mode)
     lat.set_replica(3)
     lat.set_epi(V)
     lat.sweep(T, n, 4)
     ref = O.init_config(kind, dims, M, comp, 5)
-    rst = O.sweep(kind, dims, M, K, V, ref, T, n, 4, replica=3, L=sched[0], nt=sched[1], proposal=1)
+    rst = O.sweep(kind, dims, M, K, V, ref, T, n, 4, replica=3, L=sched[0], nt=sched[1], proposal=mode)
     assert (lat.get_config() == ref).all()
     assert lat.state()[1].tolist() == rst.tolist()
 
