@@ -76,6 +76,12 @@ constexpr int MAXPLANES = 3;
 // unsigned, the top plane signed).
 struct Planes {
   uint32_t P[MAXPLANES][kMaxShells][kMaxSweepM][2];
+  // Rows of V differences for shared-direction trials (M <= 4, 4 shells):
+  // R[a * 4 + b][k] holds the low bytes (unsigned), R[a * 4 + b][4 + k] the
+  // high bytes (signed) of T_k[c] = V_k[b][c] - V_k[a][c], c = 0..3; valid
+  // (rows = 1) when every |T| < 2^15.
+  uint32_t R[16][8];
+  int rows;
 };
 
 // One lattice as the tile pass sees it.
@@ -336,6 +342,33 @@ __device__ __forceinline__ void finish_trial(uint8_t* box, int s, int sp, uint32
   }
 }
 
+// dE = sum_k sum_c T_k[c] D_k[c] from the (a, b) row of V differences in
+// shared memory (two 16-byte loads, eight dp4a), and the decision.
+template <int K>
+__device__ __forceinline__ void finish_trial_rows(uint8_t* box, int s, int sp, uint32_t a8, uint32_t b8,
+                                                  const uint32_t (&h)[kMaxShells][2], uint32_t ru,
+                                                  const uint32_t* s_rows, int nA, const uint32_t* sA,
+                                                  const uint32_t* sB, unsigned& acc, long long& dsum) {
+  const int a = (int)(a8 >> 3), b = (int)(b8 >> 3);
+  const uint4* row = reinterpret_cast<const uint4*>(s_rows + (a * 4 + b) * 8);
+  const uint4 lo = row[0], hi = row[1];
+  const uint32_t Lw[4] = {lo.x, lo.y, lo.z, lo.w}, Hw[4] = {hi.x, hi.y, hi.z, hi.w};
+  int dl = 0, dh = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const int d = (int)(h[k][0] ^ 0x80808080u);
+    dl = dp4a_su(d, Lw[k], dl);
+    dh = dp4a_ss(d, Hw[k], dh);
+  }
+  const int dE = dl + (dh << 8);
+  if (metropolis_accept(dE, ru, sA, nA, sB)) {
+    st_chk(box, s, 2 * SUB, kDbgBccBox, (uint8_t)b8);
+    st_chk(box, sp, 2 * SUB, kDbgBccBox, (uint8_t)a8);
+    acc++;
+    dsum += dE;
+  }
+}
+
 // One tile pass: stage the tile of colour `tc` with index `jt` among the
 // tiles of that colour (plus its 2-cell halo) into shared memory, run every
 // intra-colour phase of the tile, write the tile and its 1-cell partner ring
@@ -344,8 +377,8 @@ __device__ __forceinline__ void finish_trial(uint8_t* box, int s, int sp, uint32
 // Shared-direction trial; defined where the offset table lives
 // (smcx_sweep_bcc_dir.cu).
 template <int B, int K, int NW, int PL>
-__device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, const Planes& P, int nA,
-                                 const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
+__device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, const Planes& P, const uint32_t* s_rows,
+                                 int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
                                  long long& dsum);
 
 template <int K, int NW, int PL, int SLOTS, int PROP = 0>
@@ -353,6 +386,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
                                               unsigned long long sweep, uint8_t* box, uint32_t* sA, uint32_t* sB,
                                               unsigned long long* s_stat) {
   __shared__ uint8_t s_dir[512];  // phase directions (shared-direction proposals)
+  __shared__ __align__(16) uint32_t s_rows[PROP == 1 ? 128 : 4];  // V-difference rows (shared-direction)
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int ntc0 = D.nt[0] / 2, ntc1 = D.nt[1] / 2;
@@ -370,6 +404,8 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
   if (PROP == 1) {
+    if (Q.rows)
+      for (int i = tid; i < 128; i += nth) s_rows[i] = Q.R[i >> 3][i & 7];
     // per (sweep, tile, phase) (mode 1) or per (sweep, colour, block of two
     // tiles, phase) (mode 2)
     const unsigned tile = (unsigned)((ti[2] * D.nt[1] + ti[1]) * D.nt[0] + ti[0]);
@@ -458,7 +494,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
             const int s = (zr + h) * PP + (yr + h) * PX + (xr + h);
             if (PROP == 1)
               trial_shared_dir<0, K, NW, PL>(box, s, ld_chk(s_dir, ((cz * L + cy) * L + cx) * 2, 512, kDbgBccDir),
-                                             rw.y, Q, D.nA, sA, sB, acc, same, dsum);
+                                             rw.y, Q, s_rows, D.nA, sA, sB, acc, same, dsum);
             else
               trial<0, K, NW, PL>(box, s, rw.x, rw.y, Q, D.nA, sA, sB, acc, same, dsum);
           }
@@ -472,7 +508,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
             if (PROP == 1)
               trial_shared_dir<1, K, NW, PL>(box, SUB + s,
                                              ld_chk(s_dir, ((cz * L + cy) * L + cx) * 2 + 1, 512, kDbgBccDir),
-                                             keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
+                                             keep_u[j], Q, s_rows, D.nA, sA, sB, acc, same, dsum);
             else
               trial<1, K, NW, PL>(box, SUB + s, keep_d[j], keep_u[j], Q, D.nA, sA, sB, acc, same, dsum);
           }

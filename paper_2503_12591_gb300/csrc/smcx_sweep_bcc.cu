@@ -14,6 +14,22 @@ int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes) {
   long long vmax = 0;
   for (int32_t v : hd->V) vmax = std::max(vmax, std::llabs((long long)v));
   const int PL = std::max(min_planes, vmax < 32768 ? 2 : 3);
+  // V-difference rows for shared-direction trials (M <= 4, 4 shells)
+  Q->rows = (M <= 4 && K == 4) ? 1 : 0;
+  for (int a = 0; a < 4 && Q->rows; a++)
+    for (int b = 0; b < 4 && Q->rows; b++)
+      for (int k = 0; k < 4 && Q->rows; k++)
+        for (int c = 0; c < 4; c++) {
+          const long long vb = (b < M && c < M) ? hd->V[((size_t)k * M + b) * M + c] : 0;
+          const long long va = (a < M && c < M) ? hd->V[((size_t)k * M + a) * M + c] : 0;
+          const long long T = vb - va;
+          if (T < -32768 || T > 32767) {
+            Q->rows = 0;
+            break;
+          }
+          Q->R[a * 4 + b][k] |= (uint32_t)(T & 0xFF) << (8 * c);
+          Q->R[a * 4 + b][4 + k] |= (uint32_t)((T >> 8) & 0xFF) << (8 * c);
+        }
   for (int k = 0; k < K; k++)
     for (int p = 0; p < M; p++)
       for (int c = 0; c < M; c++) {

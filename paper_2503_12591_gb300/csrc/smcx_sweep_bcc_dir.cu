@@ -13,8 +13,8 @@ namespace bccfast {
 __constant__ UnionOffsets c_union = make_union_offsets();
 
 template <int B, int K, int NW, int PL>
-__device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, const Planes& P, int nA,
-                                 const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
+__device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, const Planes& P, const uint32_t* s_rows,
+                                 int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
                                  long long& dsum) {
   constexpr UTable T = make_union7<K>();
   const int sp = s + c_union.poff[B][dir];
@@ -35,7 +35,10 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
     if (T.e[j].k1 >= 0) h[T.e[j].k1][0] += one;
     if (T.e[j].k2 >= 0) h[T.e[j].k2][0] -= one;
   }
-  finish_trial<K, NW, PL>(box, s, sp, a8, b8, h, ru, P, nA, sA, sB, acc, dsum);
+  if (P.rows)
+    finish_trial_rows<K>(box, s, sp, a8, b8, h, ru, s_rows, nA, sA, sB, acc, dsum);
+  else
+    finish_trial<K, NW, PL>(box, s, sp, a8, b8, h, ru, P, nA, sA, sB, acc, dsum);
 }
 
 }  // namespace bccfast

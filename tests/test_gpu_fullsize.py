@@ -6,6 +6,9 @@ times (library-chosen schedule and kernel).
   exact composition; after the first tile colour of a sweep, sampled tiles
   (tile + partner ring) bit-exact against the oracle's single-tile pass; the
   energy change equals the sum of accepted dE; trial count.
+- BCC 800^3 with shared-direction proposals (per tile, as bench.py times
+  the headline; and per block of two tiles): the same first-colour checks
+  against the oracle's single-tile pass in that proposal mode.
 - BCC 256^3 (33.5M sites, int8): one whole sweep bit-exact against the
   oracle (configuration and statistics).
 """
@@ -40,13 +43,16 @@ def _tile_ring_sites(dims, nt, tile, m):
     return np.array(idx, np.int64)
 
 
-@pytest.mark.parametrize("work", [SCALE_BCC800, SCALE_FCC400], ids=lambda w: w.name)
-def test_full_size_first_colour_and_invariants(work):
+@pytest.mark.parametrize("work,mode", [(SCALE_BCC800, smcx.PROPOSAL_SITE), (SCALE_FCC400, smcx.PROPOSAL_SITE),
+                                       (SCALE_BCC800, smcx.PROPOSAL_TILE), (SCALE_BCC800, smcx.PROPOSAL_BLOCK)],
+                         ids=["bcc800", "fcc400", "bcc800_tile", "bcc800_block"])
+def test_full_size_first_colour_and_invariants(work, mode):
     stream = torch.cuda.current_stream()
     kind, dims, M = work.kind, work.dims, work.M
     T, seed = work.temperatures[0], work.seed
     m = 2 if kind == smcx.BCC else 4
     lat = smcx.Lattice(kind, dims, M, work.comp, init_seed=work.init_seed, storage=work.storage, stream=stream)
+    lat.set_proposal(mode)
     V = work.epi()
     lat.set_epi(V)
     L, nt = lat.schedule()
@@ -70,7 +76,7 @@ def test_full_size_first_colour_and_invariants(work):
     rng = np.random.default_rng(5)
     picks = [colour0[i] for i in rng.choice(len(colour0), 2, replace=False)]
     for t in picks:
-        O.tile_pass(kind, dims, M, work.K, V, cfg0, T, seed, 0, 0, L, nt, t)
+        O.tile_pass(kind, dims, M, work.K, V, cfg0, T, seed, 0, 0, L, nt, t, proposal=mode)
         sites = _tile_ring_sites(dims, nt, t, m)
         assert (cfg1[sites] == cfg0[sites]).all(), f"tile {t}"
     lat.close()

@@ -249,7 +249,11 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 3),
     (smcx.BCC, 4, (36, 24, 20), 4, [0.25] * 4, smcx.PACKED4, (4, (6, 4, 2)), 1200.0, 3),  # 3 blocks per colour
     (smcx.BCC, 4, (29, 18, 18), 4, [0.25] * 4, smcx.INT8, (3, (6, 2, 2)), 900.0, 3),      # odd: last block 1 tile
-], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc", "bcc_blocks", "bcc_odd_blocks"])
+    (smcx.BCC, 4, (72, 36, 36), 4, [0.25] * 4, smcx.PACKED4, (3, (4, 2, 2)), 1200.0, 3),  # 18-cell tiles, 6^3 slots
+    (smcx.BCC, 4, (70, 70, 34), 4, [0.25] * 4, smcx.INT8, (3, (4, 4, 2)), 900.0, 2),      # 17-18 cells, 2 blocks
+    (smcx.BCC, 4, (54, 36, 36), 3, [0.5, 0.3, 0.2], smcx.PACKED4, (3, (6, 2, 2)), 1500.0, 2),  # M = 3, odd
+], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc", "bcc_blocks", "bcc_odd_blocks", "bcc_pair18",
+        "bcc_pair_ragged", "bcc_pair_m3"])
 def test_shared_direction_proposals(stream, case, kernel, mode):
     """SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra colour);
     SMCX_PROPOSAL_BLOCK: one per (sweep, tile colour, block of two tiles,
