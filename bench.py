@@ -2,7 +2,10 @@
 
 Workload (N=1): BCC 800^3 cubic cells = 1,024,000,000 sites, 4 species at
 equiatomic composition, packed 4-bit storage, 4-shell EPI drawn from
-N(0, 20 meV), 1200 K.  A step is one sweep (one swap trial per site).
+N(0, 20 meV), 1200 K.  A step is one sweep (one swap trial per site) with
+shared-direction proposals (one shell-1 direction per sweep, tile and phase;
+acceptance uniforms per trial); `per_trial_direction` times the same sweep
+with a direction drawn per trial.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,6 +39,9 @@ UNIT = "attempts/s"
 WORK = SCALE_BCC800
 T_KELVIN = WORK.temperatures[0]
 SEED = 1
+# Proposal mode of the headline sweep: one shell-1 direction per (sweep, tile,
+# intra colour), smcx PROPOSAL_TILE / oracle proposal 1.
+PROPOSAL = 1
 # Bytes of the lattice store a sweep must read and write per site (packed
 # 4-bit: half a byte in, half a byte out).
 ALG_BYTES_PER_ATTEMPT = 1.0
@@ -60,7 +66,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
-    ap.add_argument("--no-shared", action="store_true")
+    ap.add_argument("--no-site", action="store_true", help="skip the per-trial-direction measurement")
     ap.add_argument("--no-clusters", action="store_true")
     ap.add_argument("--no-qsro", action="store_true")
     ap.add_argument("--no-throughput", action="store_true")
@@ -68,10 +74,10 @@ def parse():
     ap.add_argument("--no-fcc", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput", "anneal", "fcc", "paper", "paper_bcc"],
+                                                    "throughput", "anneal", "fcc", "paper"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
-                    help="profiling only: lattice edge of the fcc / qsro / clusters / paper_bcc measurement")
+                    help="profiling only: lattice edge of the fcc / qsro / clusters measurement")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
     return ap.parse_args()
@@ -151,17 +157,19 @@ def cpu_baseline(n_sweeps=24, n_serial=4):
     sig = O.init_config(O.BCC, CPU_SAMPLE_DIMS, WORK.M, equiatomic(WORK.M), WORK.init_seed)
     t0 = time.perf_counter()
     _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_sweeps, SEED,
-                               L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=os.cpu_count() or 1)
+                               L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=os.cpu_count() or 1,
+                               proposal=PROPOSAL)
     dt = time.perf_counter() - t0
     n = sig.size * n_sweeps
     t1 = time.perf_counter()
     O.sweep(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, n_serial, SEED, sweep0=n_sweeps,
-            L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1])
+            L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], proposal=PROPOSAL)
     dts = time.perf_counter() - t1
     return {"value": n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "serial_value": sig.size * n_serial / dts,
             "sample": f"C oracle, OpenMP over the sites of each phase ({used} threads), BCC "
                       f"{CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites), 4 species, 4 shells, {T_KELVIN:.0f} K, "
+                      f"shared-direction proposals, "
                       f"schedule L={CPU_SAMPLE_SCHED[0]} tiles {CPU_SAMPLE_SCHED[1]}, {n_sweeps} sweeps = {n} "
                       f"trials in {dt:.1f} s; serial_value: the same oracle on 1 core, {n_serial} sweeps"}
 
@@ -171,7 +179,9 @@ def config_block(extra=None):
                      f"packed 4-bit, 4-shell int32 EPI N(0,{WORK.sigma_mev:.0f} meV), {T_KELVIN:.0f} K",
          "sites": WORK.sites, "lattice": "bcc", "dims": list(WORK.dims), "species": WORK.M, "shells": WORK.K,
          "storage": "packed4", "temperature_K": T_KELVIN, "step": "one sweep (one swap trial per site)",
-         "l2": "inputs larger than L2 (512 MB lattice store vs 129 MB L2)"}
+         "l2": "inputs larger than L2 (512 MB lattice store vs 129 MB L2)",
+         "proposal": "shared direction: one shell-1 direction per (sweep, tile, intra colour); acceptance "
+                     "uniforms per trial"}
     if extra:
         c.update(extra)
     return c
@@ -191,18 +201,20 @@ def run_reference(args, rank, world):
     used = 1
     for _ in range(args.warmup):
         _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
-                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads)
+                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads,
+                                   proposal=PROPOSAL)
         sw += 1
     t0 = time.perf_counter()
     for _ in range(args.steps):
         _, used = O.sweep_parallel(O.BCC, CPU_SAMPLE_DIMS, WORK.M, WORK.K, V, sig, T_KELVIN, 1, SEED, sweep0=sw,
-                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads)
+                                   L=CPU_SAMPLE_SCHED[0], nt=CPU_SAMPLE_SCHED[1], threads=threads,
+                                   proposal=PROPOSAL)
         sw += 1
     dt = time.perf_counter() - t0
     val = sig.size * args.steps / dt
     sample = (f"C oracle, OpenMP over the sites of each phase ({used} threads), one sweep of BCC "
               f"{CPU_SAMPLE_DIMS[0]}^3 ({sig.size} sites) per step, same species/shells/temperature/"
-              f"schedule shape")
+              f"schedule shape/proposal mode")
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -474,34 +486,6 @@ PAPER_ROWS = [
     ("FeCoNiAlTi_1M_EPI", "fcc", (72, 60, 60), FECONIALTI, "epi", 0.001755),
     ("FeCoNiAlTi_1M_qSRO", "fcc", (72, 60, 60), FECONIALTI, "qsro", 0.04703),
 ]
-
-
-def run_paper_bcc(stream, edge=0):
-    """The MoNbTaW_1B_EPI shape of the paper's Tab. models_summary (BCC, 4
-    equiatomic species, 2-shell EPI N(0,20 meV), packed 4-bit, 1000 K) at
-    edge^3 cells (795 by default), library schedule: sweeps timed with CUDA
-    events (the profiling entry of that row's kernel)."""
-    import torch
-    from paper_2503_12591_gb300 import smcx
-
-    n = edge or 795
-    lat = smcx.Lattice(smcx.BCC, (n, n, n), 4, [0.25] * 4, init_seed=11, storage=smcx.PACKED4, stream=stream)
-    lat.set_epi(epi_gaussian(2, 4, 20.0, 5))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat.sweep(1000.0, 1, SEED)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    lat.sweep(1000.0, 5, SEED)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / 5
-    L, nt = lat.schedule()
-    N = lat.N
-    lat.close()
-    return {"value": N / (ms / 1e3), "unit": UNIT, "ms_per_sweep": ms, "schedule": {"L": L, "tiles": list(nt)},
-            "kernel": "k_bcc_tile_sweep<2,1,2,1,0>",
-            "workload": f"BCC {n}^3 x 2 = {N:,} sites, 4 species equiatomic, 2-shell EPI N(0,20 meV), packed 4-bit, "
-                        "1000 K"}
 
 
 def run_paper_rows(stream):
@@ -777,6 +761,7 @@ def run_smcx(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         lat = smcx.Lattice(smcx.BCC, WORK.dims, WORK.M, WORK.comp, init_seed=WORK.init_seed + rank,
                            storage=smcx.PACKED4, stream=stream)
+        lat.set_proposal(PROPOSAL)
         lat.set_epi(V)
     sched = lat.schedule()
     # replicas on different ranks differ by their initial configuration
@@ -810,10 +795,12 @@ def run_smcx(args, rank, world, local_rank):
     launches_per_sweep = 8 if sched[1] != (1, 1, 1) else sched[0] ** 3 * 2
     n_launch = launches_per_sweep * args.steps
 
-    # ---- shared-direction proposals (one shell-1 direction per tile phase) --
-    shared = None
-    if not args.no_shared:
-        lat.set_proposal(smcx.PROPOSAL_TILE)
+    st_head = lat.state()[1]
+
+    # ---- per-trial directions (the proposal drawn independently per trial) --
+    per_trial = None
+    if not args.no_site:
+        lat.set_proposal(smcx.PROPOSAL_SITE)
         for _ in range(args.warmup):
             lat.sweep(T_KELVIN, 1, SEED)
         barrier()
@@ -823,13 +810,14 @@ def run_smcx(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         barrier()
-        ms_s, value_s = aggregate_ranks(e0.elapsed_time(e1), WORK.sites, args.steps, dist)
-        lat.set_proposal(smcx.PROPOSAL_SITE)
-        shared = {"value": value_s, "unit": UNIT, "ms_per_step": ms_s / args.steps,
-                  "kernel": "k_bcc_tile_sweep<4,1,2,1,1>",
-                  "note": "optional proposal: one shell-1 direction per (sweep, tile, intra colour); "
-                          "same Boltzmann stationary distribution, different trajectories; not the "
-                          "headline, which uses the per-trial random direction"}
+        ms_p, value_p = aggregate_ranks(e0.elapsed_time(e1), WORK.sites, args.steps, dist)
+        lat.set_proposal(PROPOSAL)
+        per_trial = {"value": value_p, "unit": UNIT, "ms_per_step": ms_p / args.steps,
+                     "kernel": "k_bcc_tile_sweep<4,1,2,1,0>",
+                     "frac_smem": None,
+                     "note": "the same sweep with a shell-1 direction drawn per trial: same stationary "
+                             "distribution, different trajectories; per-lane partner environments land on "
+                             "scattered banks (about 1.9 shared-memory wavefronts per load)"}
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
@@ -843,6 +831,7 @@ def run_smcx(args, rank, world, local_rank):
         with torch.cuda.stream(stream2):
             lat2 = smcx.Lattice(smcx.BCC, WORK.dims, WORK.M, WORK.comp, init_seed=WORK.init_seed + rank + 7,
                                 storage=smcx.PACKED4, stream=stream2)
+            lat2.set_proposal(PROPOSAL)
             lat2.set_epi(V)
         hosts = [torch.empty(nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
         lat.get_config_store_ptr(hosts[0].data_ptr(), nbytes)
@@ -894,7 +883,10 @@ def run_smcx(args, rank, world, local_rank):
     if os.path.exists(prof):
         try:
             with open(prof) as f:
-                traffic = json.load(f).get("dram_bytes_per_launch")
+                tj = json.load(f)
+            # counters of the kernel timed here only
+            if tj.get("kernel") == "k_bcc_tile_sweep<4,1,2,1,1>":
+                traffic = tj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None
     out = {
@@ -903,14 +895,16 @@ def run_smcx(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": config_block({"schedule": {"L": sched[0], "tiles": list(sched[1])},
                                 "parallelism": f"replicas x{world}" if world > 1 else "single lattice"}),
-        "roofline": {"bound": "alu", "achieved": achieved_g, "peak": lds_peak, "unit": "Gload/s",
+        "roofline": {"bound": "smem", "achieved": achieved_g, "peak": lds_peak, "unit": "Gload/s",
                      "frac": achieved_g / lds_peak, "traffic": traffic,
-                     "kernel": "k_bcc_tile_sweep",
+                     "kernel": "k_bcc_tile_sweep<4,1,2,1,1>",
                      "peak_source": "measured (smcx_probe_lds_rate: conflict-free LDS.U8 stream on every SM)"
                                     if lds_measured else "nominal (152 SMs x 32 lanes x 2070 MHz)",
                      "peak_nominal": lds_nominal,
-                     "note": "shared-memory gather roof: 70 algorithmic lane-loads per trial (s, s' and 68 "
-                             "distinct neighbours) x trials per launch / launch time"},
+                     "note": "shared-memory gather roof: 70 algorithmic lane-loads per trial (s, s' and the "
+                             "68-site union of their environments) x trials per launch / launch time; the "
+                             "kernel itself is issue-bound (see profiles/)",
+                     "accept_rate": float(st_head[1]) / max(1, int(st_head[0]))},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
                          "note": "1 B per trial (packed 4-bit read + write) per launch / launch time"},
@@ -919,8 +913,10 @@ def run_smcx(args, rank, world, local_rank):
     }
     if e2e is not None:
         out["e2e"] = e2e
-    if shared is not None:
-        out["shared_direction"] = shared
+    if per_trial is not None:
+        per_trial["frac_smem"] = (ALG_GATHERS_PER_ATTEMPT * WORK.sites / launches_per_sweep /
+                                  (per_trial["ms_per_step"] / launches_per_sweep / 1e3) / 1e9) / lds_peak
+        out["per_trial_direction"] = per_trial
     if not args.no_batched and world == 1:
         out["batched"] = run_batched(stream)
         out["replica_exchange"] = run_exchange(stream)
@@ -965,7 +961,6 @@ def main():
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
               "throughput": run_throughput256, "anneal": run_anneal,
               "fcc": lambda st: run_fcc(st, args.edge), "paper": run_paper_rows,
-              "paper_bcc": lambda st: run_paper_bcc(st, args.edge),
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:
