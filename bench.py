@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--no-fcc", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput", "anneal", "fcc", "paper"],
+                                                    "throughput", "anneal", "fcc", "paper", "baselines"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
                     help="profiling only: lattice edge of the fcc / qsro / clusters measurement")
@@ -734,6 +734,130 @@ def run_gradient(stream):
     return out
 
 
+def run_baselines(stream):
+    """Per-config oracle timings (the C oracle as it stands, serial and OpenMP
+    on all host cores) on bounded samples, and the GPU time of the
+    oracle-sized config 1 (BCC 16^3, 100 sweeps).  Samples that are smaller
+    than their config are labelled with what was timed; a rate measured on a
+    sample stands for the config's per-trial rate (the oracle's cost per trial
+    does not depend on the lattice size)."""
+    import torch
+
+    import oracle as O
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import ORACLE_BCC16, SCALE_FCC400, THROUGHPUT_BCC256
+
+    cores = os.cpu_count() or 1
+    out = {"cores": cores}
+
+    def oracle_rate(kind, dims, M, comp, K, V, T, n_sweeps, sched, proposal=0, threads=1, init_seed=1):
+        sig = O.init_config(kind, dims, M, comp, init_seed)
+        t0 = time.perf_counter()
+        if threads == 1:
+            O.sweep(kind, dims, M, K, V, sig, T, n_sweeps, SEED, L=sched[0], nt=sched[1], proposal=proposal)
+            used = 1
+        else:
+            _, used = O.sweep_parallel(kind, dims, M, K, V, sig, T, n_sweeps, SEED, L=sched[0], nt=sched[1],
+                                       threads=threads, proposal=proposal)
+        dt = time.perf_counter() - t0
+        return sig.size * n_sweeps / dt, used, dt
+
+    # config 1: BCC 16^3 int8, 100 sweeps at 1000 K, in full (GPU and oracle)
+    w = ORACLE_BCC16
+    V1 = w.epi()
+    lat = smcx.Lattice(w.kind, w.dims, w.M, w.comp, init_seed=w.init_seed, storage=smcx.INT8, stream=stream)
+    lat.set_epi(V1)
+    sched1 = lat.schedule()
+    lat.sweep(w.temperatures[0], 3, w.seed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.sweep(w.temperatures[0], w.sweeps, w.seed)
+    e1.record(stream)
+    e1.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    lat.close()
+    r1s, _, _ = oracle_rate(w.kind, w.dims, w.M, w.comp, w.K, V1, w.temperatures[0], w.sweeps, sched1)
+    r1p, used, _ = oracle_rate(w.kind, w.dims, w.M, w.comp, w.K, V1, w.temperatures[0], w.sweeps, sched1,
+                               threads=cores)
+    out["config1"] = {"gpu": w.sites * w.sweeps / (ms1 / 1e3), "gpu_ms_100_sweeps": ms1,
+                      "oracle_1core": r1s, "oracle_cores": r1p, "oracle_threads": used,
+                      "schedule": {"L": sched1[0], "tiles": list(sched1[1])},
+                      "sample": "in full: 8192 sites x 100 sweeps (GPU and oracle)"}
+    # config 2: BCC 256^3 int8 at 2500 K: oracle on 1 sweep (OpenMP) / 1 sweep of BCC 64^3 (serial)
+    w = THROUGHPUT_BCC256
+    V2 = w.epi()
+    s2 = (3, (18, 18, 18))
+    r2p, used, dt2 = oracle_rate(w.kind, w.dims, w.M, w.comp, w.K, V2, w.temperatures[0], 1, s2, threads=cores)
+    r2s, _, _ = oracle_rate(w.kind, (64, 64, 64), w.M, w.comp, w.K, V2, w.temperatures[0], 1, (3, (4, 4, 4)))
+    out["config2"] = {"oracle_cores": r2p, "oracle_threads": used, "oracle_1core": r2s,
+                      "sample": f"OpenMP: one sweep of the full 33.5M-site lattice ({dt2:.1f} s); 1 core: one "
+                                "sweep of BCC 64^3 (same model and temperature)"}
+    # config 3a: BCC 800^3 packed, shared-direction proposals: oracle rate on BCC 128^3 (1 sweep)
+    r3p, used, _ = oracle_rate(smcx.BCC, (128, 128, 128), WORK.M, WORK.comp, WORK.K, WORK.epi(), T_KELVIN, 1,
+                               (4, (16, 16, 16)), proposal=PROPOSAL, threads=cores)
+    r3s, _, _ = oracle_rate(smcx.BCC, (64, 64, 64), WORK.M, WORK.comp, WORK.K, WORK.epi(), T_KELVIN, 1,
+                            (4, (8, 8, 8)), proposal=PROPOSAL)
+    out["config3a"] = {"oracle_cores": r3p, "oracle_threads": used, "oracle_1core": r3s,
+                       "sample": "OpenMP: one sweep of BCC 128^3 (4.2M sites); 1 core: one sweep of BCC 64^3; "
+                                 "same model, temperature and proposal mode as the 800^3 workload"}
+    # config 3b: FCC 400^3 5 species: oracle rate on FCC 64^3 (1 sweep)
+    w = SCALE_FCC400
+    V3 = w.epi()
+    r3bp, used, _ = oracle_rate(w.kind, (64, 64, 64), w.M, w.comp, w.K, V3, w.temperatures[0], 1, (3, (4, 4, 4)),
+                                threads=cores)
+    r3bs, _, _ = oracle_rate(w.kind, (32, 32, 32), w.M, w.comp, w.K, V3, w.temperatures[0], 1, (3, (2, 2, 2)))
+    out["config3b"] = {"oracle_cores": r3bp, "oracle_threads": used, "oracle_1core": r3bs,
+                       "sample": "OpenMP: one sweep of FCC 64^3 (1.05M sites); 1 core: one sweep of FCC 32^3"}
+    # config 4: 64 batched replicas (edges 24..96): every replica once, 1 sweep each
+    edges = batched_edges(BATCH_R)
+    Vb = epi_gaussian(4, 4, 20.0, 1)
+    Tb = log_temperatures(BATCH_R)
+    t0 = time.perf_counter()
+    nb = 0
+    for r, e in enumerate(edges):
+        dims = (int(e),) * 3
+        sig = O.init_config(O.BCC, dims, 4, equiatomic(4), 100 + r)
+        nt = 2
+        while (int(e) + nt - 1) // nt > 16:
+            nt += 2
+        O.sweep_parallel(O.BCC, dims, 4, 4, Vb, sig, float(Tb[r]), 1, SEED, replica=r, L=3, nt=(nt,) * 3,
+                         threads=cores)
+        nb += sig.size
+    dt4 = time.perf_counter() - t0
+    out["config4"] = {"oracle_cores": nb / dt4, "oracle_threads": cores,
+                      "sample": f"one sweep of each of the 64 replicas in turn ({nb:,} trials, {dt4:.1f} s, "
+                                "initial placement included)"}
+    # config 5a: pair counts of the 4096 BCC 8^3 configurations (the fit's forward/backward input), in full
+    B, dims5, M5, K5 = 4096, (8, 8, 8), 4, 4
+    N5 = 2 * 8 ** 3
+    cfgs = [np.random.default_rng(b).permutation(np.repeat(np.arange(M5), N5 // M5)).astype(np.int8)
+            for b in range(B)]
+    t0 = time.perf_counter()
+    for c in cfgs:
+        O.pair_counts(O.BCC, dims5, M5, K5, c)
+    dt5 = time.perf_counter() - t0
+    out["config5a"] = {"oracle_1core_configs_per_s": B / dt5,
+                       "sample": "pair counts of all 4096 configurations (the fit step's forward and backward "
+                                 "are linear in them), serial"}
+    # config 5b: fluctuation sweeps: 64 x BCC 48^3 at 1000 K, 2 sweeps + 2 pair-count samples per replica
+    V5 = epi_gaussian(4, 4, 20.0, 1)
+    t0 = time.perf_counter()
+    n5 = 0
+    for r in range(BATCH_R):
+        sig = O.init_config(O.BCC, (48, 48, 48), 4, equiatomic(4), 1000 + r)
+        for k in range(2):
+            O.sweep_parallel(O.BCC, (48, 48, 48), 4, 4, V5, sig, 1000.0, 1, SEED, sweep0=k, replica=r, L=3,
+                             nt=(4, 4, 4), threads=cores)
+            O.pair_counts(O.BCC, (48, 48, 48), 4, 4, sig)
+            n5 += sig.size
+    dt5b = time.perf_counter() - t0
+    out["config5b"] = {"oracle_cores": n5 / dt5b, "oracle_threads": cores,
+                       "sample": "2 sweeps of each of the 64 BCC 48^3 replicas, each followed by its pair counts "
+                                 f"(the fluctuation sample), {dt5b:.1f} s"}
+    return out
+
+
 def aggregate_ranks(ms, sites, steps, dist_mod=None, device="cuda"):
     """Replicas-only scaling: every rank sweeps its own lattice; the job time
     is the slowest rank's, the job's trials are the sum over ranks."""
@@ -959,7 +1083,7 @@ def main():
         import torch
         stream = torch.cuda.Stream()
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
-              "throughput": run_throughput256, "anneal": run_anneal,
+              "throughput": run_throughput256, "anneal": run_anneal, "baselines": run_baselines,
               "fcc": lambda st: run_fcc(st, args.edge), "paper": run_paper_rows,
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)

@@ -93,6 +93,30 @@ def test_batch_block_sizes_equal_plain(stream, threads):
         l.close()
 
 
+def test_batch_multi_tile_replicas_equal_oracle(stream):
+    """Replicas with several tiles per colour (4-6 per axis), so that tiles of
+    one replica are swept by different CTAs on different SMs in every colour
+    pass and read halo cells other SMs wrote in the previous pass; several
+    launches in a row.  Every replica must follow its own oracle
+    trajectory."""
+    dims = [(24, 24, 24), (36, 20, 28), (30, 30, 18), (12, 12, 12)]
+    V = epi_gaussian(4, 4, 20.0, 17)
+    T = log_temperatures(len(dims), 600.0, 2400.0)
+    scheds = [_sched(d, L=3, target=6) for d in dims]
+    lats = [_make(d, r, V, stream, scheds[r]) for r, d in enumerate(dims)]
+    b = smcx.Batch(lats, stream)
+    for _ in range(3):
+        b.sweep(T, 2, 19)
+    for r, d in enumerate(dims):
+        ref = O.init_config(O.BCC, d, 4, [0.25] * 4, 100 + r)
+        st = O.sweep(O.BCC, d, 4, 4, V, ref, T[r], 6, 19, replica=r, L=scheds[r][0], nt=scheds[r][1])
+        assert (lats[r].get_config() == ref).all(), f"replica {r} schedule {scheds[r]}"
+        assert lats[r].state()[1].tolist() == st.tolist()
+    b.close()
+    for l in lats:
+        l.close()
+
+
 def test_batch_autotune_then_oracle(stream):
     V = epi_gaussian(4, 4, 20.0, 2)
     dims = DIMS[:4]
