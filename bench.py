@@ -74,12 +74,17 @@ def parse():
     ap.add_argument("--no-fcc", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
-                                                    "throughput", "anneal", "fcc", "paper", "baselines"],
+                                                    "throughput", "anneal", "fcc", "paper", "baselines",
+                                                    "batch_launch"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
                     help="profiling only: lattice edge of the fcc / qsro / clusters measurement")
     ap.add_argument("--dims", type=int, default=0,
                     help="profiling only: cubic BCC edge other than the 800 of the workload")
+    ap.add_argument("--proposal", type=int, default=1, choices=[0, 1, 2],
+                    help="profiling only: proposal mode of the batch_launch measurement")
+    ap.add_argument("--batch-sched", default="3,17,256",
+                    help="profiling only: link cell, tile target and CTA threads of batch_launch")
     return ap.parse_args()
 
 
@@ -230,9 +235,12 @@ BATCH_R, BATCH_SWEEPS = 64, 500
 def run_batched(stream):
     """64 BCC replicas with cubic edges drawn from 24..96, temperatures
     log-spaced 300-3000 K, shared 4-shell EPI: 500 sweeps in one persistent
-    launch (graph-replayed, autotuned schedules) against the same replicas
-    swept one per smcx_sweep call; both from the same start, compared bit for
-    bit at the end."""
+    launch (graph-replayed, autotuned schedules), with shared-direction
+    proposals (the headline's mode) and with per-trial directions.  Per-trial
+    directions are also run as 64 separate handles, one smcx_sweep call each;
+    both from the same start, compared bit for bit at the end.  The
+    shared-direction batch is compared bit for bit with plain runs of 2
+    sweeps."""
     import torch
     from paper_2503_12591_gb300 import smcx
 
@@ -240,56 +248,114 @@ def run_batched(stream):
     T = log_temperatures(BATCH_R, 300.0, 3000.0)
     V = epi_gaussian(4, 4, 20.0, 1)
 
-    def make(r):
+    def make(r, mode):
         n = int(edges[r])
         lat = smcx.Lattice(smcx.BCC, (n, n, n), 4, equiatomic(4), init_seed=1000 + r, storage=smcx.INT8,
                            stream=stream)
         lat.set_replica(r)
         lat.set_epi(V)
+        lat.set_proposal(mode)
         return lat
 
-    lats = [make(r) for r in range(BATCH_R)]
-    sites = sum(l.N for l in lats)
-    b = smcx.Batch(lats, stream)
-    threads = b.autotune(T, trial_sweeps=2)
-    scheds = [l.schedule() for l in lats]
-    plain = [make(r) for r in range(BATCH_R)]
-    for p, sc in zip(plain, scheds):
-        p.set_schedule(sc)
-        p.set_block(threads)
-    b.sweep(T, 2, SEED)
-    for r, p in enumerate(plain):
-        p.sweep(T[r], 2, SEED)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.sweep(T, BATCH_SWEEPS, SEED)
-    e1.record(stream)
-    e1.synchronize()
-    ms_b = e0.elapsed_time(e1)
-    info = b.info()
-    e0.record(stream)
-    for r, p in enumerate(plain):
-        p.sweep(T[r], BATCH_SWEEPS, SEED)
-    e1.record(stream)
-    e1.synchronize()
-    ms_p = e0.elapsed_time(e1)
-    exact = all((l.get_config() == p.get_config()).all() and
-                l.state()[1].tolist() == p.state()[1].tolist() for l, p in zip(lats, plain))
-    b.close()
-    for l in lats + plain:
-        l.close()
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def one_mode(mode, plain_sweeps):
+        lats = [make(r, mode) for r in range(BATCH_R)]
+        b = smcx.Batch(lats, stream)
+        threads = b.autotune(T, trial_sweeps=2)
+        scheds = [l.schedule() for l in lats]
+        plain = [make(r, mode) for r in range(BATCH_R)]
+        for p, sc in zip(plain, scheds):
+            p.set_schedule(sc)
+            if mode == smcx.PROPOSAL_SITE:
+                p.set_block(threads)
+        b.sweep(T, 2, SEED)
+        for r, p in enumerate(plain):
+            p.sweep(T[r], 2, SEED)
+
+        def same():
+            return all((l.get_config() == p.get_config()).all() and
+                       l.state()[1].tolist() == p.state()[1].tolist() for l, p in zip(lats, plain))
+
+        exact = same() if not plain_sweeps else None
+        ms_b = timed(lambda: b.sweep(T, BATCH_SWEEPS, SEED))
+        info = b.info()
+        ms_p = None
+        if plain_sweeps:
+            ms_p = timed(lambda: [p.sweep(T[r], plain_sweeps, SEED) for r, p in enumerate(plain)])
+            exact = same()
+        b.close()
+        for l in lats + plain:
+            l.close()
+        return ms_b, ms_p, info, exact, scheds
+
+    sites = sum(2 * int(n) ** 3 for n in edges)
     att = sites * BATCH_SWEEPS
-    return {"value": att / (ms_b / 1e3), "unit": UNIT, "plain_value": att / (ms_p / 1e3),
-            "speedup_vs_plain": ms_p / ms_b, "replicas": BATCH_R, "sites": sites, "sweeps": BATCH_SWEEPS,
-            "ms_batched": ms_b, "ms_plain": ms_p, "graph": info["graph"], "grid": info["grid"],
-            "threads": info["threads"], "bit_exact_vs_plain": bool(exact),
-            "plain": "64 handles, one smcx_sweep call each (8 tile-colour launches per sweep)",
+    ms_d, _, info_d, exact_d, sch_d = one_mode(smcx.PROPOSAL_TILE, 0)
+    ms_b, ms_p, info, exact, _ = one_mode(smcx.PROPOSAL_SITE, BATCH_SWEEPS)
+    return {"value": att / (ms_d / 1e3), "unit": UNIT, "proposal": "shared direction per (sweep, tile, phase)",
+            "replicas": BATCH_R, "sites": sites, "sweeps": BATCH_SWEEPS, "ms_batched": ms_d, "graph": info_d["graph"],
+            "grid": info_d["grid"], "threads": info_d["threads"], "schedule_L": sch_d[0][0],
+            "bit_exact_vs_plain": bool(exact_d),
+            "per_trial_direction": {"value": att / (ms_b / 1e3), "ms_batched": ms_b, "grid": info["grid"],
+                                    "threads": info["threads"], "plain_value": att / (ms_p / 1e3),
+                                    "speedup_vs_plain": ms_p / ms_b, "ms_plain": ms_p,
+                                    "bit_exact_vs_plain": bool(exact),
+                                    "plain": "64 handles, one smcx_sweep call each (8 tile-colour launches per sweep)"},
             "workload": "64 BCC cubic lattices, edges U{24..96} (seed 1), 4 species, shared 4-shell EPI, "
                         "T log-spaced 300-3000 K, int8 storage"}
 
 
 EX_R, EX_EDGE, EX_ROUNDS, EX_SPR = 32, 48, 40, 10
+
+
+def run_batch_launch(stream, proposal, sched):
+    """Profiling aid: the 64-replica batched workload with a fixed schedule
+    (link cell L, tiles of at most `target` cells, `threads` per CTA), one
+    warm-up launch and one more launch of one sweep each, so that a profiler
+    can capture the second launch alone."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+
+    L, target, threads = (int(x) for x in sched.split(","))
+    edges = batched_edges(BATCH_R, 24, 96, 1)
+    T = log_temperatures(BATCH_R, 300.0, 3000.0)
+    V = epi_gaussian(4, 4, 20.0, 1)
+    lats = []
+    for r in range(BATCH_R):
+        n = int(edges[r])
+        lat = smcx.Lattice(smcx.BCC, (n, n, n), 4, equiatomic(4), init_seed=1000 + r, storage=smcx.INT8,
+                           stream=stream)
+        lat.set_replica(r)
+        lat.set_epi(V)
+        lat.set_proposal(proposal)
+        nt = 2
+        while (n + nt - 1) // nt > target:
+            nt += 2
+        lat.set_schedule((L, (nt, nt, nt)))
+        lats.append(lat)
+    b = smcx.Batch(lats, stream)
+    b.set_block(threads)
+    b.sweep(T, 1, SEED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.sweep(T, 1, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    info = b.info()
+    b.close()
+    for l in lats:
+        l.close()
+    return {"proposal": proposal, "schedule": [L, target, threads], "ms_launch": e0.elapsed_time(e1),
+            "grid": info["grid"], "threads": info["threads"], "sites": sum(2 * int(n) ** 3 for n in edges)}
 
 
 def run_exchange(stream):
@@ -1085,7 +1151,8 @@ def main():
         fn = {"batched": run_batched, "exchange": run_exchange, "gradient": run_gradient,
               "throughput": run_throughput256, "anneal": run_anneal, "baselines": run_baselines,
               "fcc": lambda st: run_fcc(st, args.edge), "paper": run_paper_rows,
-              "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge)}
+              "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge),
+              "batch_launch": lambda st: run_batch_launch(st, args.proposal, args.batch_sched)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:
         run_smcx(args, rank, world, local_rank)

@@ -220,10 +220,12 @@ int smcx_set_replica(smcx_lattice* h, int replica);
  * 1, nc_a = the colour's tile count on axis a; block = j >> 1): Philox counter
  * (block | tc << 28, (ic >> 1) | replica << 16, sweep lo, sweep hi | 2^29),
  * key = seed, word 0 for even ic and word 2 for odd ic.  The proposals are
- * keyed by (seed, sweep, colour, block), and the BCC kernel sweeps the two
- * tiles of a block in one CTA with the union of the environments read once
- * for both.  FCC lattices run the other modes on the generic tile kernel;
- * batched and qSRO sweeps run SMCX_PROPOSAL_SITE only. */
+ * keyed by (seed, sweep, colour, block); the two tiles of a block share their
+ * directions (each tile still runs in its own CTA).  The shared-direction
+ * modes run on the BCC tile kernels (single-lattice and batched) when the
+ * table has 4 shells, M <= 4 and |V| < 2^15, else on the generic tile
+ * kernel; FCC lattices run them on the generic tile kernel; qSRO sweeps run
+ * SMCX_PROPOSAL_SITE only. */
 #define SMCX_PROPOSAL_SITE 0
 #define SMCX_PROPOSAL_TILE 1
 #define SMCX_PROPOSAL_BLOCK 2
@@ -391,14 +393,17 @@ int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
  * trajectory equals the one smcx_sweep gives it alone.
  *   smcx_batch_create   references R existing handles (not owned; they must
  *                       outlive the batch), which must share M, the EPI table
- *                       (4 shells, set with smcx_set_epi) and `stream`, and
- *                       have schedules with tiles of at most 20 cells.
+ *                       (4 shells, set with smcx_set_epi), the proposal mode
+ *                       and `stream`, and have schedules with tiles of at most
+ *                       20 cells.  Shared-direction modes also need M <= 4,
+ *                       |V| < 2^15 and tiles of at most 256 link cells (one
+ *                       slot per thread).
  *   smcx_batch_sweep    n_sweeps at temperatures T[R] with Philox seed `seed`;
  *                       returns after the launch has finished; SMCX_E_TIMEOUT
  *                       if a grid barrier waited longer than its limit.
  *   smcx_batch_autotune times `trial_sweeps` batched sweeps for every
- *                       candidate (link cell 3 or 4, tiles of about 12/16/20
- *                       cells, 3 block sizes) on snapshots of the
+ *                       candidate (link cell 3 or 4, tiles of at most 12-20
+ *                       cells, 128- or 256-thread CTAs) on snapshots of the
  *                       configurations, restores them, and installs the
  *                       fastest candidate's schedules (read them back with
  *                       smcx_get_schedule) and block size (*threads).
@@ -407,7 +412,9 @@ int smcx_threshold_tables(double T, uint32_t* A, int* nA, uint32_t* B);
  *                       replayed a graph.
  *   smcx_batch_set_block threads per CTA of the next sweeps: 0 (the fewest
  *                       128-thread-or-smaller CTAs that cover a tile's link
- *                       cells with at most 2 slots per thread), 128, or 256
+ *                       cells with at most 2 slots per thread; 256 threads for
+ *                       tiles of more than 128 link cells under a
+ *                       shared-direction mode), 128, or 256
  *                       (one slot per thread; SMCX_E_UNSUPPORTED at the next
  *                       sweep if a tile has more than 256 link cells).
  *                       SMCX_E_INVALID_ARG for other values.

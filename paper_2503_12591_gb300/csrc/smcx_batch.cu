@@ -6,18 +6,19 @@
 // temperatures are independent); the paper runs them on separate GPUs, here
 // they share one GPU and one launch.  Every replica keeps its own schedule,
 // sweep counter and Philox replica id, so its trajectory is bit-identical to
-// sweeping it alone through smcx_sweep.
+// sweeping it alone through smcx_sweep, in either proposal mode.
 //
-// The kernel loops over sweeps and tile colours; in each colour the CTAs take
-// the pooled list of (replica, tile) work items of that colour, then meet at
-// a grid barrier.  The barrier waits at most `timeout_ns`: a CTA that gives
-// up writes SMCX_E_TIMEOUT into a device status word and returns, and so does
-// every other CTA once it sees the status, so the context stays usable.
+// The kernel (smcx_batch_body.cuh) loops over sweeps and tile colours; in
+// each colour the CTAs take the pooled list of (replica, tile) work items of
+// that colour, then meet at a grid barrier.  The barrier waits at most
+// `timeout_ns`: a CTA that gives up writes SMCX_E_TIMEOUT into a device status
+// word and returns, and so does every other CTA once it sees the status, so
+// the context stays usable.
 #include <algorithm>
 #include <cmath>
 #include <map>
 
-#include "smcx_bcc_tile.cuh"
+#include "smcx_batch_body.cuh"
 
 struct smcx_batch {
   std::vector<smcx_lattice*> lat;
@@ -34,6 +35,7 @@ struct smcx_batch {
   std::map<long long, cudaGraphExec_t> graphs;  // keyed by (sweeps, table size)
   std::vector<int32_t> graph_V;                 // EPI baked into the graphs
   bool items_dirty = true;
+  int items_proposal = -1;  // proposal mode the work list and block shape were built for
   int last_grid = 0;
   bool last_graph = false;
   // fluctuation accumulation: per-replica descriptors, (replica, tile) items, counts
@@ -50,84 +52,6 @@ namespace smcx {
 
 int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
 
-namespace bccfast {
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier with a time limit; returns false if the grid must stop.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* status, long long timeout_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    int ok = 1;
-    const unsigned long long t0 = global_ns();
-    while (true) {
-      const unsigned v = *((volatile unsigned*)bar);
-      if (v >= target) break;
-      if (*((volatile int*)status) != 0) {
-        ok = 0;
-        break;
-      }
-      if ((long long)(global_ns() - t0) > timeout_ns) {
-        atomicCAS(status, 0, SMCX_E_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <int K, int NW, int PL, int SLOTS>
-__device__ __forceinline__ void batch_body(const Planes& Q, const LatDesc* __restrict__ descs,
-                                           const int2* __restrict__ items, int n_items, int n_sweeps, unsigned* bar,
-                                           int* status, long long timeout_ns, int skip_cta, int max_nA) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long s_stat[3];
-  uint8_t* box = smem;
-  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
-  uint32_t* sB = sA + max_nA;
-  unsigned epoch = 0;
-  for (int s = 0; s < n_sweeps; s++)
-    for (int tc = 0; tc < 8; tc++) {
-      for (int e = blockIdx.x; e < n_items; e += gridDim.x) {
-        const int2 it = items[e];
-        const LatDesc D = descs[it.x];
-        bcc_tile_pass<K, NW, PL, SLOTS>(D, Q, tc, it.y, D.sweep + (unsigned long long)s, box, sA, sB, s_stat);
-      }
-      if ((int)blockIdx.x == skip_cta) return;
-      epoch++;
-      if (!grid_barrier(bar, epoch * gridDim.x, status, timeout_ns)) return;
-    }
-}
-
-// 128-thread CTAs (one or two link-cell slots per thread), and 256-thread
-// CTAs for tiles of up to 256 slots (6^3 with link cells of 3): one slot per
-// thread, so a tile's phases take half the sequential steps of two slots.
-template <int K, int NW, int PL, int SLOTS>
-__global__ void __launch_bounds__(128, 6)
-    k_bcc_batch(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
-                int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
-  batch_body<K, NW, PL, SLOTS>(Q, descs, items, n_items, n_sweeps, bar, status, timeout_ns, skip_cta, max_nA);
-}
-template <int K, int NW, int PL>
-__global__ void __launch_bounds__(256, 3)
-    k_bcc_batch256(const Planes Q, const LatDesc* __restrict__ descs, const int2* __restrict__ items, int n_items,
-                   int n_sweeps, unsigned* bar, int* status, long long timeout_ns, int skip_cta, int max_nA) {
-  batch_body<K, NW, PL, 1>(Q, descs, items, n_items, n_sweeps, bar, status, timeout_ns, skip_cta, max_nA);
-}
-
-}  // namespace bccfast
 
 namespace {
 
@@ -140,8 +64,8 @@ void check_batch(const smcx_batch* b) {
     if (h->M != h0->M || h->shells.K != h0->shells.K || h->V != h0->V)
       fail(SMCX_E_INVALID_ARG, "replicas must share M and the EPI table");
     if (h->stream != b->stream) fail(SMCX_E_INVALID_ARG, "replicas must share the batch stream");
-    if (h->proposal != SMCX_PROPOSAL_SITE) fail(SMCX_E_UNSUPPORTED, "batched sweeps use per-trial directions");
-    if (!bcc_fast_usable(h))
+    if (h->proposal != h0->proposal) fail(SMCX_E_INVALID_ARG, "replicas must share the proposal mode");
+    if (!bcc_fast_usable(h, 256))
       fail(SMCX_E_UNSUPPORTED, "replica schedule needs tiles of at most 20 cells (BCC, M <= 8)");
   }
   if (h0->shells.K != 4) fail(SMCX_E_UNSUPPORTED, "batched sweeps run 4-shell EPI tables");
@@ -172,7 +96,10 @@ void rebuild_items(smcx_batch* b) {
   check_cuda(cudaStreamSynchronize(b->stream), "batch work list sync");
   b->n_items = (int)items.size();
   int threads, slots;
-  if (b->threads == 256) {
+  // shared-direction proposals run one slot per thread: tiles of more than
+  // 128 slots take 256-thread CTAs unless 128 threads were asked for
+  const bool dir = b->lat[0]->proposal != 0;
+  if (b->threads == 256 || (dir && b->threads != 128 && nq * nq * nq > 128)) {
     threads = 256;  // one slot per thread
     slots = 1;
     if (nq * nq * nq > 256) fail(SMCX_E_UNSUPPORTED, "256-thread CTAs take tiles of at most 256 link-cell slots");
@@ -182,20 +109,26 @@ void rebuild_items(smcx_batch* b) {
   if (slots > 2) fail(SMCX_E_UNSUPPORTED, "batched tiles need at most 256 link-cell slots");
   b->threads = threads;
   b->slots = slots;
+  b->items_proposal = b->lat[0]->proposal;
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
   b->graphs.clear();
   b->items_dirty = false;
 }
 
-using KernelFn = void (*)(const bccfast::Planes, const bccfast::LatDesc*, const int2*, int, int, unsigned*, int*,
-                          long long, int, int);
+using bccfast::BatchKernelFn;
 
-KernelFn pick_kernel(int nw, int pl, int slots, int threads) {
+BatchKernelFn pick_kernel(int nw, int pl, int slots, int threads, int proposal) {
   using namespace bccfast;
+  if (proposal != 0) {
+    // shared-direction proposals: one compiled variant (M <= 4, |V| < 2^15)
+    if (nw != 1 || pl != 2 || slots != 1)
+      fail(SMCX_E_UNSUPPORTED, "shared-direction batches need M <= 4, |V| < 2^15 and one slot per thread");
+    return batch_dir_kernel(threads);
+  }
 #define SMCX_PICK(NW_, PL_)                                    \
-  return threads == 256 ? k_bcc_batch256<4, NW_, PL_>          \
-         : slots == 1   ? k_bcc_batch<4, NW_, PL_, 1> \
-                        : k_bcc_batch<4, NW_, PL_, 2>
+  return threads == 256 ? k_bcc_batch256<4, NW_, PL_, 0>       \
+         : slots == 1   ? k_bcc_batch<4, NW_, PL_, 1, 0> \
+                        : k_bcc_batch<4, NW_, PL_, 2, 0>
   if (nw == 1 && pl == 2) SMCX_PICK(1, 2);
   if (nw == 1) SMCX_PICK(1, 3);
   if (pl == 2) SMCX_PICK(2, 2);
@@ -222,7 +155,7 @@ void batch_sweep(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed
 }
 
 static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps, uint64_t seed) {
-  if (b->items_dirty) rebuild_items(b);
+  if (b->items_dirty || b->items_proposal != b->lat[0]->proposal) rebuild_items(b);
   const size_t R = b->lat.size();
   std::vector<bccfast::LatDesc> desc(R);
   int max_nA = 0;
@@ -248,6 +181,7 @@ static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps,
     D.seed_lo = (uint32_t)seed;
     D.seed_hi = (uint32_t)(seed >> 32);
     D.sweep = h->sweep_cum;
+    D.proposal = h->proposal;
     max_nA = std::max(max_nA, D.nA);
   }
   if (!b->d_desc) check_cuda(cudaMalloc(&b->d_desc, R * sizeof(bccfast::LatDesc)), "batch descriptors");
@@ -256,7 +190,7 @@ static void batch_sweep_launch(smcx_batch* b, const double* T, int64_t n_sweeps,
   bccfast::Planes Q;
   const int PL = build_planes(b->lat[0], &Q, 2);
   const int nw = b->lat[0]->M <= 4 ? 1 : 2;
-  KernelFn fn = pick_kernel(nw, PL, b->slots, b->threads);
+  BatchKernelFn fn = pick_kernel(nw, PL, b->slots, b->threads, b->lat[0]->proposal);
   // shared memory for the largest table of this call, rounded up so that a
   // graph instantiated for it serves nearby temperature sets as well
   const int nA_cap = std::min(kNA, ((max_nA + 255) / 256) * 256);
@@ -368,9 +302,12 @@ void batch_autotune(smcx_batch* b, const double* T, int trial, int* best_threads
     int L, target, threads;
   };
   std::vector<Cand> cands;
+  // a tile pass takes 2 L^3 phase steps whatever the tile's size, so the
+  // candidates trade tile size (lanes busy per step) against the number of
+  // items per colour (CTA rounds); shapes a kernel does not take are skipped
   for (int L : {3, 4})
-    for (int target : {12, 16, 20})
-      for (int th : {0, 128, 256}) cands.push_back({L, target, th});
+    for (int target : {12, 13, 14, 15, 16, 17, 18, 20})
+      for (int th : {128, 256}) cands.push_back({L, target, th});
   double best = 1e300;
   Cand bestc = cands[0];
   std::vector<smcx_sched> best_sched(R);
@@ -395,7 +332,7 @@ void batch_autotune(smcx_batch* b, const double* T, int trial, int* best_threads
     b->threads = c.threads;
     b->items_dirty = true;
     bool usable = true;
-    for (size_t r = 0; r < R; r++) usable = usable && bcc_fast_usable(b->lat[r]);
+    for (size_t r = 0; r < R; r++) usable = usable && bcc_fast_usable(b->lat[r], 256);
     if (!usable) continue;
     try {
       batch_sweep(b, T, 1, 0x5eedull);  // warm-up: instantiate, load tables

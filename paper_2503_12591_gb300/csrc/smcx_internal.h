@@ -168,7 +168,10 @@ void unpack_to_int8(smcx_lattice* h, int8_t* d_ids, int64_t first, int64_t count
 void pair_counts_device(smcx_lattice* h);          // fills h->d_counts
 void energy_device(smcx_lattice* h);               // fills h->d_energy (needs counts)
 void sweep_device(smcx_lattice* h, int nA, uint64_t seed, int64_t n_sweeps, int n_colours = 8);
-bool bcc_fast_usable(const smcx_lattice* h);
+// dir_slots: the most link-cell slots a tile may have under shared-direction
+// proposals (one slot per thread: 128 for the single-lattice kernel, 256 for
+// the batched kernel's 256-thread CTAs).
+bool bcc_fast_usable(const smcx_lattice* h, int dir_slots = 128);
 bool bcc_counts_usable(const smcx_lattice* h, int nt[3]);
 void pair_counts_bcc_tiled(smcx_lattice* h, const int nt[3]);
 int bcc_slots_per_axis(const int n[3], const smcx_sched& sc);

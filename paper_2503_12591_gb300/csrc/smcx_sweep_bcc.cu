@@ -42,7 +42,7 @@ int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes) {
 
 // Usable when the lattice is BCC, M <= 8, |V| < 2^23, the tiles fit the
 // 24^3 box and two link-cell slots per thread cover a tile.
-bool bcc_fast_usable(const smcx_lattice* hd) {
+bool bcc_fast_usable(const smcx_lattice* hd, int dir_slots) {
   const smcx_sched& sc = hd->sched;
   if (hd->kind != kBCC || hd->M > kMaxSweepM || !hd->have_epi) return false;
   if (hd->proposal != 0) {
@@ -61,7 +61,7 @@ bool bcc_fast_usable(const smcx_lattice* hd) {
     if (tmax + 4 > bccfast::BOX) return false;
     nq = std::max(nq, (tmax + sc.L - 1) / sc.L);
   }
-  if (hd->proposal != 0 && nq * nq * nq > 128) return false;  // one slot per thread
+  if (hd->proposal != 0 && nq * nq * nq > dir_slots) return false;  // one slot per thread
   // four slots per thread are compiled for 4 shells, M <= 4, two planes only
   if (nq * nq * nq > 256) {
     if (hd->shells.K != 4 || hd->M > 4) return false;

@@ -1,10 +1,11 @@
-// BCC sweep with shared-direction proposals (SMCX_PROPOSAL_TILE): the one
-// compiled variant (4 shells, M <= 4, two byte planes, one link-cell slot per
-// thread).  The direction of a phase is the same for every lane, so the
-// union of the s and s' environments is read with offsets from a constant-
-// memory table (one row per sublattice and direction) and the shells of every
-// entry are compile-time constants.
-#include "smcx_bcc_tile.cuh"
+// BCC sweep with shared-direction proposals (SMCX_PROPOSAL_TILE and
+// SMCX_PROPOSAL_BLOCK), single-lattice and batched: the one compiled variant
+// (4 shells, M <= 4, two byte planes, one link-cell slot per thread).  The
+// direction of a phase is the same for every lane, so the union of the s and
+// s' environments is read with offsets from a constant-memory table (one row
+// per sublattice and direction) and the shells of every entry are
+// compile-time constants.
+#include "smcx_batch_body.cuh"
 
 namespace smcx {
 
@@ -42,6 +43,10 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
 }
 
 }  // namespace bccfast
+
+bccfast::BatchKernelFn batch_dir_kernel(int threads) {
+  return threads == 256 ? bccfast::k_bcc_batch256<4, 1, 2, 1> : bccfast::k_bcc_batch<4, 1, 2, 1, 1>;
+}
 
 void sweep_bcc_dir(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads, int64_t n,
                    int nc) {

@@ -117,6 +117,63 @@ def test_batch_multi_tile_replicas_equal_oracle(stream):
         l.close()
 
 
+@pytest.mark.parametrize("mode", [smcx.PROPOSAL_TILE, smcx.PROPOSAL_BLOCK])
+@pytest.mark.parametrize("threads", [0, 128, 256])
+def test_batch_shared_direction_equals_plain_and_oracle(stream, mode, threads):
+    """Shared-direction proposals in the persistent launch: one shell-1
+    direction per (sweep, tile, phase), or per (sweep, colour, block of two
+    tiles, phase).  Replicas of one and of several tiles per colour, link
+    cells of 3 and 4, tiles of up to 216 link-cell slots (256-thread CTAs) or
+    125 (either block size); two launches in a row, the second a graph
+    replay.  Each replica must equal its plain run and its oracle
+    trajectory."""
+    dims = [(12, 12, 12), (36, 34, 32), (24, 24, 24), (13, 20, 18), (40, 12, 20)]
+    V = epi_gaussian(4, 4, 20.0, 23)
+    T = log_temperatures(len(dims), 400.0, 2800.0)
+    target = 18 if threads != 128 else 15
+    scheds = [_sched(d, L=3, target=target if i != 2 else 6) for i, d in enumerate(dims)]
+    scheds[3] = _sched(dims[3], L=4, target=10)
+    lats = [_make(d, r, V, stream, scheds[r]) for r, d in enumerate(dims)]
+    for l in lats:
+        l.set_proposal(mode)
+    b = smcx.Batch(lats, stream)
+    if threads:
+        b.set_block(threads)
+    b.sweep(T, 2, 31)
+    b.sweep(T, 3, 31)
+    if threads:
+        assert b.info()["threads"] == threads
+    for r, d in enumerate(dims):
+        plain = _make(d, r, V, stream, scheds[r], storage=smcx.INT8)
+        plain.set_proposal(mode)
+        plain.sweep(T[r], 5, 31)
+        got = lats[r].get_config()
+        assert (got == plain.get_config()).all(), f"replica {r} differs from its plain run"
+        assert lats[r].state()[1].tolist() == plain.state()[1].tolist()
+        plain.close()
+        if r in (0, 2, 3):
+            ref = O.init_config(O.BCC, d, 4, [0.25] * 4, 100 + r)
+            st = O.sweep(O.BCC, d, 4, 4, V, ref, T[r], 5, 31, replica=r, L=scheds[r][0], nt=scheds[r][1],
+                         proposal=mode)
+            assert (got == ref).all(), f"replica {r} schedule {scheds[r]}"
+            assert lats[r].state()[1].tolist() == st.tolist()
+    b.close()
+    for l in lats:
+        l.close()
+
+
+def test_batch_mixed_proposal_modes_refused(stream):
+    V = epi_gaussian(4, 4, 20.0, 1)
+    dims = [(12, 12, 12), (16, 16, 16)]
+    lats = [_make(d, r, V, stream, _sched(d)) for r, d in enumerate(dims)]
+    lats[1].set_proposal(smcx.PROPOSAL_TILE)
+    with pytest.raises(smcx.SmcxError):
+        b = smcx.Batch(lats, stream)
+        b.sweep(log_temperatures(2, 500.0, 1000.0), 1, 1)
+    for l in lats:
+        l.close()
+
+
 def test_batch_autotune_then_oracle(stream):
     V = epi_gaussian(4, 4, 20.0, 2)
     dims = DIMS[:4]
