@@ -536,7 +536,7 @@ def run_qsro(stream, edge=0):
             "schedule": {"L": sched_q[0], "tiles": list(sched_q[1])},
             "pair_schedule": {"L": sched_pair[0], "tiles": list(sched_pair[1])},
             "acceptance": float(st[1]) / max(1, int(st[0])),
-            "kernel": "k_qsro_fcc<3>" if max(-(-d // t) for d, t in zip(W_.dims, sched_q[1])) <= 20
+            "kernel": "k_qsro_fcc_n<3>" if max(-(-d // t) for d, t in zip(W_.dims, sched_q[1])) <= 20
                       else "k_tile_sweep_qsro<FCC,3>",
             "workload": f"FCC {W_.dims[0]}^3 = {N / 1e6:.0f}M sites, 5 species 0.3/0.25/0.2/0.15/0.1, 3-shell EPI "
                         "N(0,30 meV) + qSRO W U{-300..300} (0.01 meV), packed 4-bit, 1000 K"}

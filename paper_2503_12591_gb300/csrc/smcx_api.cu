@@ -47,6 +47,7 @@ void release(smcx_lattice* h) {
   cudaFree(h->d_wtab);
   cudaFree(h->d_flag);
   cudaFree(h->d_stage);
+  cudaFree(h->d_qcnt);
 }
 
 // One int8 id per site, allocated on first configuration transfer and kept.

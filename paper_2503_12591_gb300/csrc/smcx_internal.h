@@ -134,6 +134,7 @@ struct smcx_lattice {
   int32_t* d_wtab = nullptr;              // W[a][b][k][c], then X[a][b]
   int* d_flag = nullptr;                  // device error flag
   uint8_t* d_stage = nullptr;             // host<->device staging (int8 ids)
+  uint16_t* d_qcnt = nullptr;             // qSRO same-species counts, one word per site (FCC sweeps)
   size_t stage_bytes = 0;
 
   int kernel_choice = 0;  // 0 = fastest usable, 1 = generic tile/link-cell kernels

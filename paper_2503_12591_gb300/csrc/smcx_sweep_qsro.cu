@@ -270,13 +270,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tile_sweep_qsro(const SweepPar
 }
 
 // ---------------------------------------------------------------------------
-// FCC qSRO sweep on the even-point layout: the FCC sites are the even points
-// of the half-unit grid, stored at byte (x + y QPX + z QPP) / 2 of a box of
-// QEXT half units per axis (tile <= 20 cells + 3-cell halo), so a neighbour
-// along v is at a constant offset from ANY site.  Every same-species count of
-// a union site is then an unrolled run of immediate-offset loads, with no
-// offset table and no sublattice case; the shell of s' seen from a union
-// site is a runtime value, taken through a three-way switch.
+// FCC even-point species box (used to count every site's same-species
+// neighbours at the start of a sweep call): the FCC sites are the even
+// points of the half-unit grid, stored at byte (x + y QPX + z QPP) / 2 of a
+// box of QEXT half units per axis (tile <= 20 cells + 3-cell halo), so a
+// neighbour along v is at a constant offset from any site and a shell count
+// is an unrolled run of immediate-offset loads.
 // ---------------------------------------------------------------------------
 namespace qfcc {
 constexpr int H = 3;
@@ -325,72 +324,223 @@ __device__ __forceinline__ int count_shell(const uint8_t* box, int t, int c) {
   for (int j = T.start[KS]; j < T.start[KS + 1]; j++) n += (box[t + hoff(T.v[j].x, T.v[j].y, T.v[j].z)] == c);
   return n;
 }
-__device__ __forceinline__ int count_rt(const uint8_t* box, int t, int k, int c) {
-  switch (k) {
-    case 0: return count_shell<0>(box, t, c);
-    case 1: return count_shell<1>(box, t, c);
-    default: return count_shell<2>(box, t, c);
+// Stage tile + 3-cell halo (species bytes at the even points), 8 rows of
+// loads in flight per lane; every thread of the CTA takes part.
+__device__ __forceinline__ void stage_box(const SweepParams& P, uint8_t* box, const int (&t0)[3], const int (&ts)[3]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  constexpr int U = 8;
+  const int rows = ey * ez;
+  const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
+  for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
+    uint32_t v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int row = row0 + u;
+      v[u] = 0;
+      if (row < rows && lane < ex) {
+        const int ys = row % ey, zs = row / ey;
+        const long long cell =
+            ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+        v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
+                                      : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int row = row0 + u;
+      if (row < rows && lane < ex) {
+        const int ys = row % ey, zs = row / ey;
+        const int base = hoff(2 * lane, 2 * ys, 2 * zs);
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          box[base + boff(b)] =
+              (uint8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+      }
+    }
   }
-}
-// Sites t = s + v_j of shell KS around s with species a or b that see s' in
-// another shell k2 (or not at all, k2 = -1): n_KS(t) changes by d1 = +1
-// (t holds b) or -1 (t holds a), n_k2(t) by -d1.  The loop over the shell
-// runs with offsets from a table (keeps the code small enough for the
-// instruction cache); each count is an immediate-offset run.
-template <int KS>
-__device__ __forceinline__ int env_s_shell(const uint8_t* box, const int* qoff, const signed char* k2row,
-                                           const int32_t* wq, int M, int s, int sa, int sb) {
-  constexpr QTable T = make_qvecs();
-  int dE = 0;
-#pragma unroll 2
-  for (int j = T.start[KS]; j < T.start[KS + 1]; j++) {
-    const int t = s + qoff[j];
-    const int c = box[t];
-    if (c != sa && c != sb) continue;
-    const int k2 = k2row[j];
-    if (k2 == -2 || k2 == KS) continue;  // t is s', or sees s and s' in one shell
-    const int d1 = (c == sb) ? 1 : -1;
-    dE += wq[KS * M + c] * (2 * d1 * count_shell<KS>(box, t, c) + 1);
-    if (k2 >= 0) dE += wq[k2 * M + c] * (-2 * d1 * count_rt(box, t, k2, c) + 1);
-  }
-  return dE;
-}
-// Sites t = s' + v_j of shell KS around s' outside the environment of s:
-// n_KS(t) changes by d2 = -1 (t holds b) or +1 (t holds a).
-template <int KS>
-__device__ __forceinline__ int env_p_shell(const uint8_t* box, const int* qoff, const signed char* insrow,
-                                           const int32_t* wq, int M, int sp, int sa, int sb) {
-  constexpr QTable T = make_qvecs();
-  int dE = 0;
-#pragma unroll 2
-  for (int j = T.start[KS]; j < T.start[KS + 1]; j++) {
-    if (insrow[j]) continue;
-    const int t = sp + qoff[j];
-    const int c = box[t];
-    if (c != sa && c != sb) continue;
-    const int d2 = (c == sb) ? -1 : 1;
-    dE += wq[KS * M + c] * (2 * d2 * count_shell<KS>(box, t, c) + 1);
-  }
-  return dE;
 }
 }  // namespace qfcc
 
+// ---------------------------------------------------------------------------
+// FCC qSRO sweep with maintained counts.  Every site's same-species counts
+// n_k(i) (k < K) live beside its species: in a device array (one 16-bit
+// word per site, written by k_qsro_fcc_count_init at the start of each sweep
+// call) and, during a tile pass, in a 16-bit shared-memory box (species in
+// bits 0..2, n_0 in bits 3..6 (<= 12), n_1 in 7..9 (<= 6), n_2 in 10..14
+// (<= 24)).  A trial then reads the count of a changing environment site
+// with one load instead of counting its shell, and an accepted swap updates
+// the counts it changes: s and s' take the counts the pair loop found, and
+// every other environment site i of species a or b that sees s and s' in
+// different shells gets its one or two count fields moved by +-1 (one add
+// to the packed word; a field never leaves its range, so no carry crosses
+// fields).
+//
+// The box covers the half units [2 t0 - 3, 2 (t0 + ts) + 2] of each axis:
+// every site a trial of the tile reads (the two environments) or whose
+// count it changes.  Its origin is the odd point 2 t0 - 3, so a site's box
+// coordinates have an odd sum, and element (x + y NPX + z NPP + 1) / 2 (odd
+// pitches) stores the box's FCC sites without gaps; a lattice vector is a
+// constant element offset.  A tile pass writes back the species of the tile
+// and its 1-cell ring and the counts of the whole box.  Tiles of one colour
+// are at least 3 cells (6 half units) apart, so no two boxes of a launch
+// share a site whose count either of them changes or writes.
+// ---------------------------------------------------------------------------
+namespace qfn {
+constexpr int TMAX = 20;
+constexpr int EXT = 2 * TMAX + 6;   // 46 half units per axis
+constexpr int NPX = EXT + 1;        // 47, odd
+constexpr int NPP = NPX * EXT + 1;  // 2163, odd
+constexpr int NELEM = ((EXT - 1) + (EXT - 1) * NPX + (EXT - 1) * NPP + 1) / 2 + 1;
+constexpr int BOX_BYTES = (NELEM * 2 + 15) / 16 * 16;
+// element of box point (x, y, z), x + y + z odd
+__host__ __device__ constexpr int eidx(int x, int y, int z) { return (x + y * NPX + z * NPP + 1) / 2; }
+// element offset of a lattice vector (even coordinate sum)
+__host__ __device__ constexpr int voff(int x, int y, int z) { return (x + y * NPX + z * NPP) / 2; }
+__host__ __device__ constexpr int bx_of(int b) { return (b == 1 || b == 2) ? 1 : 0; }
+__host__ __device__ constexpr int by_of(int b) { return (b == 1 || b == 3) ? 1 : 0; }
+__host__ __device__ constexpr int bz_of(int b) { return (b == 2 || b == 3) ? 1 : 0; }
+__host__ __device__ constexpr int fshift(int k) { return k == 0 ? 3 : k == 1 ? 7 : 10; }
+__host__ __device__ constexpr int fmask(int k) { return k == 0 ? 15 : k == 1 ? 7 : 31; }
+__device__ __forceinline__ int field_rt(uint32_t v, int k) {
+  return k == 0 ? (int)((v >> 3) & 15u) : k == 1 ? (int)((v >> 7) & 7u) : (int)((v >> 10) & 31u);
+}
+// packed count word of the per-shell counts n[0..K-1]
 template <int K>
-__global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const QsroTables Q) {
+__device__ __forceinline__ uint32_t pack_counts(const int (&n)[K]) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) w |= (uint32_t)n[k] << (fshift(k) - 3);
+  return w;
+}
+// The environment sites whose counts a trial along partner direction d can
+// change, ordered by class so that the kernel's loops see every class at a
+// compile-time position: es[d][i] (sites t = s + v of the environment of s,
+// class (k1 = shell of t around s, k2 = shell of t around s' or -1 outside
+// the K shells), t != s' and k1 != k2), then ep[d][i] (sites t = s' + v
+// outside the environment of s and != s, class k = shell around s').  The
+// classes' sizes are the same for all 12 directions (they are images of one
+// another under the cubic group); `ok` checks that.  Entries are element
+// offsets in the count box.
+__host__ __device__ constexpr int fcc_shell(int x, int y, int z, int K) {
+  const int r = x * x + y * y + z * z;
+  const int k = r == 2 ? 0 : r == 4 ? 1 : r == 6 ? 2 : -1;
+  return k < K ? k : -1;
+}
+template <int K>
+struct QClass {
+  short es[12][42], ep[12][42];
+  int k1[42], k2[42], kp[42];  // class of slot i
+  int NS, NP;
+  bool ok;
+};
+template <int K>
+__host__ __device__ constexpr QClass<K> make_qclass() {
+  constexpr qfcc::QTable T = qfcc::make_qvecs();
+  constexpr int NV = vec_count(kFCC, K);
+  QClass<K> q{};
+  q.ok = true;
+  for (int d = 0; d < 12; d++) {
+    const int px = T.v[d].x, py = T.v[d].y, pz = T.v[d].z;
+    int n = 0;
+    for (int a = 0; a < K; a++)
+      for (int b = -1; b < K; b++) {
+        if (b == a) continue;
+        for (int j = 0; j < NV; j++) {
+          if (T.v[j].k != a) continue;
+          const int ux = T.v[j].x - px, uy = T.v[j].y - py, uz = T.v[j].z - pz;
+          if (ux == 0 && uy == 0 && uz == 0) continue;
+          if (fcc_shell(ux, uy, uz, K) != b) continue;
+          if (d == 0) {
+            q.k1[n] = a;
+            q.k2[n] = b;
+          } else if (q.k1[n] != a || q.k2[n] != b) {
+            q.ok = false;
+          }
+          q.es[d][n++] = (short)voff(T.v[j].x, T.v[j].y, T.v[j].z);
+        }
+      }
+    if (d == 0) q.NS = n;
+    else if (n != q.NS) q.ok = false;
+    int m = 0;
+    for (int a = 0; a < K; a++)
+      for (int j = 0; j < NV; j++) {
+        if (T.v[j].k != a) continue;
+        const int wx = T.v[j].x + px, wy = T.v[j].y + py, wz = T.v[j].z + pz;
+        if ((wx == 0 && wy == 0 && wz == 0) || fcc_shell(wx, wy, wz, K) >= 0) continue;
+        if (d == 0) q.kp[m] = a;
+        else if (q.kp[m] != a) q.ok = false;
+        q.ep[d][m++] = (short)voff(T.v[j].x, T.v[j].y, T.v[j].z);
+      }
+    if (d == 0) q.NP = m;
+    else if (m != q.NP) q.ok = false;
+  }
+  return q;
+}
+static_assert(make_qclass<2>().ok && make_qclass<3>().ok, "class sizes differ between partner directions");
+__constant__ QClass<2> c_qclass2 = make_qclass<2>();
+__constant__ QClass<3> c_qclass3 = make_qclass<3>();
+template <int K>
+__device__ __forceinline__ const QClass<K>& qclass();
+template <>
+__device__ __forceinline__ const QClass<2>& qclass<2>() { return c_qclass2; }
+template <>
+__device__ __forceinline__ const QClass<3>& qclass<3>() { return c_qclass3; }
+}  // namespace qfn
+
+// Counts of every site of the tile (all tiles in one launch): species staged
+// in the even-point box, n_k(i) counted there, one 16-bit
+// word per site (n_0 | n_1 << 4 | n_2 << 7) written to cnt[4 cell + b].
+template <int K>
+__global__ void __launch_bounds__(128) k_qsro_fcc_count_init(const SweepParams P, uint16_t* __restrict__ cnt) {
   using namespace qfcc;
-  constexpr QTable T = make_qvecs();
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint8_t* box = smem;
+  int bid = blockIdx.x;
+  const int ti[3] = {bid % P.nt[0], (bid / P.nt[0]) % P.nt[1], bid / (P.nt[0] * P.nt[1])};
+  int t0[3], ts[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const int base = P.n[a] / P.nt[a], rem = P.n[a] % P.nt[a];
+    ts[a] = base + (ti[a] < rem ? 1 : 0);
+    t0[a] = ti[a] * base + min(ti[a], rem);
+  }
+  stage_box(P, box, t0, ts);
+  __syncthreads();
+  const int nx = P.n[0], ny = P.n[1];
+  const int ncell = ts[0] * ts[1] * ts[2];
+  for (int i = threadIdx.x; i < 4 * ncell; i += blockDim.x) {
+    const int b = i & 3, c = i >> 2;
+    const int xr = c % ts[0], yr = (c / ts[0]) % ts[1], zr = c / (ts[0] * ts[1]);
+    const int t = hoff(2 * (xr + H), 2 * (yr + H), 2 * (zr + H)) + boff(b);
+    const int sp = box[t];
+    uint32_t w = (uint32_t)count_shell<0>(box, t, sp) | ((uint32_t)count_shell<1>(box, t, sp) << 4);
+    if (K > 2) w |= (uint32_t)count_shell<2>(box, t, sp) << 7;
+    const long long cell = ((long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
+    cnt[4 * cell + b] = (uint16_t)w;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, 2)
+    k_qsro_fcc_n(const SweepParams P, const QsroTables Q, uint16_t* __restrict__ cnt) {
+  using namespace qfn;
+  constexpr qfcc::QTable T = qfcc::make_qvecs();
   constexpr int NV = vec_count(kFCC, K);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
-  __shared__ signed char s_k2[12 * NV], s_ins[12 * NV];
+  constexpr QClass<K> QC = make_qclass<K>();
+  constexpr int NS = QC.NS, NP = QC.NP;
+  __shared__ short s_es[12 * NS], s_ep[12 * NP];
   __shared__ int s_qoff[NV];
 
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int M = P.M, KM = K * P.M, MM = P.M * P.M;
   const int nW = MM * KM + MM;
-  uint8_t* box = smem;
+  uint16_t* box = reinterpret_cast<uint16_t*>(smem);
   int32_t* s_w = reinterpret_cast<int32_t*>(smem + BOX_BYTES);
 
   int bid = blockIdx.x;
@@ -409,37 +559,40 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
   if (tid < 3) s_stat[tid] = 0;
   for (int i = tid; i < nW; i += nth) s_w[i] = P.wtab[i];
   for (int i = tid; i < KM; i += nth) s_wq[i] = Q.W[i];
-  for (int i = tid; i < 12 * NV; i += nth) {
-    s_k2[i] = Q.k2[i / NV][i % NV];
-    s_ins[i] = Q.in_s[i / NV][i % NV];
-  }
+  for (int i = tid; i < 12 * NS; i += nth) s_es[i] = qclass<K>().es[i / NS][i % NS];
+  for (int i = tid; i < 12 * NP; i += nth) s_ep[i] = qclass<K>().ep[i / NP][i % NP];
   if (tid < NV) {
     int o = 0;
 #pragma unroll
     for (int j = 0; j < NV; j++)
-      if (j == tid) o = hoff(T.v[j].x, T.v[j].y, T.v[j].z);
+      if (j == tid) o = voff(T.v[j].x, T.v[j].y, T.v[j].z);
     s_qoff[tid] = o;  // the first 12 entries are the partner offsets
   }
 
-  // stage tile + 3-cell halo, 8 rows of loads in flight per lane
-  const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
+  // stage the cells [t0 - 2, t0 + ts + 2) of each axis: species and counts,
+  // the sites inside the box (box coordinate 2 i - 1 + basis in [0, 2 ts + 5])
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const int ex = ts[0] + 4, ey = ts[1] + 4, ez = ts[2] + 4;
+  const int lim[3] = {2 * ts[0] + 5, 2 * ts[1] + 5, 2 * ts[2] + 5};
   {
-    constexpr int U = 8;
+    constexpr int U = 4;
     const int rows = ey * ez;
-    const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
+    const int gx = lane < ex ? wrap_add(t0[0] - 2, lane, nx) : 0;
     for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
       uint32_t v[U];
+      uint2 c4[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int row = row0 + u;
         v[u] = 0;
+        c4[u] = make_uint2(0, 0);
         if (row < rows && lane < ex) {
           const int ys = row % ey, zs = row / ey;
           const long long cell =
-              ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+              ((long long)wrap_add(t0[2] - 2, zs, nz) * ny + wrap_add(t0[1] - 2, ys, ny)) * nx + gx;
           v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
                                         : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+          c4[u] = *reinterpret_cast<const uint2*>(cnt + 4 * cell);
         }
       }
 #pragma unroll
@@ -447,11 +600,14 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
         const int row = row0 + u;
         if (row < rows && lane < ex) {
           const int ys = row % ey, zs = row / ey;
-          const int base = hoff(2 * lane, 2 * ys, 2 * zs);
 #pragma unroll
-          for (int b = 0; b < 4; b++)
-            box[base + boff(b)] =
-                (uint8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+          for (int b = 0; b < 4; b++) {
+            const int x = 2 * lane - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
+            if (x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]) continue;
+            const uint32_t sp = P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
+            const uint32_t cw = ((b < 2 ? c4[u].x : c4[u].y) >> (16 * (b & 1))) & 0xFFFFu;
+            box[eidx(x, y, z)] = (uint16_t)(sp | (cw << 3));
+          }
         }
       }
     }
@@ -469,7 +625,7 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
       for (int cx = 0; cx < L; cx++) {
         const int xr = cx + L * qx, yr = cy + L * qy, zr = cz + L * qz;
         const bool here = slot && xr < ts[0] && yr < ts[1] && zr < ts[2];
-        const int cbase = hoff(2 * (xr + H), 2 * (yr + H), 2 * (zr + H));
+        const int cbase = eidx(2 * xr + 3, 2 * yr + 3, 2 * zr + 3);
         const unsigned long long cell = ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
         uint4 rw = make_uint4(0, 0, 0, 0);
         for (int b = 0; b < 4; b++) {
@@ -477,52 +633,93 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
             if ((b & 1) == 0) rw = attempt_block(cell * 4 + b, P.sweep, P.replica, P.seed_lo, P.seed_hi);
             const uint32_t rd = (b & 1) ? rw.z : rw.x;
             const uint32_t ru = (b & 1) ? rw.w : rw.y;
-            const int s = cbase + boff(b);
+            const int s = cbase + voff(bx_of(b), by_of(b), bz_of(b));
             const int dir = (int)__umulhi(rd, 12u);
             const int po = s_qoff[dir];
             const int sp = s + po;
-            const int sa = box[s], sb = box[sp];
+            const int sa = box[s] & 7, sb = box[sp] & 7;
             if (sa == sb) {
               same++;
             } else {
               const int32_t* W = s_w + (sa * M + sb) * KM;
               int dE = s_w[MM * KM + sa * M + sb];
+              // pair part and the counts of s and s' after the swap: a and b
+              // around s and around s' (s' holds b and s holds a before the
+              // swap: each is taken out of the other's count afterwards)
               int na_s[K], nb_s[K], na_p[K], nb_p[K];
 #pragma unroll
               for (int k = 0; k < K; k++) na_s[k] = nb_s[k] = na_p[k] = nb_p[k] = 0;
 #pragma unroll
               for (int j = 0; j < NV; j++) {
-                const int k = T.v[j].k, o = hoff(T.v[j].x, T.v[j].y, T.v[j].z);
-                const int c = box[s + o];
+                const int k = T.v[j].k, o = voff(T.v[j].x, T.v[j].y, T.v[j].z);
+                const int c = box[s + o] & 7;
                 dE += W[k * M + c];
-                if (o != po) {
-                  na_s[k] += (c == sa);
-                  nb_s[k] += (c == sb);
-                }
-                const int cp = box[sp + o];
+                na_s[k] += (c == sa);
+                nb_s[k] += (c == sb);
+                const int cp = box[sp + o] & 7;
                 dE -= W[k * M + cp];
-                if (o != -po) {
-                  na_p[k] += (cp == sa);
-                  nb_p[k] += (cp == sb);
+                na_p[k] += (cp == sa);
+                nb_p[k] += (cp == sb);
+              }
+              nb_s[0]--;
+              na_p[0]--;
+              int wqa[K], wqb[K];
+#pragma unroll
+              for (int k = 0; k < K; k++) {
+                wqa[k] = s_wq[k * M + sa];
+                wqb[k] = s_wq[k * M + sb];
+                dE += wqb[k] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) + wqa[k] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
+              }
+              // environment sites whose counts move, branch-free: d = +1
+              // (the site holds b), -1 (a) or 0 (another species); a count
+              // n moving by d changes the term by W (2 n d + d^2)
+              const short* es = s_es + dir * NS;
+              const short* ep = s_ep + dir * NP;
+#pragma unroll
+              for (int i = 0; i < NS; i++) {
+                const uint32_t w = box[s + es[i]];
+                const int c = (int)(w & 7u);
+                const bool isb = c == sb, isa = c == sa;
+                const int d = (int)isb - (int)isa, ad = (int)(isb | isa);
+                const int k1 = QC.k1[i], k2 = QC.k2[i];
+                const int n1 = (int)((w >> fshift(k1)) & (uint32_t)fmask(k1));
+                dE += (isb ? wqb[k1] : wqa[k1]) * (2 * d * n1 + ad);
+                if (k2 >= 0) {
+                  const int n2 = (int)((w >> fshift(k2)) & (uint32_t)fmask(k2));
+                  dE += (isb ? wqb[k2] : wqa[k2]) * (ad - 2 * d * n2);
                 }
               }
 #pragma unroll
-              for (int k = 0; k < K; k++)
-                dE += s_wq[k * M + sb] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) +
-                      s_wq[k * M + sa] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
-              // sites of the environment of s whose terms change, then those
-              // that see only s'
-              const signed char* k2row = s_k2 + dir * NV;
-              const signed char* insrow = s_ins + dir * NV;
-              dE += env_s_shell<0>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
-              dE += env_s_shell<1>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
-              if (K > 2) dE += env_s_shell<2>(box, s_qoff, k2row, s_wq, M, s, sa, sb);
-              dE += env_p_shell<0>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
-              dE += env_p_shell<1>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
-              if (K > 2) dE += env_p_shell<2>(box, s_qoff, insrow, s_wq, M, sp, sa, sb);
+              for (int i = 0; i < NP; i++) {
+                const uint32_t w = box[sp + ep[i]];
+                const int c = (int)(w & 7u);
+                const bool isb = c == sb, isa = c == sa;
+                const int d = (int)isa - (int)isb, ad = (int)(isb | isa);
+                const int k = QC.kp[i];
+                const int n = (int)((w >> fshift(k)) & (uint32_t)fmask(k));
+                dE += (isb ? wqb[k] : wqa[k]) * (2 * d * n + ad);
+              }
               if (metropolis_accept(dE, ru, P.thr, P.nA, P.thr + kNA)) {
-                box[s] = (uint8_t)sb;
-                box[sp] = (uint8_t)sa;
+                box[s] = (uint16_t)(sb | (pack_counts<K>(nb_s) << 3));
+                box[sp] = (uint16_t)(sa | (pack_counts<K>(na_p) << 3));
+#pragma unroll
+                for (int i = 0; i < NS; i++) {
+                  const int t = s + es[i];
+                  const uint32_t w = box[t];
+                  const int c = (int)(w & 7u);
+                  const int d = (int)(c == sb) - (int)(c == sa);
+                  const int k1 = QC.k1[i], k2 = QC.k2[i];
+                  const int dw = d * ((1 << fshift(k1)) - (k2 >= 0 ? (1 << fshift(k2)) : 0));
+                  if (d != 0) box[t] = (uint16_t)((int)w + dw);
+                }
+#pragma unroll
+                for (int i = 0; i < NP; i++) {
+                  const int t = sp + ep[i];
+                  const uint32_t w = box[t];
+                  const int c = (int)(w & 7u);
+                  const int d = (int)(c == sa) - (int)(c == sb);
+                  if (d != 0) box[t] = (uint16_t)((int)w + d * (1 << fshift(QC.kp[i])));
+                }
                 acc++;
                 dsum += dE;
               }
@@ -532,23 +729,39 @@ __global__ void __launch_bounds__(128, 3) k_qsro_fcc(const SweepParams P, const 
         }
       }
 
-  // write back tile + 1-cell partner ring
-  const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
-  for (int row = warp; row < wy * wz; row += nwarp) {
-    const int yw = row % wy, zw = row / wy;
-    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
+  // write back the species of the tile and its 1-cell ring, the counts of
+  // every site in the box
+  for (int row = warp; row < ey * ez; row += nwarp) {
+    const int ys = row % ey, zs = row / ey;
+    const int gy = wrap_add(t0[1] - 2, ys, ny), gz = wrap_add(t0[2] - 2, zs, nz);
     const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xw = lane; xw < wx; xw += 32) {
-      const long long cell = rbase + wrap_add(t0[0] - 1, xw, nx);
-      const int base = hoff(2 * (xw + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
-      uint32_t s4[4];
+    for (int xs = lane; xs < ex; xs += 32) {
+      const long long cell = rbase + wrap_add(t0[0] - 2, xs, nx);
+      uint32_t w4[4];
+      bool in[4];
 #pragma unroll
-      for (int b = 0; b < 4; b++) s4[b] = box[base + boff(b)];
-      if (P.storage == SMCX_INT8)
-        *reinterpret_cast<uint32_t*>(P.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
-      else
-        *reinterpret_cast<uint16_t*>(P.sites + 2 * cell) =
-            (uint16_t)(s4[0] | (s4[1] << 4) | (s4[2] << 8) | (s4[3] << 12));
+      for (int b = 0; b < 4; b++) {
+        const int x = 2 * xs - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
+        in[b] = !(x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]);
+        w4[b] = in[b] ? box[eidx(x, y, z)] : 0u;
+      }
+      if (in[0] && in[1] && in[2] && in[3]) {
+        *reinterpret_cast<uint2*>(cnt + 4 * cell) =
+            make_uint2((w4[0] >> 3) | ((w4[1] >> 3) << 16), (w4[2] >> 3) | ((w4[3] >> 3) << 16));
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (in[b]) cnt[4 * cell + b] = (uint16_t)(w4[b] >> 3);
+      }
+      const bool ring = xs >= 1 && xs <= ts[0] + 2 && ys >= 1 && ys <= ts[1] + 2 && zs >= 1 && zs <= ts[2] + 2;
+      if (ring) {
+        if (P.storage == SMCX_INT8)
+          *reinterpret_cast<uint32_t*>(P.sites + 4 * cell) =
+              (w4[0] & 7u) | ((w4[1] & 7u) << 8) | ((w4[2] & 7u) << 16) | ((w4[3] & 7u) << 24);
+        else
+          *reinterpret_cast<uint16_t*>(P.sites + 2 * cell) =
+              (uint16_t)((w4[0] & 7u) | ((w4[1] & 7u) << 4) | ((w4[2] & 7u) << 8) | ((w4[3] & 7u) << 12));
+      }
     }
   }
   atomicAdd(&s_stat[0], acc);
@@ -743,27 +956,34 @@ void sweep_qsro_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps
   // FCC with tiles of at most 20 cells, link cells >= 4, 5^3 slots at most,
   // a 4-byte aligned store: the even-point kernel
   const int tm = std::max(tmax[0], std::max(tmax[1], tmax[2]));
+  const int tmin = std::min(hd->n[0] / sc.nt[0], std::min(hd->n[1] / sc.nt[1], hd->n[2] / sc.nt[2]));
   const int nq = (tm + sc.L - 1) / sc.L;
-  if (hd->kind == kFCC && K >= 2 && tm <= qfcc::TMAX && nq * nq * nq <= 128 &&
+  // FCC, 2 or 3 shells, tiles of 3 to 20 cells: the maintained-count kernel,
+  // after one launch that counts every site's same-species neighbours (tiles
+  // of >= 3 cells keep the boxes of one colour, and a box and its own
+  // periodic image, apart)
+  if (hd->kind == kFCC && (K == 2 || K == 3) && tm <= qfn::TMAX && tmin >= 3 && nq * nq * nq <= 128 &&
       reinterpret_cast<uintptr_t>(P.sites) % 4 == 0) {
+    const long long ncell = (long long)hd->n[0] * hd->n[1] * hd->n[2];
+    if (!hd->d_qcnt) check_cuda(cudaMalloc(&hd->d_qcnt, (size_t)ncell * 4 * sizeof(uint16_t)), "qSRO count array");
+    auto init = K == 2 ? k_qsro_fcc_count_init<2> : k_qsro_fcc_count_init<3>;
+    check_cuda(cudaFuncSetAttribute(init, cudaFuncAttributeMaxDynamicSharedMemorySize, qfcc::BOX_BYTES),
+               "qSRO count smem attribute");
+    init<<<sc.nt[0] * sc.nt[1] * sc.nt[2], 128, qfcc::BOX_BYTES, hd->stream>>>(P, hd->d_qcnt);
     const int nW = P.M * P.M * K * P.M + P.M * P.M;
-    const size_t smem = qfcc::BOX_BYTES + (size_t)nW * 4;
-    auto run = [&](auto kern) {
-      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                 "qSRO FCC smem attribute");
-      check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
-                 "qSRO FCC carveout");
-      for (int64_t sw = 0; sw < n_sweeps; sw++) {
-        P.sweep = hd->sweep_cum + (uint64_t)sw;
-        for (int tc = 0; tc < n_colours; tc++) {
-          P.tc = tc;
-          kern<<<P.ntc[0] * P.ntc[1] * P.ntc[2], 128, smem, hd->stream>>>(P, T);
-        }
+    const size_t smem = qfn::BOX_BYTES + (size_t)nW * 4;
+    auto kern = K == 2 ? k_qsro_fcc_n<2> : k_qsro_fcc_n<3>;
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "qSRO FCC smem attribute");
+    check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100), "qSRO FCC carveout");
+    for (int64_t sw = 0; sw < n_sweeps; sw++) {
+      P.sweep = hd->sweep_cum + (uint64_t)sw;
+      for (int tc = 0; tc < n_colours; tc++) {
+        P.tc = tc;
+        kern<<<P.ntc[0] * P.ntc[1] * P.ntc[2], 128, smem, hd->stream>>>(P, T, hd->d_qcnt);
       }
-      check_cuda(cudaGetLastError(), "qSRO FCC sweep launch");
-    };
-    if (K == 2) run(k_qsro_fcc<2>);
-    else run(k_qsro_fcc<3>);
+    }
+    check_cuda(cudaGetLastError(), "qSRO FCC sweep launch");
     return;
   }
   if (hd->kind == kBCC) {
