@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--only", default="", choices=["", "batched", "exchange", "gradient", "clusters", "qsro",
                                                     "throughput", "anneal", "fcc", "paper", "baselines",
-                                                    "batch_launch"],
+                                                    "batch_launch", "qsro_launch"],
                     help="profiling only: run one secondary measurement and print its JSON")
     ap.add_argument("--edge", type=int, default=0,
                     help="profiling only: lattice edge of the fcc / qsro / clusters measurement")
@@ -356,6 +356,37 @@ def run_batch_launch(stream, proposal, sched):
         l.close()
     return {"proposal": proposal, "schedule": [L, target, threads], "ms_launch": e0.elapsed_time(e1),
             "grid": info["grid"], "threads": info["threads"], "sites": sum(2 * int(n) ** 3 for n in edges)}
+
+
+def run_qsro_launch(stream, edge=0):
+    """Profiling aid: the qSRO workload (FCC 400^3 unless --edge) with the
+    schedule of its bench line fixed (link cells of 4, 20 tiles per axis),
+    one warm-up sweep and one more sweep, so that a profiler can capture a
+    launch of the second sweep alone (skip the first sweep's 8)."""
+    import torch
+    from paper_2503_12591_gb300 import smcx
+    from paper_2503_12591_gb300.inputs import SCALE_FCC400 as W_
+
+    if edge:
+        import dataclasses
+        W_ = dataclasses.replace(W_, dims=(edge,) * 3)
+    W = np.random.default_rng(77).integers(-300, 301, (W_.K, W_.M)).astype(np.int32)
+    lat = smcx.Lattice(W_.kind, W_.dims, W_.M, W_.comp, init_seed=W_.init_seed, storage=W_.storage, stream=stream)
+    lat.set_epi(W_.epi())
+    lat.set_qsro(W)
+    nt = 2
+    while -(-W_.dims[0] // nt) > 20:
+        nt += 2
+    lat.set_schedule((4, (nt, nt, nt)))
+    lat.sweep(1000.0, 1, SEED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.sweep(1000.0, 1, SEED)
+    e1.record(stream)
+    e1.synchronize()
+    lat.close()
+    return {"edge": W_.dims[0], "schedule": [4, nt], "ms_sweep": e0.elapsed_time(e1)}
 
 
 def run_exchange(stream):
@@ -1152,7 +1183,8 @@ def main():
               "throughput": run_throughput256, "anneal": run_anneal, "baselines": run_baselines,
               "fcc": lambda st: run_fcc(st, args.edge), "paper": run_paper_rows,
               "clusters": lambda st: run_clusters(st, args.edge), "qsro": lambda st: run_qsro(st, args.edge),
-              "batch_launch": lambda st: run_batch_launch(st, args.proposal, args.batch_sched)}
+              "batch_launch": lambda st: run_batch_launch(st, args.proposal, args.batch_sched),
+              "qsro_launch": lambda st: run_qsro_launch(st, args.edge)}
         print(json.dumps({args.only: fn[args.only](stream)}), flush=True)
     else:
         run_smcx(args, rank, world, local_rank)

@@ -388,16 +388,21 @@ __device__ __forceinline__ void stage_box(const SweepParams& P, uint8_t* box, co
 // share a site whose count either of them changes or writes.
 // ---------------------------------------------------------------------------
 namespace qfn {
+// Box of tiles of at most TM cells: 2 TM + 6 half units per axis (even), odd
+// pitches.  TM = 20 (101 KB, 2 CTAs per SM) and TM = 17 (66 KB, 3 CTAs).
+template <int TM>
+struct QBox {
+  static constexpr int EXT = 2 * TM + 6;
+  static constexpr int NPX = EXT + 1;
+  static constexpr int NPP = NPX * EXT + 1;
+  static constexpr int NELEM = ((EXT - 1) + (EXT - 1) * NPX + (EXT - 1) * NPP + 1) / 2 + 1;
+  static constexpr int BOX_BYTES = (NELEM * 2 + 15) / 16 * 16;
+  // element of box point (x, y, z), x + y + z odd
+  __host__ __device__ static constexpr int eidx(int x, int y, int z) { return (x + y * NPX + z * NPP + 1) / 2; }
+  // element offset of a lattice vector (even coordinate sum)
+  __host__ __device__ static constexpr int voff(int x, int y, int z) { return (x + y * NPX + z * NPP) / 2; }
+};
 constexpr int TMAX = 20;
-constexpr int EXT = 2 * TMAX + 6;   // 46 half units per axis
-constexpr int NPX = EXT + 1;        // 47, odd
-constexpr int NPP = NPX * EXT + 1;  // 2163, odd
-constexpr int NELEM = ((EXT - 1) + (EXT - 1) * NPX + (EXT - 1) * NPP + 1) / 2 + 1;
-constexpr int BOX_BYTES = (NELEM * 2 + 15) / 16 * 16;
-// element of box point (x, y, z), x + y + z odd
-__host__ __device__ constexpr int eidx(int x, int y, int z) { return (x + y * NPX + z * NPP + 1) / 2; }
-// element offset of a lattice vector (even coordinate sum)
-__host__ __device__ constexpr int voff(int x, int y, int z) { return (x + y * NPX + z * NPP) / 2; }
 __host__ __device__ constexpr int bx_of(int b) { return (b == 1 || b == 2) ? 1 : 0; }
 __host__ __device__ constexpr int by_of(int b) { return (b == 1 || b == 3) ? 1 : 0; }
 __host__ __device__ constexpr int bz_of(int b) { return (b == 2 || b == 3) ? 1 : 0; }
@@ -435,7 +440,7 @@ struct QClass {
   int NS, NP;
   bool ok;
 };
-template <int K>
+template <int K, int TM>
 __host__ __device__ constexpr QClass<K> make_qclass() {
   constexpr qfcc::QTable T = qfcc::make_qvecs();
   constexpr int NV = vec_count(kFCC, K);
@@ -458,7 +463,7 @@ __host__ __device__ constexpr QClass<K> make_qclass() {
           } else if (q.k1[n] != a || q.k2[n] != b) {
             q.ok = false;
           }
-          q.es[d][n++] = (short)voff(T.v[j].x, T.v[j].y, T.v[j].z);
+          q.es[d][n++] = (short)QBox<TM>::voff(T.v[j].x, T.v[j].y, T.v[j].z);
         }
       }
     if (d == 0) q.NS = n;
@@ -471,22 +476,23 @@ __host__ __device__ constexpr QClass<K> make_qclass() {
         if ((wx == 0 && wy == 0 && wz == 0) || fcc_shell(wx, wy, wz, K) >= 0) continue;
         if (d == 0) q.kp[m] = a;
         else if (q.kp[m] != a) q.ok = false;
-        q.ep[d][m++] = (short)voff(T.v[j].x, T.v[j].y, T.v[j].z);
+        q.ep[d][m++] = (short)QBox<TM>::voff(T.v[j].x, T.v[j].y, T.v[j].z);
       }
     if (d == 0) q.NP = m;
     else if (m != q.NP) q.ok = false;
   }
   return q;
 }
-static_assert(make_qclass<2>().ok && make_qclass<3>().ok, "class sizes differ between partner directions");
-__constant__ QClass<2> c_qclass2 = make_qclass<2>();
-__constant__ QClass<3> c_qclass3 = make_qclass<3>();
-template <int K>
-__device__ __forceinline__ const QClass<K>& qclass();
-template <>
-__device__ __forceinline__ const QClass<2>& qclass<2>() { return c_qclass2; }
-template <>
-__device__ __forceinline__ const QClass<3>& qclass<3>() { return c_qclass3; }
+static_assert(make_qclass<2, 20>().ok && make_qclass<3, 20>().ok, "class sizes differ between partner directions");
+__constant__ QClass<2> c_qclass2_20 = make_qclass<2, 20>();
+__constant__ QClass<3> c_qclass3_20 = make_qclass<3, 20>();
+__constant__ QClass<2> c_qclass2_17 = make_qclass<2, 17>();
+__constant__ QClass<3> c_qclass3_17 = make_qclass<3, 17>();
+template <int K, int TM>
+__device__ __forceinline__ const QClass<K>& qclass() {
+  if constexpr (K == 2) return TM == 20 ? c_qclass2_20 : c_qclass2_17;
+  else return TM == 20 ? c_qclass3_20 : c_qclass3_17;
+}
 }  // namespace qfn
 
 // Counts of every site of the tile (all tiles in one launch): species staged
@@ -522,16 +528,18 @@ __global__ void __launch_bounds__(128) k_qsro_fcc_count_init(const SweepParams P
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(128, 2)
+template <int K, int TM>
+__global__ void __launch_bounds__(128, TM == 20 ? 2 : 3)
     k_qsro_fcc_n(const SweepParams P, const QsroTables Q, uint16_t* __restrict__ cnt) {
   using namespace qfn;
+  using BX = QBox<TM>;
+  constexpr int BOX_BYTES = BX::BOX_BYTES;
   constexpr qfcc::QTable T = qfcc::make_qvecs();
   constexpr int NV = vec_count(kFCC, K);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   __shared__ int32_t s_wq[kMaxShells * kMaxSweepM];
-  constexpr QClass<K> QC = make_qclass<K>();
+  constexpr QClass<K> QC = make_qclass<K, TM>();
   constexpr int NS = QC.NS, NP = QC.NP;
   __shared__ short s_es[12 * NS], s_ep[12 * NP];
   __shared__ int s_qoff[NV];
@@ -559,13 +567,13 @@ __global__ void __launch_bounds__(128, 2)
   if (tid < 3) s_stat[tid] = 0;
   for (int i = tid; i < nW; i += nth) s_w[i] = P.wtab[i];
   for (int i = tid; i < KM; i += nth) s_wq[i] = Q.W[i];
-  for (int i = tid; i < 12 * NS; i += nth) s_es[i] = qclass<K>().es[i / NS][i % NS];
-  for (int i = tid; i < 12 * NP; i += nth) s_ep[i] = qclass<K>().ep[i / NP][i % NP];
+  for (int i = tid; i < 12 * NS; i += nth) s_es[i] = (qclass<K, TM>().es)[i / NS][i % NS];
+  for (int i = tid; i < 12 * NP; i += nth) s_ep[i] = (qclass<K, TM>().ep)[i / NP][i % NP];
   if (tid < NV) {
     int o = 0;
 #pragma unroll
     for (int j = 0; j < NV; j++)
-      if (j == tid) o = voff(T.v[j].x, T.v[j].y, T.v[j].z);
+      if (j == tid) o = BX::voff(T.v[j].x, T.v[j].y, T.v[j].z);
     s_qoff[tid] = o;  // the first 12 entries are the partner offsets
   }
 
@@ -606,7 +614,7 @@ __global__ void __launch_bounds__(128, 2)
             if (x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]) continue;
             const uint32_t sp = P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
             const uint32_t cw = ((b < 2 ? c4[u].x : c4[u].y) >> (16 * (b & 1))) & 0xFFFFu;
-            box[eidx(x, y, z)] = (uint16_t)(sp | (cw << 3));
+            box[BX::eidx(x, y, z)] = (uint16_t)(sp | (cw << 3));
           }
         }
       }
@@ -625,7 +633,7 @@ __global__ void __launch_bounds__(128, 2)
       for (int cx = 0; cx < L; cx++) {
         const int xr = cx + L * qx, yr = cy + L * qy, zr = cz + L * qz;
         const bool here = slot && xr < ts[0] && yr < ts[1] && zr < ts[2];
-        const int cbase = eidx(2 * xr + 3, 2 * yr + 3, 2 * zr + 3);
+        const int cbase = BX::eidx(2 * xr + 3, 2 * yr + 3, 2 * zr + 3);
         const unsigned long long cell = ((unsigned long long)(t0[2] + zr) * ny + (t0[1] + yr)) * nx + (t0[0] + xr);
         uint4 rw = make_uint4(0, 0, 0, 0);
         for (int b = 0; b < 4; b++) {
@@ -633,7 +641,7 @@ __global__ void __launch_bounds__(128, 2)
             if ((b & 1) == 0) rw = attempt_block(cell * 4 + b, P.sweep, P.replica, P.seed_lo, P.seed_hi);
             const uint32_t rd = (b & 1) ? rw.z : rw.x;
             const uint32_t ru = (b & 1) ? rw.w : rw.y;
-            const int s = cbase + voff(bx_of(b), by_of(b), bz_of(b));
+            const int s = cbase + BX::voff(bx_of(b), by_of(b), bz_of(b));
             const int dir = (int)__umulhi(rd, 12u);
             const int po = s_qoff[dir];
             const int sp = s + po;
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(128, 2)
               for (int k = 0; k < K; k++) na_s[k] = nb_s[k] = na_p[k] = nb_p[k] = 0;
 #pragma unroll
               for (int j = 0; j < NV; j++) {
-                const int k = T.v[j].k, o = voff(T.v[j].x, T.v[j].y, T.v[j].z);
+                const int k = T.v[j].k, o = BX::voff(T.v[j].x, T.v[j].y, T.v[j].z);
                 const int c = box[s + o] & 7;
                 dE += W[k * M + c];
                 na_s[k] += (c == sa);
@@ -743,7 +751,7 @@ __global__ void __launch_bounds__(128, 2)
       for (int b = 0; b < 4; b++) {
         const int x = 2 * xs - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
         in[b] = !(x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]);
-        w4[b] = in[b] ? box[eidx(x, y, z)] : 0u;
+        w4[b] = in[b] ? box[BX::eidx(x, y, z)] : 0u;
       }
       if (in[0] && in[1] && in[2] && in[3]) {
         *reinterpret_cast<uint2*>(cnt + 4 * cell) =
@@ -971,8 +979,10 @@ void sweep_qsro_device(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps
                "qSRO count smem attribute");
     init<<<sc.nt[0] * sc.nt[1] * sc.nt[2], 128, qfcc::BOX_BYTES, hd->stream>>>(P, hd->d_qcnt);
     const int nW = P.M * P.M * K * P.M + P.M * P.M;
-    const size_t smem = qfn::BOX_BYTES + (size_t)nW * 4;
-    auto kern = K == 2 ? k_qsro_fcc_n<2> : k_qsro_fcc_n<3>;
+    const bool small = tm <= 17;  // the 66 KB box: three CTAs per SM
+    const size_t smem = (small ? qfn::QBox<17>::BOX_BYTES : qfn::QBox<20>::BOX_BYTES) + (size_t)nW * 4;
+    auto kern = K == 2 ? (small ? k_qsro_fcc_n<2, 17> : k_qsro_fcc_n<2, 20>)
+                       : (small ? k_qsro_fcc_n<3, 17> : k_qsro_fcc_n<3, 20>);
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "qSRO FCC smem attribute");
     check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100), "qSRO FCC carveout");
