@@ -898,6 +898,34 @@ def run_baselines(stream):
     out["config3a"] = {"oracle_cores": r3p, "oracle_threads": used, "oracle_1core": r3s,
                        "sample": "OpenMP: one sweep of BCC 128^3 (4.2M sites); 1 core: one sweep of BCC 64^3; "
                                  "same model, temperature and proposal mode as the 800^3 workload"}
+    # config 3a in full: one sweep of the 1.024B-site lattice by the oracle (OpenMP) and by the GPU, from
+    # the same seeded equiatomic start (numpy), in the bench's schedule and proposal mode; compared bit for
+    # bit (configuration and statistics)
+    n_full = 2 * 800 ** 3
+    start = np.repeat(np.arange(WORK.M, dtype=np.int8), n_full // WORK.M)
+    np.random.default_rng(2024).shuffle(start)
+    lat = smcx.Lattice(smcx.BCC, (800, 800, 800), WORK.M, WORK.comp, init_seed=1, storage=smcx.PACKED4,
+                       sched=(4, (40, 40, 40)), stream=stream)
+    lat.set_config(start)
+    lat.set_epi(WORK.epi())
+    lat.set_proposal(PROPOSAL)
+    lat.sweep(T_KELVIN, 1, SEED)
+    got = lat.get_config()
+    st_gpu = lat.state()[1]
+    lat.close()
+    sig = start
+    del start
+    t0 = time.perf_counter()
+    st_orc, used = O.sweep_parallel(smcx.BCC, (800, 800, 800), WORK.M, WORK.K, WORK.epi(), sig, T_KELVIN, 1, SEED,
+                                    L=4, nt=(40, 40, 40), threads=cores, proposal=PROPOSAL)
+    dtf = time.perf_counter() - t0
+    out["config3a_full"] = {"oracle_cores": n_full / dtf, "oracle_threads": used, "seconds": dtf,
+                            "bit_exact_vs_gpu": bool((got == sig).all()) and st_orc.tolist() == st_gpu.tolist(),
+                            "sample": "in full: one sweep of the 1,024,000,000-site lattice (schedule L = 4, "
+                                      "40 tiles per axis, shared-direction proposals, 1200 K) from a seeded "
+                                      "equiatomic numpy start, the GPU's sweep from the same start compared "
+                                      "site by site"}
+    del got, sig
     # config 3b: FCC 400^3 5 species: oracle rate on FCC 64^3 (1 sweep)
     w = SCALE_FCC400
     V3 = w.epi()

@@ -194,3 +194,36 @@ def test_qsro_sweep_energies_trace(stream):
         assert E[i] == O.energy_qsro(kind, dims, M, K, V, W, ref)
     assert (lat.get_config() == ref).all()
     assert lat.state()[0] == 4
+
+
+@pytest.mark.parametrize("K,dims,M,storage,sched,calls", [
+    # tiles of 3 cells on two axes (the smallest the count kernel takes)
+    (3, (12, 6, 8), 5, smcx.PACKED4, (4, (4, 2, 2)), (1, 2, 1)),
+    (3, (6, 6, 6), 4, smcx.INT8, (4, (2, 2, 2)), (2, 2)),
+    # 17-cell tiles: the largest of the 66 KB box (three CTAs per SM)
+    (3, (34, 34, 20), 4, smcx.INT8, (4, (2, 2, 2)), (1, 1)),
+    # 18-cell tiles: the 101 KB box
+    (3, (36, 34, 20), 5, smcx.PACKED4, (4, (2, 2, 2)), (1, 1)),
+    # two shells, six species, 20-cell tiles
+    (2, (40, 40, 40), 6, smcx.PACKED4, (4, (2, 2, 2)), (1,)),
+])
+def test_qsro_count_kernel_shapes_and_calls(stream, K, dims, M, storage, sched, calls):
+    """The FCC maintained-count kernel at its tile-size limits, with several
+    sweep calls in a row: the counts are recomputed at the start of each
+    call and carried through its sweeps, so every call must continue the
+    oracle's trajectory bit for bit."""
+    V = epi_gaussian(K, M, 20.0, 41)
+    W = _w(K, M, 42)
+    lat = smcx.Lattice(smcx.FCC, dims, M, [1.0 / M] * M, init_seed=9, storage=storage, sched=sched, stream=stream)
+    lat.set_epi(V)
+    lat.set_qsro(W)
+    ref = lat.get_config()
+    done = 0
+    for n in calls:
+        lat.sweep(1000.0, n, 23)
+        st = O.sweep_qsro(smcx.FCC, dims, M, K, V, W, ref, 1000.0, n, 23, sweep0=done, L=sched[0], nt=sched[1])
+        done += n
+        assert (lat.get_config() == ref).all(), f"after {done} sweeps"
+    assert lat.state()[0] == done
+    assert lat.energy() == O.energy_qsro(smcx.FCC, dims, M, K, V, W, ref)
+    lat.close()
