@@ -493,6 +493,97 @@ __device__ __forceinline__ const QClass<K>& qclass() {
   if constexpr (K == 2) return TM == 20 ? c_qclass2_20 : c_qclass2_17;
   else return TM == 20 ? c_qclass3_20 : c_qclass3_17;
 }
+// Energy change of the environment-of-s slots [I0, I1): a site holding b
+// (d = +1) or a (d = -1) sees its count in the shell of s move by d and in
+// the shell of s' (if any) by -d; a count n moving by d changes the term by
+// W (2 n d + d^2); other species give d = 0.
+template <int K, int TM, int I0, int I1>
+__device__ __forceinline__ int es_energy(const uint16_t* box, const short* es, int s, int sa, int sb,
+                                         const int (&wqa)[K], const int (&wqb)[K]) {
+  constexpr QClass<K> QC = make_qclass<K, TM>();
+  int dE = 0;
+#pragma unroll
+  for (int i = I0; i < I1; i++) {
+    const uint32_t w = box[s + es[i]];
+    const int c = (int)(w & 7u);
+    const bool isb = c == sb, isa = c == sa;
+    const int d = (int)isb - (int)isa, ad = (int)(isb | isa);
+    const int k1 = QC.k1[i], k2 = QC.k2[i];
+    const int n1 = (int)((w >> fshift(k1)) & (uint32_t)fmask(k1));
+    dE += (isb ? wqb[k1] : wqa[k1]) * (2 * d * n1 + ad);
+    if (k2 >= 0) {
+      const int n2 = (int)((w >> fshift(k2)) & (uint32_t)fmask(k2));
+      dE += (isb ? wqb[k2] : wqa[k2]) * (ad - 2 * d * n2);
+    }
+  }
+  return dE;
+}
+// The count updates of the same slots after an accepted swap.
+template <int K, int TM, int I0, int I1>
+__device__ __forceinline__ void es_update(uint16_t* box, const short* es, int s, int sa, int sb) {
+  constexpr QClass<K> QC = make_qclass<K, TM>();
+#pragma unroll
+  for (int i = I0; i < I1; i++) {
+    const int t = s + es[i];
+    const uint32_t w = box[t];
+    const int c = (int)(w & 7u);
+    const int d = (int)(c == sb) - (int)(c == sa);
+    const int k1 = QC.k1[i], k2 = QC.k2[i];
+    const int dw = d * ((1 << fshift(k1)) - (k2 >= 0 ? (1 << fshift(k2)) : 0));
+    if (d != 0) box[t] = (uint16_t)((int)w + dw);
+  }
+}
+// Sites around s' outside the environment of s: a site holding a (d = +1)
+// or b (d = -1) sees its count in the shell of s' move by d.
+template <int K, int TM>
+__device__ __forceinline__ int ep_energy(const uint16_t* box, const short* ep, int sp, int sa, int sb,
+                                         const int (&wqa)[K], const int (&wqb)[K]) {
+  constexpr QClass<K> QC = make_qclass<K, TM>();
+  int dE = 0;
+#pragma unroll
+  for (int i = 0; i < QC.NP; i++) {
+    const uint32_t w = box[sp + ep[i]];
+    const int c = (int)(w & 7u);
+    const bool isb = c == sb, isa = c == sa;
+    const int d = (int)isa - (int)isb, ad = (int)(isb | isa);
+    const int k = QC.kp[i];
+    const int n = (int)((w >> fshift(k)) & (uint32_t)fmask(k));
+    dE += (isb ? wqb[k] : wqa[k]) * (2 * d * n + ad);
+  }
+  return dE;
+}
+template <int K, int TM>
+__device__ __forceinline__ void ep_update(uint16_t* box, const short* ep, int sp, int sa, int sb) {
+  constexpr QClass<K> QC = make_qclass<K, TM>();
+#pragma unroll
+  for (int i = 0; i < QC.NP; i++) {
+    const int t = sp + ep[i];
+    const uint32_t w = box[t];
+    const int c = (int)(w & 7u);
+    const int d = (int)(c == sa) - (int)(c == sb);
+    if (d != 0) box[t] = (uint16_t)((int)w + d * (1 << fshift(QC.kp[i])));
+  }
+}
+// Pair part around one end: sum_k sum_v W[k][c(e + v)] (SIGN +1 around s,
+// -1 around s'), with the counts of species a and b there.
+template <int K, int TM, int SIGN>
+__device__ __forceinline__ int pair_side(const uint16_t* box, int e, const int32_t* W, int M, int sa, int sb,
+                                         int (&na)[K], int (&nb)[K]) {
+  constexpr qfcc::QTable T = qfcc::make_qvecs();
+  constexpr int NV = vec_count(kFCC, K);
+  int dE = 0;
+#pragma unroll
+  for (int k = 0; k < K; k++) na[k] = nb[k] = 0;
+#pragma unroll
+  for (int j = 0; j < NV; j++) {
+    const int k = T.v[j].k;
+    const int c = box[e + QBox<TM>::voff(T.v[j].x, T.v[j].y, T.v[j].z)] & 7;
+    dE += SIGN * W[k * M + c];
+    na[k] += (c == sa);
+    nb[k] += (c == sb);
+  }
+  return dE;
+}
 }  // namespace qfn
 
 // Counts of every site of the tile (all tiles in one launch): species staged
@@ -643,91 +734,39 @@ __global__ void __launch_bounds__(128, TM == 20 ? 2 : 3)
             const uint32_t ru = (b & 1) ? rw.w : rw.y;
             const int s = cbase + BX::voff(bx_of(b), by_of(b), bz_of(b));
             const int dir = (int)__umulhi(rd, 12u);
-            const int po = s_qoff[dir];
-            const int sp = s + po;
+            const int sp = s + s_qoff[dir];
             const int sa = box[s] & 7, sb = box[sp] & 7;
             if (sa == sb) {
               same++;
             } else {
               const int32_t* W = s_w + (sa * M + sb) * KM;
-              int dE = s_w[MM * KM + sa * M + sb];
-              // pair part and the counts of s and s' after the swap: a and b
-              // around s and around s' (s' holds b and s holds a before the
-              // swap: each is taken out of the other's count afterwards)
-              int na_s[K], nb_s[K], na_p[K], nb_p[K];
-#pragma unroll
-              for (int k = 0; k < K; k++) na_s[k] = nb_s[k] = na_p[k] = nb_p[k] = 0;
-#pragma unroll
-              for (int j = 0; j < NV; j++) {
-                const int k = T.v[j].k, o = BX::voff(T.v[j].x, T.v[j].y, T.v[j].z);
-                const int c = box[s + o] & 7;
-                dE += W[k * M + c];
-                na_s[k] += (c == sa);
-                nb_s[k] += (c == sb);
-                const int cp = box[sp + o] & 7;
-                dE -= W[k * M + cp];
-                na_p[k] += (cp == sa);
-                nb_p[k] += (cp == sb);
-              }
-              nb_s[0]--;
-              na_p[0]--;
               int wqa[K], wqb[K];
 #pragma unroll
               for (int k = 0; k < K; k++) {
                 wqa[k] = s_wq[k * M + sa];
                 wqb[k] = s_wq[k * M + sb];
-                dE += wqb[k] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) + wqa[k] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
               }
-              // environment sites whose counts move, branch-free: d = +1
-              // (the site holds b), -1 (a) or 0 (another species); a count
-              // n moving by d changes the term by W (2 n d + d^2)
+              // pair part and the counts of s and s' after the swap: b
+              // around s without s' (which holds b before the swap), a around
+              // s' without s
+              int na_s[K], nb_s[K], na_p[K], nb_p[K];
+              int dE = s_w[MM * KM + sa * M + sb] + pair_side<K, TM, 1>(box, s, W, M, sa, sb, na_s, nb_s) +
+                       pair_side<K, TM, -1>(box, sp, W, M, sa, sb, na_p, nb_p);
+              nb_s[0]--;
+              na_p[0]--;
+#pragma unroll
+              for (int k = 0; k < K; k++)
+                dE += wqb[k] * (nb_s[k] * nb_s[k] - nb_p[k] * nb_p[k]) + wqa[k] * (na_p[k] * na_p[k] - na_s[k] * na_s[k]);
+              // environment sites whose counts move
               const short* es = s_es + dir * NS;
               const short* ep = s_ep + dir * NP;
-#pragma unroll
-              for (int i = 0; i < NS; i++) {
-                const uint32_t w = box[s + es[i]];
-                const int c = (int)(w & 7u);
-                const bool isb = c == sb, isa = c == sa;
-                const int d = (int)isb - (int)isa, ad = (int)(isb | isa);
-                const int k1 = QC.k1[i], k2 = QC.k2[i];
-                const int n1 = (int)((w >> fshift(k1)) & (uint32_t)fmask(k1));
-                dE += (isb ? wqb[k1] : wqa[k1]) * (2 * d * n1 + ad);
-                if (k2 >= 0) {
-                  const int n2 = (int)((w >> fshift(k2)) & (uint32_t)fmask(k2));
-                  dE += (isb ? wqb[k2] : wqa[k2]) * (ad - 2 * d * n2);
-                }
-              }
-#pragma unroll
-              for (int i = 0; i < NP; i++) {
-                const uint32_t w = box[sp + ep[i]];
-                const int c = (int)(w & 7u);
-                const bool isb = c == sb, isa = c == sa;
-                const int d = (int)isa - (int)isb, ad = (int)(isb | isa);
-                const int k = QC.kp[i];
-                const int n = (int)((w >> fshift(k)) & (uint32_t)fmask(k));
-                dE += (isb ? wqb[k] : wqa[k]) * (2 * d * n + ad);
-              }
+              dE += es_energy<K, TM, 0, NS>(box, es, s, sa, sb, wqa, wqb);
+              dE += ep_energy<K, TM>(box, ep, sp, sa, sb, wqa, wqb);
               if (metropolis_accept(dE, ru, P.thr, P.nA, P.thr + kNA)) {
                 box[s] = (uint16_t)(sb | (pack_counts<K>(nb_s) << 3));
                 box[sp] = (uint16_t)(sa | (pack_counts<K>(na_p) << 3));
-#pragma unroll
-                for (int i = 0; i < NS; i++) {
-                  const int t = s + es[i];
-                  const uint32_t w = box[t];
-                  const int c = (int)(w & 7u);
-                  const int d = (int)(c == sb) - (int)(c == sa);
-                  const int k1 = QC.k1[i], k2 = QC.k2[i];
-                  const int dw = d * ((1 << fshift(k1)) - (k2 >= 0 ? (1 << fshift(k2)) : 0));
-                  if (d != 0) box[t] = (uint16_t)((int)w + dw);
-                }
-#pragma unroll
-                for (int i = 0; i < NP; i++) {
-                  const int t = sp + ep[i];
-                  const uint32_t w = box[t];
-                  const int c = (int)(w & 7u);
-                  const int d = (int)(c == sa) - (int)(c == sb);
-                  if (d != 0) box[t] = (uint16_t)((int)w + d * (1 << fshift(QC.kp[i])));
-                }
+                es_update<K, TM, 0, NS>(box, es, s, sa, sb);
+                ep_update<K, TM>(box, ep, sp, sa, sb);
                 acc++;
                 dsum += dE;
               }
