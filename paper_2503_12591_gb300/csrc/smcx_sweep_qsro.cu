@@ -14,11 +14,18 @@
 //  * every other site i of the two environments whose species c is a or b
 //    and that sees s in shell k1 and s' in shell k2 with k1 != k2: n_k1(i)
 //    changes by d1 = +1 (c = b) or -1 (c = a) and n_k2(i) by -d1, so its term
-//    changes by W_k[c] (2 d n_k(i) + 1) for those shells; n_k(i) is counted
-//    from i's own shell-k neighbours in shared memory.  Sites of other
+//    changes by W_k[c] (2 d n_k(i) + 1) for those shells.  Sites of other
 //    species, or seeing both ends in the same shell, do not change.
+// Two kernels get n_k(i):
+//  * k_qsro_fcc_n (FCC, 2 or 3 shells, tiles of 3 to 20 cells) keeps every
+//    site's counts beside its species (a device array written once per sweep
+//    call, a 16-bit shared-memory box during a tile pass) and updates them
+//    on accepted swaps, so a count is one load;
+//  * k_tile_sweep_qsro (BCC, and FCC with larger tiles) counts i's own
+//    shell-k neighbours in shared memory.
 // k2 (the shell of s' - i for i = s + v) and whether s' + v lies in the
-// environment of s are per-direction tables built on the host.
+// environment of s are per-direction tables (built on the host for the
+// generic kernel, at compile time for the FCC one).
 //
 // The trial reads R1 + 2 R_K around its centre, so the schedule uses the
 // larger link cell and halo of this model (FCC with 3 shells: L >= 4, the
