@@ -223,9 +223,9 @@ int smcx_set_replica(smcx_lattice* h, int replica);
  * keyed by (seed, sweep, colour, block); the two tiles of a block share their
  * directions (each tile still runs in its own CTA).  The shared-direction
  * modes run on the BCC tile kernels (single-lattice and batched) when the
- * table has 4 shells, M <= 4 and |V| < 2^15, else on the generic tile
- * kernel; FCC lattices run them on the generic tile kernel; qSRO sweeps run
- * SMCX_PROPOSAL_SITE only. */
+ * table has 4 shells, M <= 4 and |V| < 2^15, on the FCC tile kernel when it
+ * has 3 shells and M = 5, or M <= 4 with |V| < 2^15, else on the generic
+ * tile kernel; qSRO sweeps run SMCX_PROPOSAL_SITE only. */
 #define SMCX_PROPOSAL_SITE 0
 #define SMCX_PROPOSAL_TILE 1
 #define SMCX_PROPOSAL_BLOCK 2

@@ -208,6 +208,111 @@ __device__ __forceinline__ void trial(uint8_t* box, int s, uint32_t rd, uint32_t
     finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
 }
 
+// ---- shared-direction proposals (SMCX_PROPOSAL_TILE / _BLOCK) ------------
+// One shell-1 direction p per (sweep, tile, intra colour): every lane of a
+// phase swaps along the same vector, so the warp reads the union of the two
+// environments at common offsets.  A site in shell k1 around s and k2 around
+// s' = s + p adds one to counter k1 and subtracts one from counter k2; sites
+// seeing both ends in the same shell cancel and are not read, nor are s and
+// s' themselves (their bond is not part of either environment after the
+// swap).  For 3 shells that leaves 50 of the 84 environment loads.  Entries
+// are ordered by class (k1, k2), the same sequence of classes for every
+// direction (the 12 directions are images of one another under the cubic
+// group), so the shells are compile-time constants and only the box offsets,
+// from a constant-memory row per direction, depend on p.
+__host__ __device__ constexpr int fshell(int x, int y, int z) {
+  const int r = x * x + y * y + z * z;
+  return r == 2 ? 0 : r == 4 ? 1 : r == 6 ? 2 : -1;
+}
+constexpr int kFUnionMax = 64;
+struct FUnion {
+  int off[12][kFUnionMax];
+  int k1[kFUnionMax], k2[kFUnionMax];
+  int n;
+  bool ok;
+};
+__host__ __device__ constexpr FUnion make_funion() {
+  constexpr FTable T = make_fvecs();
+  FUnion u{};
+  u.ok = true;
+  for (int d = 0; d < 12; d++) {
+    const int px = T.v[d].x, py = T.v[d].y, pz = T.v[d].z;
+    int n = 0;
+    for (int a = -1; a < 3; a++)
+      for (int b = -1; b < 3; b++) {
+        if ((a < 0 && b < 0) || a == b) continue;
+        // sites of shell a around s (a >= 0) seen in shell b around s'; or,
+        // for a = -1, sites of shell b around s' outside the shells of s
+        for (int j = 0; j < T.n; j++) {
+          int x = 0, y = 0, z = 0;
+          if (a >= 0) {
+            if (T.v[j].k != a) continue;
+            x = T.v[j].x;
+            y = T.v[j].y;
+            z = T.v[j].z;
+            if (x == px && y == py && z == pz) continue;  // s'
+            if (fshell(x - px, y - py, z - pz) != b) continue;
+          } else {
+            if (T.v[j].k != b) continue;
+            x = T.v[j].x + px;
+            y = T.v[j].y + py;
+            z = T.v[j].z + pz;
+            if ((x == 0 && y == 0 && z == 0) || fshell(x, y, z) >= 0) continue;  // s, or around s
+          }
+          if (n >= kFUnionMax) {
+            u.ok = false;
+            continue;
+          }
+          if (d == 0) {
+            u.k1[n] = a;
+            u.k2[n] = b;
+          } else if (u.k1[n] != a || u.k2[n] != b) {
+            u.ok = false;
+          }
+          u.off[d][n++] = hoff(x, y, z);
+        }
+      }
+    if (d == 0) u.n = n;
+    else if (n != u.n) u.ok = false;
+  }
+  return u;
+}
+static_assert(make_funion().ok, "FCC union classes differ between directions");
+__constant__ FUnion c_funion = make_funion();
+
+template <int K, int NW, int PL>
+__device__ __forceinline__ void trial_dir(uint8_t* box, int s, int dir, uint32_t ru, const int* s_poff,
+                                          const uint32_t* sP, const int32_t* sR, int nA, const uint32_t* sA,
+                                          const uint32_t* sB, unsigned& acc, unsigned& same, long long& dsum) {
+  static_assert(K == 3 && NW <= 1, "shared-direction FCC trials: 3 shells, one counter word");
+  constexpr FUnion U = make_funion();
+  const int sp = s + s_poff[dir];
+  const uint32_t a8 = ld_chk(box, s, BOX_BYTES, kDbgFccBox), b8 = ld_chk(box, sp, BOX_BYTES, kDbgFccBox);
+  if (a8 == b8) {
+    same++;
+    return;
+  }
+  uint32_t h[kMaxShells][2];
+#pragma unroll
+  for (int k = 0; k < kMaxShells; k++) {
+    h[k][0] = NW == 0 ? kBias6 : 0x80808080u;
+    h[k][1] = 0x80808080u;
+  }
+  const int* off = c_funion.off[dir];
+#pragma unroll
+  for (int i = 0; i < U.n; i++) {
+    const uint32_t v = ld_chk(box, s + off[i], BOX_BYTES, kDbgFccBox);
+    uint32_t one;
+    asm("shl.b32 %0, 1, %1;" : "=r"(one) : "r"(v));
+    if (U.k1[i] >= 0) h[U.k1[i]][0] += one;
+    if (U.k2[i] >= 0) h[U.k2[i]][0] -= one;
+  }
+  if constexpr (NW == 0)
+    finish_six<K>(box, s, sp, a8, b8, h, ru, sR, nA, sA, sB, acc, dsum);
+  else
+    finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
+}
+
 // box, partner offsets (16 ints), six-bit rows (25 x 17 words), plane rows
 // (3 x 3 x 8 x 2 words), sA, sB
 constexpr int kPlaneWords = 3 * 3 * 8 * 2;
@@ -216,10 +321,11 @@ __host__ __device__ constexpr size_t smem_bytes(int nA) {
   return BOX_BYTES + 16 * 4 + kRowWords * 4 + kPlaneWords * 4 + (size_t)(nA + kNB) * 4;
 }
 
-template <int K, int NW, int PL>
+template <int K, int NW, int PL, int PROP = 0>
 __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, const Rows6 R, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
+  __shared__ uint8_t s_dir[PROP ? 512 : 4];  // phase directions (shared-direction proposals)
   uint8_t* box = smem;
   int* s_poff = reinterpret_cast<int*>(smem + BOX_BYTES);
   int32_t* sR = s_poff + 16;
@@ -250,6 +356,19 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
   }
   for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
   for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+  if constexpr (PROP != 0) {
+    // per (sweep, tile, intra colour ic) (mode 1) or per (sweep, colour,
+    // block of two tiles, ic) (mode 2): one Philox block per ic pair pr =
+    // ic >> 1, word 0 for even ic, word 2 for odd ic
+    const unsigned tile = (unsigned)((ti[2] * D.nt[1] + ti[1]) * D.nt[0] + ti[0]);
+    for (int pr = tid; pr < 2 * D.L * D.L * D.L; pr += nth) {
+      const uint4 r = D.proposal == 2 ? block_direction_block(D.seed_lo, D.seed_hi, D.sweep, D.replica, tc,
+                                                              (unsigned)jt >> 1, pr)
+                                      : phase_direction_block(D.seed_lo, D.seed_hi, D.sweep, D.replica, tile, pr);
+      st_chk(s_dir, 2 * pr, 512, kDbgBccDir, (uint8_t)__umulhi(r.x, 12u));
+      st_chk(s_dir, 2 * pr + 1, 512, kDbgBccDir, (uint8_t)__umulhi(r.z, 12u));
+    }
+  }
   if (tid < 12) {
     constexpr FTable T = make_fvecs();
     int o = 0;
@@ -315,15 +434,25 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
         for (int pr = 0; pr < 2; pr++) {
           // sublattices 2 pr and 2 pr + 1 share the Philox block of pair cell*2 + pr
           uint4 rw = make_uint4(0, 0, 0, 0);
+          const int ic = (((cz * L + cy) * L + cx) * 4) + 2 * pr;
           if (here) {
             rw = attempt_block(cell * 4 + 2 * pr, D.sweep, D.replica, D.seed_lo, D.seed_hi);
-            trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, sP, sR, D.nA,
-                             sA, sB, acc, same, dsum);
+            if constexpr (PROP != 0)
+              trial_dir<K, NW, PL>(box, cbase + boff(2 * pr), ld_chk(s_dir, ic, 512, kDbgBccDir), rw.y, s_poff, sP,
+                                   sR, D.nA, sA, sB, acc, same, dsum);
+            else
+              trial<K, NW, PL>(box, cbase + boff(2 * pr), rw.x, rw.y, s_poff, sP, sR, D.nA,
+                               sA, sB, acc, same, dsum);
           }
           __syncthreads();
-          if (here)
-            trial<K, NW, PL>(box, cbase + boff(2 * pr + 1), rw.z, rw.w, s_poff,
-                             sP, sR, D.nA, sA, sB, acc, same, dsum);
+          if (here) {
+            if constexpr (PROP != 0)
+              trial_dir<K, NW, PL>(box, cbase + boff(2 * pr + 1), ld_chk(s_dir, ic + 1, 512, kDbgBccDir), rw.w,
+                                   s_poff, sP, sR, D.nA, sA, sB, acc, same, dsum);
+            else
+              trial<K, NW, PL>(box, cbase + boff(2 * pr + 1), rw.z, rw.w, s_poff,
+                               sP, sR, D.nA, sA, sB, acc, same, dsum);
+          }
           __syncthreads();
         }
       }
@@ -368,13 +497,23 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
 
 int build_planes(const smcx_lattice* hd, bccfast::Planes* Q, int min_planes);
 
-// FCC pair model, M <= 8, K <= 3, |V| < 2^23, per-trial directions, a tiled
-// schedule with tiles of at most 15 cells and link cells of at least 3 (one
-// slot of at most 5^3 per thread of a 128-thread CTA), 16-byte aligned store.
+// FCC pair model, M <= 8, K <= 3, |V| < 2^23, a tiled schedule with tiles of
+// at most 15 cells and link cells of at least 3 (one slot of at most 5^3 per
+// thread of a 128-thread CTA), 16-byte aligned store.  Shared-direction
+// proposals: 3 shells and one counter word (M <= 5; M <= 4 with |V| < 2^15).
 bool fcc_fast_usable(const smcx_lattice* hd) {
   const smcx_sched& sc = hd->sched;
   if (hd->kind != kFCC || hd->M > kMaxSweepM || !hd->have_epi || !hd->Wq.empty()) return false;
-  if (hd->proposal != SMCX_PROPOSAL_SITE || hd->shells.K > 3) return false;
+  if (hd->shells.K > 3) return false;
+  if (hd->proposal != SMCX_PROPOSAL_SITE) {
+    if (hd->shells.K != 3 || hd->M > 5) return false;
+    if (hd->M == 5) {
+      // six-bit counters: every field difference fits
+    } else {
+      for (int32_t v : hd->V)
+        if (v >= 32768 || v <= -32768) return false;  // one counter word, two byte planes
+    }
+  }
   if (sc.L < 3 || sc.nt[0] < 2 || sc.nt[1] < 2 || sc.nt[2] < 2) return false;
   if (halo_cells(hd->shells) != 2 || ring_cells(hd->shells) != 1) return false;
   if (reinterpret_cast<uintptr_t>(hd->d_sites) % 4 != 0) return false;
@@ -410,6 +549,7 @@ void sweep_fcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
   D.seed_lo = (uint32_t)seed;
   D.seed_hi = (uint32_t)(seed >> 32);
   D.M = hd->M;
+  D.proposal = hd->proposal;
   bccfast::Planes Q;
   const int K = hd->shells.K;
   const int PL = build_planes(hd, &Q, K == 3 ? 2 : 3);
@@ -442,7 +582,12 @@ void sweep_fcc_fast(smcx_lattice* hd, int nA, uint64_t seed, int64_t n_sweeps, i
       for (int tc = 0; tc < n_colours; tc++) kern<<<grid, 128, smem, hd->stream>>>(D, Q, R, tc);
     }
   };
-  if (NW == 0) {
+  if (D.proposal != 0) {
+    // shared-direction proposals (fcc_fast_usable: 3 shells, one counter word)
+    if (NW == 0) run(fccfast::k_fcc_tile_sweep<3, 0, 0, 1>);
+    else if (NW == 1 && PL == 2) run(fccfast::k_fcc_tile_sweep<3, 1, 2, 1>);
+    else fail(SMCX_E_UNSUPPORTED, "shared-direction FCC kernel: 3 shells, M <= 5");
+  } else if (NW == 0) {
     if (K == 3) run(fccfast::k_fcc_tile_sweep<3, 0, 0>);
     else if (K == 2) run(fccfast::k_fcc_tile_sweep<2, 0, 0>);
     else run(fccfast::k_fcc_tile_sweep<1, 0, 0>);
