@@ -381,7 +381,10 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
                                  int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
                                  long long& dsum);
 
-template <int K, int NW, int PL, int SLOTS, int PROP = 0>
+// TL1: the acceptance tables are read from global memory through L1 instead
+// of being copied into shared memory (sA, sB then point into D.thr), which
+// frees 5 KB of shared memory per CTA.
+template <int K, int NW, int PL, int SLOTS, int PROP = 0, bool TL1 = false>
 __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q, int tc, int jt,
                                               unsigned long long sweep, uint8_t* box, uint32_t* sA, uint32_t* sB,
                                               unsigned long long* s_stat) {
@@ -401,8 +404,13 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   }
   __syncthreads();  // the previous pass of this CTA is done with the tables
   if (tid < 3) s_stat[tid] = 0;
-  for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
-  for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+  if (TL1) {
+    sA = const_cast<uint32_t*>(D.thr);
+    sB = const_cast<uint32_t*>(D.thr) + kNA;
+  } else {
+    for (int i = tid; i < D.nA; i += nth) sA[i] = D.thr[i];
+    for (int i = tid; i < kNB; i += nth) sB[i] = D.thr[kNA + i];
+  }
   if (PROP == 1) {
     if (Q.rows)
       for (int i = tid; i < 128; i += nth) s_rows[i] = Q.R[i >> 3][i & 7];
@@ -556,13 +564,13 @@ __host__ __device__ constexpr size_t smem_bytes(int nA) { return 2 * SUB + (size
 
 // Single-lattice sweep kernel: one CTA per tile of colour `tc`.
 template <int K, int NW, int PL, int SLOTS, int PROP>
-__global__ void __launch_bounds__(128, 6) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
+__global__ void __launch_bounds__(128, PROP == 1 ? 7 : 6) k_bcc_tile_sweep(const LatDesc D, const Planes Q, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   uint8_t* box = smem;
   uint32_t* sA = reinterpret_cast<uint32_t*>(smem + 2 * SUB);
   uint32_t* sB = sA + D.nA;
-  bcc_tile_pass<K, NW, PL, SLOTS, PROP>(D, Q, tc, blockIdx.x, D.sweep, box, sA, sB, s_stat);
+  bcc_tile_pass<K, NW, PL, SLOTS, PROP, PROP == 1>(D, Q, tc, blockIdx.x, D.sweep, box, sA, sB, s_stat);
 }
 
 }  // namespace bccfast
@@ -570,10 +578,14 @@ __global__ void __launch_bounds__(128, 6) k_bcc_tile_sweep(const LatDesc D, cons
 template <int K, int NW, int PL, int SLOTS, int PROP = 0>
 inline void launch_bcc(smcx_lattice* hd, bccfast::LatDesc& D, const bccfast::Planes& Q, int threads,
                        int64_t n_sweeps, int n_colours) {
-  const size_t smem = bccfast::smem_bytes(D.nA);
+  const size_t smem = PROP == 1 ? (size_t)2 * bccfast::SUB : bccfast::smem_bytes(D.nA);
   check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS, PROP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
              "bcc sweep smem attribute");
+  if (PROP == 1)
+    check_cuda(cudaFuncSetAttribute(bccfast::k_bcc_tile_sweep<K, NW, PL, SLOTS, PROP>,
+                                    cudaFuncAttributePreferredSharedMemoryCarveout, 100),
+               "bcc sweep carveout");
   const int grid = (D.nt[0] / 2) * (D.nt[1] / 2) * (D.nt[2] / 2);
   const unsigned long long first = D.sweep;
   for (int64_t s = 0; s < n_sweeps; s++) {
