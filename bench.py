@@ -269,7 +269,7 @@ def run_batched(stream):
     def one_mode(mode, plain_sweeps):
         lats = [make(r, mode) for r in range(BATCH_R)]
         b = smcx.Batch(lats, stream)
-        threads = b.autotune(T, trial_sweeps=2)
+        threads = b.autotune(T, trial_sweeps=8)  # near-equal candidates: enough sweeps to rank them
         scheds = [l.schedule() for l in lats]
         plain = [make(r, mode) for r in range(BATCH_R)]
         for p, sc in zip(plain, scheds):
