@@ -381,6 +381,72 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
                                  int nA, const uint32_t* sA, const uint32_t* sB, unsigned& acc, unsigned& same,
                                  long long& dsum);
 
+// Stage the tile and its 2-cell halo from 32-bit words of the site store, CW
+// cells per word (4: one byte per cell, two 4-bit ids; 2: two int8 ids per
+// cell).  Box column c of a row holds the cell at global x = t0x - 2 + c
+// (periodic); the NWR words of a box row start at the multiple of CW at or
+// below t0x - 2, and with nx a multiple of CW no word straddles the wrap.
+// Lane l of a warp takes word l % NWR of row l / NWR of each group of RPS
+// rows; warp w stages the planes w, w + nwarp, ..., and issues the loads of
+// PLB planes (PLB * RS words per lane) before it unpacks them.
+template <int CW>
+__device__ __forceinline__ void stage_words(const LatDesc& D, uint8_t* box, const int (&t0)[3], int ex, int ey,
+                                            int ez, int lane, int warp, int nwarp) {
+  constexpr int h = 2;
+  constexpr int NWR = (BOX + CW - 1) / CW + 1;  // words per box row (7 or 13)
+  constexpr int RPS = 32 / NWR;                 // rows per warp step (4 or 2)
+  constexpr int RS = BOX / RPS;                 // steps per plane (6 or 12)
+  constexpr int PLB = 2;                        // planes per batch of loads
+  constexpr int WPC = CW == 4 ? 1 : 2;          // bytes per cell
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  const int xs = t0[0] - h;
+  const int r = xs & (CW - 1);  // xs - r is a multiple of CW (also for xs < 0)
+  const int m = lane % NWR, ry = lane / NWR;
+  const bool lane_ok = ry < RPS && CW * m - r < ex;
+  int gw = (xs - r + CW * m) % nx;  // first cell of this lane's word
+  gw += gw < 0 ? nx : 0;
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(D.sites);
+  const long long nword = (long long)nx * ny * nz * WPC / 4;
+  for (int zb = warp; zb < ez; zb += nwarp * PLB) {
+    uint32_t v[PLB][RS];
+#pragma unroll
+    for (int p = 0; p < PLB; p++) {
+      const int zs = zb + p * nwarp;
+      const long long zrow = zs < ez ? (long long)wrap_add(t0[2] - h, zs, nz) * ny : 0;
+#pragma unroll
+      for (int q = 0; q < RS; q++) {
+        const int ys = RPS * q + ry;
+        v[p][q] = 0;
+        if (zs < ez && ys < ey && lane_ok) {
+          const long long cell = (zrow + wrap_add(t0[1] - h, ys, ny)) * nx + gw;
+          v[p][q] = ld_chk(words, cell * WPC / 4, nword, kDbgSite);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < PLB; p++) {
+      const int zs = zb + p * nwarp;
+#pragma unroll
+      for (int q = 0; q < RS; q++) {
+        const int ys = RPS * q + ry;
+        if (zs < ez && ys < ey && lane_ok) {
+          const int bi = zs * PP + ys * PX + CW * m - r;
+#pragma unroll
+          for (int j = 0; j < CW; j++) {
+            const int c = CW * m + j - r;
+            if (c >= 0 && c < ex) {
+              const uint32_t s0 = CW == 4 ? (v[p][q] >> (8 * j)) & 15u : (v[p][q] >> (16 * j)) & 0xFFu;
+              const uint32_t s1 = CW == 4 ? (v[p][q] >> (8 * j + 4)) & 15u : (v[p][q] >> (16 * j + 8)) & 0xFFu;
+              st_chk(box, bi + j, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
+              st_chk(box, SUB + bi + j, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // TL1: the acceptance tables are read from global memory through L1 instead
 // of being copied into shared memory (sA, sB then point into D.thr), which
 // frees 5 KB of shared memory per CTA.
@@ -430,38 +496,44 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
   constexpr int h = 2;
   const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
   const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
-  // ex <= BOX = 24 < 32: one lane per box column.  Each warp first issues the
-  // loads of U rows, then unpacks and stores them, so U global loads per lane
-  // are in flight instead of one.
-  constexpr int U = 8;
-  const int rows = ey * ez;
-  const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
   const long long ncell = (long long)nx * ny * nz;
-  for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
-    uint32_t v[U];
+  if (D.storage == SMCX_INT8 ? (nx & 1) == 0 : (nx & 3) == 0) {
+    if (D.storage == SMCX_INT8)
+      stage_words<2>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+    else
+      stage_words<4>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+  } else {
+    // one lane per box column (ex <= BOX = 24 < 32); warp w stages the
+    // planes w, w + nwarp, ...; each warp issues the loads of U rows of a
+    // plane before it unpacks them
+    constexpr int U = 8;
+    const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
+    for (int zs = warp; zs < ez; zs += nwarp) {
+      const long long zrow = (long long)wrap_add(t0[2] - h, zs, nz) * ny;
+      for (int ys0 = 0; ys0 < ey; ys0 += U) {
+        uint32_t v[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      v[u] = 0;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const long long cell =
-            ((long long)wrap_add(t0[2] - h, zs, nz) * ny + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
-        v[u] = D.storage == SMCX_INT8
-                   ? (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(D.sites), cell, ncell, kDbgSite)
-                   : (uint32_t)ld_chk(D.sites, cell, ncell, kDbgSite);
-      }
-    }
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          v[u] = 0;
+          if (ys < ey && lane < ex) {
+            const long long cell = (zrow + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
+            v[u] = D.storage == SMCX_INT8
+                       ? (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(D.sites), cell, ncell, kDbgSite)
+                       : (uint32_t)ld_chk(D.sites, cell, ncell, kDbgSite);
+          }
+        }
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
-        const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
-        const int bi = zs * PP + ys * PX + lane;
-        st_chk(box, bi, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
-        st_chk(box, SUB + bi, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          if (ys < ey && lane < ex) {
+            const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
+            const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
+            const int bi = zs * PP + ys * PX + lane;
+            st_chk(box, bi, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
+            st_chk(box, SUB + bi, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
+          }
+        }
       }
     }
   }
@@ -524,23 +596,25 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
         __syncthreads();
       }
 
-  // write back tile + 1-cell partner ring
+  // write back tile + 1-cell partner ring: one lane per column (wx <= 22 <
+  // 32), warp w the planes w, w + nwarp, ...
   const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
-  for (int row = warp; row < wy * wz; row += nwarp) {
-    const int yw = row % wy, zw = row / wy;
-    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xw = lane; xw < wx; xw += 32) {
-      const int gx = wrap_add(t0[0] - 1, xw, nx);
-      const long long cell = rbase + gx;
-      const int bi = (zw + h - 1) * PP + (yw + h - 1) * PX + (xw + h - 1);
-      const uint32_t s0 = ld_chk(box, bi, 2 * SUB, kDbgBccWrite) >> 3;
-      const uint32_t s1 = ld_chk(box, SUB + bi, 2 * SUB, kDbgBccWrite) >> 3;
-      if (D.storage == SMCX_INT8) {
-        st_chk(D.sites, 2 * cell, 2 * ncell, kDbgSite, (uint8_t)s0);
-        st_chk(D.sites, 2 * cell + 1, 2 * ncell, kDbgSite, (uint8_t)s1);
-      } else {
-        st_chk(D.sites, cell, ncell, kDbgSite, (uint8_t)(s0 | (s1 << 4)));
+  const int gxw = lane < wx ? wrap_add(t0[0] - 1, lane, nx) : 0;
+  for (int zw = warp; zw < wz; zw += nwarp) {
+    const long long zrow = (long long)wrap_add(t0[2] - 1, zw, nz) * ny;
+#pragma unroll 4
+    for (int yw = 0; yw < wy; yw++) {
+      if (lane < wx) {
+        const long long cell = (zrow + wrap_add(t0[1] - 1, yw, ny)) * nx + gxw;
+        const int bi = (zw + h - 1) * PP + (yw + h - 1) * PX + (lane + h - 1);
+        const uint32_t s0 = ld_chk(box, bi, 2 * SUB, kDbgBccWrite) >> 3;
+        const uint32_t s1 = ld_chk(box, SUB + bi, 2 * SUB, kDbgBccWrite) >> 3;
+        if (D.storage == SMCX_INT8) {
+          st_chk(D.sites, 2 * cell, 2 * ncell, kDbgSite, (uint8_t)s0);
+          st_chk(D.sites, 2 * cell + 1, 2 * ncell, kDbgSite, (uint8_t)s1);
+        } else {
+          st_chk(D.sites, cell, ncell, kDbgSite, (uint8_t)(s0 | (s1 << 4)));
+        }
       }
     }
   }

@@ -80,6 +80,11 @@ SWEEP_CASES = [
     (smcx.BCC, 3, (24, 20, 22), 6, [1 / 6] * 6, smcx.PACKED4, (4, (2, 2, 2)), 1500.0, 3),
     (smcx.BCC, 4, (40, 24, 26), 8, [0.125] * 8, smcx.INT8, (3, (2, 2, 2)), 2000.0, 2),
     (smcx.BCC, 4, (42, 40, 38), 4, [0.25] * 4, smcx.PACKED4, (4, (4, 2, 2)), 1000.0, 2),
+    # staging from 32-bit words: tile origins at every x offset mod 4 (packed) and mod 2 (int8),
+    # and an odd x extent that takes the per-column path
+    (smcx.BCC, 4, (44, 20, 18), 4, [0.25] * 4, smcx.PACKED4, (3, (4, 2, 2)), 1000.0, 2),
+    (smcx.BCC, 4, (22, 15, 14), 4, [0.25] * 4, smcx.INT8, (3, (2, 2, 2)), 1000.0, 3),
+    (smcx.BCC, 4, (15, 12, 14), 4, [0.25] * 4, smcx.INT8, (3, (2, 2, 2)), 1000.0, 3),
     (smcx.FCC, 3, (12, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (4, 4, 4)), 1200.0, 5),
     (smcx.FCC, 3, (9, 10, 11), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.INT8, (3, (2, 4, 2)), 1200.0, 4),
     (smcx.FCC, 3, (9, 9, 9), 4, [0.25] * 4, smcx.PACKED4, (3, (1, 1, 1)), 1000.0, 4),      # link-cell
@@ -252,6 +257,7 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     (smcx.BCC, 4, (72, 36, 36), 4, [0.25] * 4, smcx.PACKED4, (3, (4, 2, 2)), 1200.0, 3),  # 18-cell tiles, 6^3 slots
     (smcx.BCC, 4, (70, 70, 34), 4, [0.25] * 4, smcx.INT8, (3, (4, 4, 2)), 900.0, 2),      # 17-18 cells, 2 blocks
     (smcx.BCC, 4, (54, 36, 36), 3, [0.5, 0.3, 0.2], smcx.PACKED4, (3, (6, 2, 2)), 1500.0, 2),  # M = 3, odd
+    (smcx.BCC, 4, (52, 20, 20), 4, [0.25] * 4, smcx.PACKED4, (4, (4, 2, 2)), 1200.0, 2),  # x origins mod 4: 2, 3, 0, 1
     # FCC shared-direction kernel: byte counters (M = 4), 15/14/13-cell tiles
     (smcx.FCC, 3, (30, 28, 26), 4, [0.25] * 4, smcx.INT8, (3, (2, 2, 2)), 1000.0, 2),
     # six-bit counters (M = 5), ragged tiles, link cells of 4
@@ -259,7 +265,7 @@ def test_epi_scale_byte_planes(stream, sigma_mev):
     # M = 2 (one counter word), 3 blocks per colour on x
     (smcx.FCC, 3, (36, 12, 12), 2, [0.6, 0.4], smcx.PACKED4, (3, (6, 2, 2)), 800.0, 2),
 ], ids=["bcc20", "bcc_ragged", "bcc_L3", "bcc_linkcell", "fcc", "bcc_blocks", "bcc_odd_blocks", "bcc_pair18",
-        "bcc_pair_ragged", "bcc_pair_m3", "fcc_m4", "fcc_ragged_L4", "fcc_m2_blocks"])
+        "bcc_pair_ragged", "bcc_pair_m3", "bcc_word_offsets", "fcc_m4", "fcc_ragged_L4", "fcc_m2_blocks"])
 def test_shared_direction_proposals(stream, case, kernel, mode):
     """SMCX_PROPOSAL_TILE: one direction per (sweep, tile, intra colour);
     SMCX_PROPOSAL_BLOCK: one per (sweep, tile colour, block of two tiles,
