@@ -619,9 +619,7 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
     }
   }
 
-  atomicAdd(&s_stat[0], (unsigned long long)acc);
-  atomicAdd(&s_stat[1], (unsigned long long)same);
-  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  add_stats_warp(s_stat, acc, same, dsum);
   __syncthreads();
   if (tid == 0) {
     atomicAdd(&D.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 2);

@@ -148,6 +148,23 @@ __device__ __forceinline__ bool metropolis_accept(int dE, uint32_t u, const uint
   return u < thr;
 }
 
+// Add a thread's trial counts to the CTA's shared counters (accepted,
+// same-species, sum of accepted dE): summed across the warp first, so that
+// each warp makes one shared atomic per counter.  Every lane of the warp
+// must call it.
+__device__ __forceinline__ void add_stats_warp(unsigned long long* s_stat, unsigned acc, unsigned same,
+                                               long long dsum) {
+  acc = __reduce_add_sync(0xffffffffu, acc);
+  same = __reduce_add_sync(0xffffffffu, same);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_stat[0], (unsigned long long)acc);
+    atomicAdd(&s_stat[1], (unsigned long long)same);
+    atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  }
+}
+
 __device__ __forceinline__ int wrap_add(int x, int d, int n) {
   int t = x + d;
   t += (t < 0) ? n : 0;

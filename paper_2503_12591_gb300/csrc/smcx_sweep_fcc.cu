@@ -313,6 +313,73 @@ __device__ __forceinline__ void trial_dir(uint8_t* box, int s, int dir, uint32_t
     finish_rows<K, NW, PL>(box, s, sp, a8, b8, h, ru, sP, nA, sA, sB, acc, dsum);
 }
 
+// Stage the tile and its 2-cell halo from 32-bit words of the site store,
+// CPW cells per word (2: 16-bit cells of four 4-bit ids; 1: four int8 ids).
+// Box column c of a row holds the cell at global x = t0x - 2 + c (periodic);
+// the NWR words of a box row start at the multiple of CPW at or below
+// t0x - 2, and with nx a multiple of CPW no word straddles the wrap.  Lane l
+// of a warp takes word l % NWR of row l / NWR of each group of RPS rows; warp
+// w stages the planes w, w + nwarp, ..., and issues the loads of PLB planes
+// (PLB * RS words per lane) before it unpacks them.
+template <int NW, int CPW>
+__device__ __forceinline__ void stage_words(const LatDesc& D, uint8_t* box, const int (&t0)[3], int ex, int ey,
+                                            int ez, int lane, int warp, int nwarp) {
+  constexpr int BE = TMAX + 2 * H;               // box edge (cells)
+  constexpr int NWR = CPW == 2 ? BE / 2 + 1 : BE;  // words per box row (10 or 19)
+  constexpr int RPS = 32 / NWR;                  // rows per warp step (3 or 1)
+  constexpr int RS = (BE + RPS - 1) / RPS;       // steps per plane (7 or 19)
+  constexpr int PLB = CPW == 2 ? 2 : 1;          // planes per batch of loads
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  const int xs = t0[0] - H;
+  const int r = xs & (CPW - 1);
+  const int m = lane % NWR, ry = lane / NWR;
+  const bool lane_ok = ry < RPS && CPW * m - r < ex;
+  int gw = (xs - r + CPW * m) % nx;  // first cell of this lane's word
+  gw += gw < 0 ? nx : 0;
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(D.sites);
+  const long long nword = (long long)nx * ny * nz / CPW;
+  for (int zb = warp; zb < ez; zb += nwarp * PLB) {
+    uint32_t v[PLB][RS];
+#pragma unroll
+    for (int p = 0; p < PLB; p++) {
+      const int zs = zb + p * nwarp;
+      const long long zrow = zs < ez ? (long long)wrap_add(t0[2] - H, zs, nz) * ny : 0;
+#pragma unroll
+      for (int q = 0; q < RS; q++) {
+        const int ys = RPS * q + ry;
+        v[p][q] = 0;
+        if (zs < ez && ys < ey && lane_ok) {
+          const long long cell = (zrow + wrap_add(t0[1] - H, ys, ny)) * nx + gw;
+          v[p][q] = ld_chk(words, cell / CPW, nword, kDbgSite);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < PLB; p++) {
+      const int zs = zb + p * nwarp;
+#pragma unroll
+      for (int q = 0; q < RS; q++) {
+        const int ys = RPS * q + ry;
+        if (zs < ez && ys < ey && lane_ok) {
+#pragma unroll
+          for (int j = 0; j < CPW; j++) {
+            const int c = CPW * m + j - r;
+            if (c >= 0 && c < ex) {
+              const uint32_t cv = CPW == 2 ? (v[p][q] >> (16 * j)) & 0xFFFFu : v[p][q];
+              const int base = hoff(2 * c, 2 * ys, 2 * zs);
+#pragma unroll
+              for (int b = 0; b < 4; b++) {
+                const uint32_t sp = CPW == 2 ? (cv >> (4 * b)) & 15u : (cv >> (8 * b)) & 0xFFu;
+                st_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox, (uint8_t)(NW == 0 ? sp * 6 : sp << 3));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // box, partner offsets (16 ints), six-bit rows (25 x 17 words), plane rows
 // (3 x 3 x 8 x 2 words), sA, sB
 constexpr int kPlaneWords = 3 * 3 * 8 * 2;
@@ -378,38 +445,41 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
     s_poff[tid] = o;
   }
 
-  // stage tile + 2-cell halo: one box column (cell x) per lane, rows (y, z)
-  // per warp, 8 rows of global loads in flight per lane
+  // stage tile + 2-cell halo
   const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
   const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
-  {
+  if (D.storage == SMCX_INT8)
+    stage_words<NW, 1>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+  else if ((nx & 1) == 0)
+    stage_words<NW, 2>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+  else {
+    // odd x extent, 16-bit cells: one box column (cell x) per lane, warp w
+    // the planes w, w + nwarp, ..., 8 rows of global loads in flight per lane
     constexpr int U = 8;
-    const int rows = ey * ez;
     const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
-    for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
-      uint32_t v[U];
+    for (int zs = warp; zs < ez; zs += nwarp) {
+      const long long zrow = (long long)wrap_add(t0[2] - H, zs, nz) * ny;
+      for (int ys0 = 0; ys0 < ey; ys0 += U) {
+        uint32_t v[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int row = row0 + u;
-        v[u] = 0;
-        if (row < rows && lane < ex) {
-          const int ys = row % ey, zs = row / ey;
-          const long long cell =
-              ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
-          v[u] = D.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(D.sites + 4 * cell)
-                                        : (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell));
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          v[u] = 0;
+          if (ys < ey && lane < ex) {
+            const long long cell = (zrow + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+            v[u] = (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell));
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int row = row0 + u;
-        if (row < rows && lane < ex) {
-          const int ys = row % ey, zs = row / ey;
-          const int base = hoff(2 * lane, 2 * ys, 2 * zs);
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          if (ys < ey && lane < ex) {
+            const int base = hoff(2 * lane, 2 * ys, 2 * zs);
 #pragma unroll
-          for (int b = 0; b < 4; b++) {
-            const uint32_t sp = D.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
-            st_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox, (uint8_t)(NW == 0 ? sp * 6 : sp << 3));
+            for (int b = 0; b < 4; b++) {
+              const uint32_t sp = (v[u] >> (4 * b)) & 15u;
+              st_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox, (uint8_t)(NW == 0 ? sp * 6 : sp << 3));
+            }
           }
         }
       }
@@ -457,33 +527,34 @@ __global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, cons
         }
       }
 
-  // write back tile + 1-cell partner ring
+  // write back tile + 1-cell partner ring: one lane per column (wx <= 17 <
+  // 32), warp w the planes w, w + nwarp, ...
   const int wx = ts[0] + 2, wy = ts[1] + 2, wz = ts[2] + 2;
-  for (int row = warp; row < wy * wz; row += nwarp) {
-    const int yw = row % wy, zw = row / wy;
-    const int gy = wrap_add(t0[1] - 1, yw, ny), gz = wrap_add(t0[2] - 1, zw, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xw = lane; xw < wx; xw += 32) {
-      const long long cell = rbase + wrap_add(t0[0] - 1, xw, nx);
-      const int base = hoff(2 * (xw + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
-      uint32_t s4[4];
+  const int gxw = lane < wx ? wrap_add(t0[0] - 1, lane, nx) : 0;
+  for (int zw = warp; zw < wz; zw += nwarp) {
+    const long long zrow = (long long)wrap_add(t0[2] - 1, zw, nz) * ny;
+#pragma unroll 4
+    for (int yw = 0; yw < wy; yw++) {
+      if (lane < wx) {
+        const long long cell = (zrow + wrap_add(t0[1] - 1, yw, ny)) * nx + gxw;
+        const int base = hoff(2 * (lane + H - 1), 2 * (yw + H - 1), 2 * (zw + H - 1));
+        uint32_t s4[4];
 #pragma unroll
-      for (int b = 0; b < 4; b++) {
-        const uint32_t v = ld_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox);
-        s4[b] = NW == 0 ? (uint32_t)species6(v) : v >> 3;
-      }
-      if (D.storage == SMCX_INT8) {
-        *reinterpret_cast<uint32_t*>(D.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
-      } else {
-        *reinterpret_cast<uint16_t*>(D.sites + 2 * cell) =
-            (uint16_t)(s4[0] | (s4[1] << 4) | (s4[2] << 8) | (s4[3] << 12));
+        for (int b = 0; b < 4; b++) {
+          const uint32_t v = ld_chk(box, base + boff(b), BOX_BYTES, kDbgFccBox);
+          s4[b] = NW == 0 ? (uint32_t)species6(v) : v >> 3;
+        }
+        if (D.storage == SMCX_INT8) {
+          *reinterpret_cast<uint32_t*>(D.sites + 4 * cell) = s4[0] | (s4[1] << 8) | (s4[2] << 16) | (s4[3] << 24);
+        } else {
+          *reinterpret_cast<uint16_t*>(D.sites + 2 * cell) =
+              (uint16_t)(s4[0] | (s4[1] << 4) | (s4[2] << 8) | (s4[3] << 12));
+        }
       }
     }
   }
 
-  atomicAdd(&s_stat[0], (unsigned long long)acc);
-  atomicAdd(&s_stat[1], (unsigned long long)same);
-  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  add_stats_warp(s_stat, acc, same, dsum);
   __syncthreads();
   if (tid == 0) {
     atomicAdd(&D.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 4);

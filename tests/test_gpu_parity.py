@@ -95,6 +95,9 @@ SWEEP_CASES = [
     (smcx.FCC, 1, (12, 12, 10), 2, [0.5, 0.5], smcx.PACKED4, (3, (2, 2, 2)), 700.0, 4),
     (smcx.FCC, 3, (18, 12, 12), 4, [0.25] * 4, smcx.PACKED4, (3, (2, 2, 2)), 1100.0, 3),
     (smcx.FCC, 3, (12, 12, 12), 6, [1 / 6] * 6, smcx.INT8, (3, (2, 2, 2)), 1300.0, 3),
+    # FCC staging: 16-bit cells from words with an odd tile origin, and an odd x extent (per-column path)
+    (smcx.FCC, 3, (22, 12, 12), 5, [0.3, 0.25, 0.2, 0.15, 0.1], smcx.PACKED4, (3, (2, 2, 2)), 1200.0, 3),
+    (smcx.FCC, 3, (21, 12, 12), 4, [0.25] * 4, smcx.PACKED4, (3, (2, 2, 2)), 1200.0, 3),
 ]
 
 
