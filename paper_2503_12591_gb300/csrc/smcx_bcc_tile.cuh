@@ -390,8 +390,8 @@ __device__ void trial_shared_dir(uint8_t* box, int s, int dir, uint32_t ru, cons
 // rows; warp w stages the planes w, w + nwarp, ..., and issues the loads of
 // PLB planes (PLB * RS words per lane) before it unpacks them.
 template <int CW>
-__device__ __forceinline__ void stage_words(const LatDesc& D, uint8_t* box, const int (&t0)[3], int ex, int ey,
-                                            int ez, int lane, int warp, int nwarp) {
+__device__ __forceinline__ void stage_words(const LatDesc& D, uint8_t* box, const int* t0, int ex, int ey, int ez,
+                                            int lane, int warp, int nwarp) {
   constexpr int h = 2;
   constexpr int NWR = (BOX + CW - 1) / CW + 1;  // words per box row (7 or 13)
   constexpr int RPS = 32 / NWR;                 // rows per warp step (4 or 2)
@@ -447,6 +447,56 @@ __device__ __forceinline__ void stage_words(const LatDesc& D, uint8_t* box, cons
   }
 }
 
+// Stage a tile (origin t0, extent ts) and its 2-cell halo into the box: from
+// 32-bit words when nx is a multiple of the cells per word, else one lane per
+// box column (ex <= BOX = 24 < 32), warp w the planes w, w + nwarp, ..., the
+// loads of U rows of a plane issued before any is unpacked.  Every thread of
+// the CTA takes part.
+__device__ __forceinline__ void stage_box(const LatDesc& D, uint8_t* box, const int* t0, const int* ts, int lane,
+                                          int warp, int nwarp) {
+  constexpr int h = 2;
+  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
+  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
+  const long long ncell = (long long)nx * ny * nz;
+  if (D.storage == SMCX_INT8 ? (nx & 1) == 0 : (nx & 3) == 0) {
+    if (D.storage == SMCX_INT8)
+      stage_words<2>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+    else
+      stage_words<4>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
+  } else {
+    constexpr int U = 8;
+    const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
+    for (int zs = warp; zs < ez; zs += nwarp) {
+      const long long zrow = (long long)wrap_add(t0[2] - h, zs, nz) * ny;
+      for (int ys0 = 0; ys0 < ey; ys0 += U) {
+        uint32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          v[u] = 0;
+          if (ys < ey && lane < ex) {
+            const long long cell = (zrow + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
+            v[u] = D.storage == SMCX_INT8
+                       ? (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(D.sites), cell, ncell, kDbgSite)
+                       : (uint32_t)ld_chk(D.sites, cell, ncell, kDbgSite);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          if (ys < ey && lane < ex) {
+            const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
+            const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
+            const int bi = zs * PP + ys * PX + lane;
+            st_chk(box, bi, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
+            st_chk(box, SUB + bi, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
+          }
+        }
+      }
+    }
+  }
+}
+
 // TL1: the acceptance tables are read from global memory through L1 instead
 // of being copied into shared memory (sA, sB then point into D.thr), which
 // frees 5 KB of shared memory per CTA.
@@ -494,49 +544,9 @@ __device__ __forceinline__ void bcc_tile_pass(const LatDesc& D, const Planes& Q,
 
   // stage tile + 2-cell halo
   constexpr int h = 2;
-  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
   const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
   const long long ncell = (long long)nx * ny * nz;
-  if (D.storage == SMCX_INT8 ? (nx & 1) == 0 : (nx & 3) == 0) {
-    if (D.storage == SMCX_INT8)
-      stage_words<2>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
-    else
-      stage_words<4>(D, box, t0, ex, ey, ez, lane, warp, nwarp);
-  } else {
-    // one lane per box column (ex <= BOX = 24 < 32); warp w stages the
-    // planes w, w + nwarp, ...; each warp issues the loads of U rows of a
-    // plane before it unpacks them
-    constexpr int U = 8;
-    const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
-    for (int zs = warp; zs < ez; zs += nwarp) {
-      const long long zrow = (long long)wrap_add(t0[2] - h, zs, nz) * ny;
-      for (int ys0 = 0; ys0 < ey; ys0 += U) {
-        uint32_t v[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int ys = ys0 + u;
-          v[u] = 0;
-          if (ys < ey && lane < ex) {
-            const long long cell = (zrow + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
-            v[u] = D.storage == SMCX_INT8
-                       ? (uint32_t)ld_chk(reinterpret_cast<const uint16_t*>(D.sites), cell, ncell, kDbgSite)
-                       : (uint32_t)ld_chk(D.sites, cell, ncell, kDbgSite);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-          const int ys = ys0 + u;
-          if (ys < ey && lane < ex) {
-            const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
-            const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
-            const int bi = zs * PP + ys * PX + lane;
-            st_chk(box, bi, 2 * SUB, kDbgBccStage, (uint8_t)(s0 << 3));
-            st_chk(box, SUB + bi, 2 * SUB, kDbgBccStage, (uint8_t)(s1 << 3));
-          }
-        }
-      }
-    }
-  }
+  stage_box(D, box, t0, ts, lane, warp, nwarp);
   __syncthreads();
 
   // link-cell slots of this thread: q = tid + j * nth

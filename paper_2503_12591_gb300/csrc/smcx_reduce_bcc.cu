@@ -34,43 +34,7 @@ __device__ __forceinline__ void tile_of_index(const LatDesc& D, int t, int t0[3]
 }
 
 __device__ __forceinline__ void stage_tile(const LatDesc& D, uint8_t* box, const int t0[3], const int ts[3]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  constexpr int h = 2;
-  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
-  const int nx = D.n[0], ny = D.n[1], nz = D.n[2];
-  // ex <= BOX = 24 < 32: one lane per box column.  Each warp first issues the
-  // loads of U rows, then unpacks and stores them, so U global loads per lane
-  // are in flight instead of one.
-  constexpr int U = 8;
-  const int rows = ey * ez;
-  const int gx = lane < ex ? wrap_add(t0[0] - h, lane, nx) : 0;
-  for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
-    uint32_t v[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      v[u] = 0;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const long long cell =
-            ((long long)wrap_add(t0[2] - h, zs, nz) * ny + wrap_add(t0[1] - h, ys, ny)) * nx + gx;
-        v[u] = D.storage == SMCX_INT8 ? (uint32_t)(*reinterpret_cast<const uint16_t*>(D.sites + 2 * cell))
-                                      : (uint32_t)D.sites[cell];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const uint32_t s0 = D.storage == SMCX_INT8 ? (v[u] & 0xFFu) : (v[u] & 15u);
-        const uint32_t s1 = D.storage == SMCX_INT8 ? (v[u] >> 8) : (v[u] >> 4);
-        const int bi = zs * PP + ys * PX + lane;
-        box[bi] = (uint8_t)(s0 << 3);
-        box[SUB + bi] = (uint8_t)(s1 << 3);
-      }
-    }
-  }
+  stage_box(D, box, t0, ts, threadIdx.x & 31, threadIdx.x >> 5, blockDim.x >> 5);
 }
 
 // Exact division of 0 <= c < 2^16 by 2 <= d < 2^10 with a 32-bit multiply-high

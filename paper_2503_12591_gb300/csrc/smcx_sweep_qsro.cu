@@ -331,39 +331,40 @@ __device__ __forceinline__ int count_shell(const uint8_t* box, int t, int c) {
   for (int j = T.start[KS]; j < T.start[KS + 1]; j++) n += (box[t + hoff(T.v[j].x, T.v[j].y, T.v[j].z)] == c);
   return n;
 }
-// Stage tile + 3-cell halo (species bytes at the even points), 8 rows of
-// loads in flight per lane; every thread of the CTA takes part.
+// Stage tile + 3-cell halo (species bytes at the even points): one box
+// column per lane, warp w the planes w, w + nwarp, ..., the loads of 8 rows
+// of a plane issued before any is unpacked; every thread of the CTA takes
+// part.
 __device__ __forceinline__ void stage_box(const SweepParams& P, uint8_t* box, const int (&t0)[3], const int (&ts)[3]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int ex = ts[0] + 2 * H, ey = ts[1] + 2 * H, ez = ts[2] + 2 * H;
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
   constexpr int U = 8;
-  const int rows = ey * ez;
   const int gx = lane < ex ? wrap_add(t0[0] - H, lane, nx) : 0;
-  for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
-    uint32_t v[U];
+  for (int zs = warp; zs < ez; zs += nwarp) {
+    const long long zrow = (long long)wrap_add(t0[2] - H, zs, nz) * ny;
+    for (int ys0 = 0; ys0 < ey; ys0 += U) {
+      uint32_t v[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      v[u] = 0;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const long long cell =
-            ((long long)wrap_add(t0[2] - H, zs, nz) * ny + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
-        v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
-                                      : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+      for (int u = 0; u < U; u++) {
+        const int ys = ys0 + u;
+        v[u] = 0;
+        if (ys < ey && lane < ex) {
+          const long long cell = (zrow + wrap_add(t0[1] - H, ys, ny)) * nx + gx;
+          v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
+                                        : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int row = row0 + u;
-      if (row < rows && lane < ex) {
-        const int ys = row % ey, zs = row / ey;
-        const int base = hoff(2 * lane, 2 * ys, 2 * zs);
+      for (int u = 0; u < U; u++) {
+        const int ys = ys0 + u;
+        if (ys < ey && lane < ex) {
+          const int base = hoff(2 * lane, 2 * ys, 2 * zs);
 #pragma unroll
-        for (int b = 0; b < 4; b++)
-          box[base + boff(b)] =
-              (uint8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+          for (int b = 0; b < 4; b++)
+            box[base + boff(b)] =
+                (uint8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+        }
       }
     }
   }
@@ -681,38 +682,40 @@ __global__ void __launch_bounds__(128, TM == 20 ? 2 : 3)
   const int ex = ts[0] + 4, ey = ts[1] + 4, ez = ts[2] + 4;
   const int lim[3] = {2 * ts[0] + 5, 2 * ts[1] + 5, 2 * ts[2] + 5};
   {
-    constexpr int U = 4;
-    const int rows = ey * ez;
+    // one box column per lane (ex <= 24 < 32), warp w the planes w, w +
+    // nwarp, ..., the loads of U rows of a plane issued before any is
+    // unpacked
+    constexpr int U = 8;
     const int gx = lane < ex ? wrap_add(t0[0] - 2, lane, nx) : 0;
-    for (int row0 = warp * U; row0 < rows; row0 += nwarp * U) {
-      uint32_t v[U];
-      uint2 c4[U];
+    for (int zs = warp; zs < ez; zs += nwarp) {
+      const long long zrow = (long long)wrap_add(t0[2] - 2, zs, nz) * ny;
+      for (int ys0 = 0; ys0 < ey; ys0 += U) {
+        uint32_t v[U];
+        uint2 c4[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int row = row0 + u;
-        v[u] = 0;
-        c4[u] = make_uint2(0, 0);
-        if (row < rows && lane < ex) {
-          const int ys = row % ey, zs = row / ey;
-          const long long cell =
-              ((long long)wrap_add(t0[2] - 2, zs, nz) * ny + wrap_add(t0[1] - 2, ys, ny)) * nx + gx;
-          v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
-                                        : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
-          c4[u] = *reinterpret_cast<const uint2*>(cnt + 4 * cell);
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          v[u] = 0;
+          c4[u] = make_uint2(0, 0);
+          if (ys < ey && lane < ex) {
+            const long long cell = (zrow + wrap_add(t0[1] - 2, ys, ny)) * nx + gx;
+            v[u] = P.storage == SMCX_INT8 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
+                                          : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+            c4[u] = *reinterpret_cast<const uint2*>(cnt + 4 * cell);
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int row = row0 + u;
-        if (row < rows && lane < ex) {
-          const int ys = row % ey, zs = row / ey;
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          if (ys < ey && lane < ex) {
 #pragma unroll
-          for (int b = 0; b < 4; b++) {
-            const int x = 2 * lane - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
-            if (x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]) continue;
-            const uint32_t sp = P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
-            const uint32_t cw = ((b < 2 ? c4[u].x : c4[u].y) >> (16 * (b & 1))) & 0xFFFFu;
-            box[BX::eidx(x, y, z)] = (uint16_t)(sp | (cw << 3));
+            for (int b = 0; b < 4; b++) {
+              const int x = 2 * lane - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
+              if (x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]) continue;
+              const uint32_t sp = P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u;
+              const uint32_t cw = ((b < 2 ? c4[u].x : c4[u].y) >> (16 * (b & 1))) & 0xFFFFu;
+              box[BX::eidx(x, y, z)] = (uint16_t)(sp | (cw << 3));
+            }
           }
         }
       }
@@ -785,42 +788,43 @@ __global__ void __launch_bounds__(128, TM == 20 ? 2 : 3)
 
   // write back the species of the tile and its 1-cell ring, the counts of
   // every site in the box
-  for (int row = warp; row < ey * ez; row += nwarp) {
-    const int ys = row % ey, zs = row / ey;
-    const int gy = wrap_add(t0[1] - 2, ys, ny), gz = wrap_add(t0[2] - 2, zs, nz);
-    const long long rbase = ((long long)gz * ny + gy) * nx;
-    for (int xs = lane; xs < ex; xs += 32) {
-      const long long cell = rbase + wrap_add(t0[0] - 2, xs, nx);
-      uint32_t w4[4];
-      bool in[4];
+  const int gxs = lane < ex ? wrap_add(t0[0] - 2, lane, nx) : 0;
+  for (int zs = warp; zs < ez; zs += nwarp) {
+    const long long zrow = (long long)wrap_add(t0[2] - 2, zs, nz) * ny;
+#pragma unroll 2
+    for (int ys = 0; ys < ey; ys++) {
+      if (lane < ex) {
+        const int xs = lane;
+        const long long cell = (zrow + wrap_add(t0[1] - 2, ys, ny)) * nx + gxs;
+        uint32_t w4[4];
+        bool in[4];
 #pragma unroll
-      for (int b = 0; b < 4; b++) {
-        const int x = 2 * xs - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
-        in[b] = !(x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]);
-        w4[b] = in[b] ? box[BX::eidx(x, y, z)] : 0u;
-      }
-      if (in[0] && in[1] && in[2] && in[3]) {
-        *reinterpret_cast<uint2*>(cnt + 4 * cell) =
-            make_uint2((w4[0] >> 3) | ((w4[1] >> 3) << 16), (w4[2] >> 3) | ((w4[3] >> 3) << 16));
-      } else {
+        for (int b = 0; b < 4; b++) {
+          const int x = 2 * xs - 1 + bx_of(b), y = 2 * ys - 1 + by_of(b), z = 2 * zs - 1 + bz_of(b);
+          in[b] = !(x < 0 || y < 0 || z < 0 || x > lim[0] || y > lim[1] || z > lim[2]);
+          w4[b] = in[b] ? box[BX::eidx(x, y, z)] : 0u;
+        }
+        if (in[0] && in[1] && in[2] && in[3]) {
+          *reinterpret_cast<uint2*>(cnt + 4 * cell) =
+              make_uint2((w4[0] >> 3) | ((w4[1] >> 3) << 16), (w4[2] >> 3) | ((w4[3] >> 3) << 16));
+        } else {
 #pragma unroll
-        for (int b = 0; b < 4; b++)
-          if (in[b]) cnt[4 * cell + b] = (uint16_t)(w4[b] >> 3);
-      }
-      const bool ring = xs >= 1 && xs <= ts[0] + 2 && ys >= 1 && ys <= ts[1] + 2 && zs >= 1 && zs <= ts[2] + 2;
-      if (ring) {
-        if (P.storage == SMCX_INT8)
-          *reinterpret_cast<uint32_t*>(P.sites + 4 * cell) =
-              (w4[0] & 7u) | ((w4[1] & 7u) << 8) | ((w4[2] & 7u) << 16) | ((w4[3] & 7u) << 24);
-        else
-          *reinterpret_cast<uint16_t*>(P.sites + 2 * cell) =
-              (uint16_t)((w4[0] & 7u) | ((w4[1] & 7u) << 4) | ((w4[2] & 7u) << 8) | ((w4[3] & 7u) << 12));
+          for (int b = 0; b < 4; b++)
+            if (in[b]) cnt[4 * cell + b] = (uint16_t)(w4[b] >> 3);
+        }
+        const bool ring = xs >= 1 && xs <= ts[0] + 2 && ys >= 1 && ys <= ts[1] + 2 && zs >= 1 && zs <= ts[2] + 2;
+        if (ring) {
+          if (P.storage == SMCX_INT8)
+            *reinterpret_cast<uint32_t*>(P.sites + 4 * cell) =
+                (w4[0] & 7u) | ((w4[1] & 7u) << 8) | ((w4[2] & 7u) << 16) | ((w4[3] & 7u) << 24);
+          else
+            *reinterpret_cast<uint16_t*>(P.sites + 2 * cell) =
+                (uint16_t)((w4[0] & 7u) | ((w4[1] & 7u) << 4) | ((w4[2] & 7u) << 8) | ((w4[3] & 7u) << 12));
+        }
       }
     }
   }
-  atomicAdd(&s_stat[0], acc);
-  atomicAdd(&s_stat[1], same);
-  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  add_stats_warp(s_stat, (unsigned)acc, (unsigned)same, dsum);
   __syncthreads();
   if (tid == 0) {
     atomicAdd(&P.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * 4);
