@@ -204,4 +204,80 @@ struct SweepParams {
   signed char gp[4][kMaxZ1][4];   // global (dx, dy, dz, b') of partners
 };
 
+// Generic tiled kernels: stage the cells [t0 - h, t0 + ts + h) of each axis
+// (periodic; the halo never exceeds one lattice edge) into a box of int8
+// species, cell (xs, ys, zs) at ((zs BY + ys) BX + xs) m.  One box column per
+// lane, warp w the rows w U .. w U + U - 1, w U + nwarp U, ... of each plane;
+// the loads of U rows are issued before any is unpacked.  blockDim is a
+// multiple of 32; every thread of the CTA takes part.
+template <int m>
+__device__ __forceinline__ void stage_generic(const SweepParams& P, int8_t* box, const int* t0, const int* ts, int h) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
+  for (int zs = 0; zs < ez; zs++) {
+    const long long zrow = (long long)wrap_add(t0[2] - h, zs, P.n[2]) * P.n[1];
+    for (int ys0 = warp * U; ys0 < ey; ys0 += nwarp * U)
+      for (int xs0 = 0; xs0 < ex; xs0 += 32) {
+        const int xs = xs0 + lane;
+        const int gx = xs < ex ? wrap_add(t0[0] - h, xs, P.n[0]) : 0;
+        uint32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          v[u] = 0;
+          if (ys < ey && xs < ex) {
+            const long long cell = (zrow + wrap_add(t0[1] - h, ys, P.n[1])) * P.n[0] + gx;
+            if (P.storage == SMCX_INT8)
+              v[u] = m == 4 ? *reinterpret_cast<const uint32_t*>(P.sites + 4 * cell)
+                            : (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell));
+            else
+              v[u] = m == 4 ? (uint32_t)(*reinterpret_cast<const uint16_t*>(P.sites + 2 * cell))
+                            : (uint32_t)P.sites[cell];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int ys = ys0 + u;
+          if (ys < ey && xs < ex) {
+            const int bi = ((zs * P.BY + ys) * P.BX + xs) * m;
+#pragma unroll
+            for (int b = 0; b < m; b++)
+              box[bi + b] = (int8_t)(P.storage == SMCX_INT8 ? (v[u] >> (8 * b)) & 0xFFu : (v[u] >> (4 * b)) & 15u);
+          }
+        }
+      }
+  }
+}
+
+// Generic tiled kernels: write the tile and its partner ring (rg cells) back
+// from the box staged by stage_generic with halo h.  One column per lane,
+// warp w the rows w, w + nwarp, ... of each plane.
+template <int m>
+__device__ __forceinline__ void write_back_generic(const SweepParams& P, const int8_t* box, const int* t0,
+                                                   const int* ts, int h, int rg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int wx = ts[0] + 2 * rg, wy = ts[1] + 2 * rg, wz = ts[2] + 2 * rg;
+  for (int zw = 0; zw < wz; zw++) {
+    const long long zrow = (long long)wrap_add(t0[2] - rg, zw, P.n[2]) * P.n[1];
+    const int zs = zw + h - rg;
+    for (int yw = warp; yw < wy; yw += nwarp) {
+      const long long rbase = (zrow + wrap_add(t0[1] - rg, yw, P.n[1])) * P.n[0];
+      const int ys = yw + h - rg;
+      for (int xw = lane; xw < wx; xw += 32) {
+        const long long cell = rbase + wrap_add(t0[0] - rg, xw, P.n[0]);
+        const int bi = ((zs * P.BY + ys) * P.BX + (xw + h - rg)) * m;
+        if (P.storage == SMCX_INT8) {
+#pragma unroll
+          for (int b = 0; b < m; b++) P.sites[cell * m + b] = (uint8_t)box[bi + b];
+        } else {
+#pragma unroll
+          for (int q = 0; q < m / 2; q++)
+            P.sites[cell * (m / 2) + q] = (uint8_t)(box[bi + 2 * q] | (box[bi + 2 * q + 1] << 4));
+        }
+      }
+    }
+  }
+}
+
 }  // namespace smcx

@@ -100,26 +100,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tile_sweep_qsro(const SweepPar
   for (int i = tid; i <= K; i += nth) s_start[i] = Q.start[i];
 
   const int h = P.h;
-  const int ex = ts[0] + 2 * h, ey = ts[1] + 2 * h, ez = ts[2] + 2 * h;
-  for (int i = tid; i < ex * ey * ez; i += nth) {
-    const int xs = i % ex, r = i / ex, ys = r % ey, zs = r / ey;
-    const int gx = wrap_add(t0[0] - h, xs, P.n[0]);
-    const int gy = wrap_add(t0[1] - h, ys, P.n[1]);
-    const int gz = wrap_add(t0[2] - h, zs, P.n[2]);
-    const long long cell = ((long long)gz * P.n[1] + gy) * P.n[0] + gx;
-    const int bi = ((zs * P.BY + ys) * P.BX + xs) * m;
-    if (P.storage == SMCX_INT8) {
-#pragma unroll
-      for (int b = 0; b < m; b++) box[bi + b] = (int8_t)P.sites[cell * m + b];
-    } else {
-#pragma unroll
-      for (int q = 0; q < m / 2; q++) {
-        const uint8_t byte = P.sites[cell * (m / 2) + q];
-        box[bi + 2 * q] = (int8_t)(byte & 15);
-        box[bi + 2 * q + 1] = (int8_t)(byte >> 4);
-      }
-    }
-  }
+  stage_generic<m>(P, box, t0, ts, h);
   __syncthreads();
 
   // same-species neighbours of box site i (sublattice bi) in shell k
@@ -244,29 +225,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_tile_sweep_qsro(const SweepPar
     __syncthreads();
   }
 
-  const int rg = P.ring;
-  const int wx = ts[0] + 2 * rg, wy = ts[1] + 2 * rg, wz = ts[2] + 2 * rg;
-  for (int i = tid; i < wx * wy * wz; i += nth) {
-    const int xw = i % wx, r = i / wx, yw = r % wy, zw = r / wy;
-    const int xs = xw + h - rg, ys = yw + h - rg, zs = zw + h - rg;
-    const int gx = wrap_add(t0[0] - rg, xw, P.n[0]);
-    const int gy = wrap_add(t0[1] - rg, yw, P.n[1]);
-    const int gz = wrap_add(t0[2] - rg, zw, P.n[2]);
-    const long long cell = ((long long)gz * P.n[1] + gy) * P.n[0] + gx;
-    const int bi = ((zs * P.BY + ys) * P.BX + xs) * m;
-    if (P.storage == SMCX_INT8) {
-#pragma unroll
-      for (int b = 0; b < m; b++) P.sites[cell * m + b] = (uint8_t)box[bi + b];
-    } else {
-#pragma unroll
-      for (int q = 0; q < m / 2; q++)
-        P.sites[cell * (m / 2) + q] = (uint8_t)(box[bi + 2 * q] | (box[bi + 2 * q + 1] << 4));
-    }
-  }
+  write_back_generic<m>(P, box, t0, ts, h, P.ring);
 
-  atomicAdd(&s_stat[0], acc);
-  atomicAdd(&s_stat[1], same);
-  atomicAdd(&s_stat[2], (unsigned long long)dsum);
+  add_stats_warp(s_stat, (unsigned)acc, (unsigned)same, dsum);
   __syncthreads();
   if (tid == 0) {
     atomicAdd(&P.stats[0], (unsigned long long)ts[0] * ts[1] * ts[2] * m);
