@@ -1073,7 +1073,7 @@ def run_smcx(args, rank, world, local_rank):
                      "frac_smem": None,
                      "note": "the same sweep with a shell-1 direction drawn per trial: same stationary "
                              "distribution, different trajectories; per-lane partner environments land on "
-                             "scattered banks (about 1.9 shared-memory wavefronts per load)"}
+                             "scattered banks (about 1.84 shared-memory wavefronts per load, the shared pipe at 93% of its peak)"}
 
     # ---- end to end through the C ABI with host buffers -------------------
     e2e = None
