@@ -388,8 +388,10 @@ __host__ __device__ constexpr size_t smem_bytes(int nA) {
   return BOX_BYTES + 16 * 4 + kRowWords * 4 + kPlaneWords * 4 + (size_t)(nA + kNB) * 4;
 }
 
+// Five CTAs per SM: the box and its tables (42.8 KB) allow no sixth, so the
+// launch bounds leave the kernel 102 registers (it takes 96).
 template <int K, int NW, int PL, int PROP = 0>
-__global__ void __launch_bounds__(128, 6) k_fcc_tile_sweep(const LatDesc D, const Planes Q, const Rows6 R, int tc) {
+__global__ void __launch_bounds__(128, 5) k_fcc_tile_sweep(const LatDesc D, const Planes Q, const Rows6 R, int tc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long s_stat[3];
   __shared__ uint8_t s_dir[PROP ? 512 : 4];  // phase directions (shared-direction proposals)
